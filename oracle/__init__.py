@@ -1,0 +1,201 @@
+"""Scalar CPU oracle for split block Bloom filters (arXiv 2101.01719).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` import this package.  The product path (the
+CUDA library and its Python binding) never imports, links or calls it.
+
+The arithmetic lives in ``sbbf_oracle.c`` (plain C99, no intrinsics); this
+module compiles it with gcc and exposes it through ctypes on numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sbbf_oracle.c")
+_HDR = os.path.join(_HERE, "sbbf_oracle.h")
+_LIB_PATH = os.path.join(_HERE, "libsbbf_oracle.so")
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/libsbbf_oracle.so`` (gcc, -O2, C99)."""
+    stale = (not os.path.exists(_LIB_PATH)
+             or os.path.getmtime(_LIB_PATH) < max(os.path.getmtime(_SRC),
+                                                  os.path.getmtime(_HDR)))
+    if force or stale:
+        tmp = _LIB_PATH + ".tmp.%d" % os.getpid()
+        cmd = ["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-Wall", "-Wextra",
+               "-o", tmp, _SRC, "-lm", "-lpthread"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _u64p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+
+
+def _u32p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB_PATH)
+            u64, u32, sz, i32 = (ctypes.c_uint64, ctypes.c_uint32,
+                                 ctypes.c_size_t, ctypes.c_int)
+            P64, P32 = ctypes.POINTER(u64), ctypes.POINTER(u32)
+            sigs = {
+                "oracle_block_index": (u64, [u64, u32]),
+                "oracle_make_mask": (None, [u32, P32]),
+                "oracle_seeds": (None, [P32]),
+                "oracle_insert": (None, [P32, u32, P64, sz]),
+                "oracle_insert_block_range": (None, [P32, u32, P64, sz, u64, u64]),
+                "oracle_find_one": (i32, [P32, u32, u64]),
+                "oracle_find": (None, [P32, u32, P64, sz, P32]),
+                "oracle_union": (None, [P32, P32, sz]),
+                "oracle_multi_insert": (u64, [P32, P64, P32, u32, P64, P32, sz]),
+                "oracle_multi_find": (u64, [P32, P64, P32, u32, P64, P32, sz, P32]),
+                "oracle_fpr_poisson": (ctypes.c_double, [ctypes.c_double]),
+                "oracle_fpr_standard": (ctypes.c_double,
+                                        [ctypes.c_double, ctypes.c_double]),
+                "oracle_splitmix64_at": (u64, [u64, u64]),
+                "oracle_splitmix64_fill": (None, [u64, u64, sz, P64]),
+                "oracle_find_mt": (i32, [P32, u32, P64, sz, P32, i32]),
+                "oracle_insert_mt": (i32, [P32, u32, P64, sz, i32]),
+                "oracle_num_cores": (i32, []),
+            }
+            for name, (res, args) in sigs.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _c_u64(a):
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    return a
+
+
+def _c_u32(a):
+    return np.ascontiguousarray(a, dtype=np.uint32)
+
+
+# ---- thin numpy wrappers -------------------------------------------------
+
+def seeds() -> np.ndarray:
+    out = np.zeros(8, np.uint32)
+    lib().oracle_seeds(_u32p(out))
+    return out
+
+
+def block_index(h: int, num_blocks: int) -> int:
+    return int(lib().oracle_block_index(h, num_blocks))
+
+
+def make_mask(x: int) -> np.ndarray:
+    out = np.zeros(8, np.uint32)
+    lib().oracle_make_mask(x & 0xFFFFFFFF, _u32p(out))
+    return out
+
+
+def new_filter(num_blocks: int) -> np.ndarray:
+    """An empty filter: num_blocks * 8 zero words."""
+    return np.zeros(int(num_blocks) * 8, np.uint32)
+
+
+def insert(words: np.ndarray, num_blocks: int, hashes) -> np.ndarray:
+    h = _c_u64(hashes)
+    assert words.dtype == np.uint32 and words.flags.c_contiguous
+    assert words.size == 8 * num_blocks
+    lib().oracle_insert(_u32p(words), num_blocks, _u64p(h), h.size)
+    return words
+
+
+def insert_block_range(sub_words, num_blocks, hashes, lo, hi):
+    h = _c_u64(hashes)
+    assert sub_words.dtype == np.uint32 and sub_words.size == 8 * (hi - lo)
+    lib().oracle_insert_block_range(_u32p(sub_words), num_blocks, _u64p(h),
+                                    h.size, lo, hi)
+    return sub_words
+
+
+def find_one(words, num_blocks, h) -> bool:
+    return bool(lib().oracle_find_one(_u32p(words), num_blocks, h))
+
+
+def find(words: np.ndarray, num_blocks: int, hashes) -> np.ndarray:
+    h = _c_u64(hashes)
+    out = np.zeros((h.size + 31) // 32, np.uint32)
+    lib().oracle_find(_u32p(words), num_blocks, _u64p(h), h.size, _u32p(out))
+    return out
+
+
+def union(dst: np.ndarray, src: np.ndarray) -> np.ndarray:
+    assert dst.size == src.size
+    s = _c_u32(src)
+    lib().oracle_union(_u32p(dst), _u32p(s), dst.size)
+    return dst
+
+
+def multi_insert(arena, base_block, num_blocks, hashes, ids) -> int:
+    h, t = _c_u64(hashes), _c_u32(ids)
+    bb, nb = _c_u64(base_block), _c_u32(num_blocks)
+    return int(lib().oracle_multi_insert(_u32p(arena), _u64p(bb), _u32p(nb),
+                                         nb.size, _u64p(h), _u32p(t), h.size))
+
+
+def multi_find(arena, base_block, num_blocks, hashes, ids):
+    h, t = _c_u64(hashes), _c_u32(ids)
+    bb, nb = _c_u64(base_block), _c_u32(num_blocks)
+    out = np.zeros((h.size + 31) // 32, np.uint32)
+    bad = lib().oracle_multi_find(_u32p(arena), _u64p(bb), _u32p(nb), nb.size,
+                                  _u64p(h), _u32p(t), h.size, _u32p(out))
+    return out, int(bad)
+
+
+def fpr_poisson(a: float) -> float:
+    return float(lib().oracle_fpr_poisson(a))
+
+
+def fpr_standard(bits_per_key: float, k: float) -> float:
+    return float(lib().oracle_fpr_standard(bits_per_key, k))
+
+
+def splitmix64_at(seed: int, i: int) -> int:
+    return int(lib().oracle_splitmix64_at(seed, i))
+
+
+def splitmix64_fill(seed: int, start: int, n: int) -> np.ndarray:
+    out = np.empty(n, np.uint64)
+    lib().oracle_splitmix64_fill(seed, start, n, _u64p(out))
+    return out
+
+
+def find_mt(words, num_blocks, hashes, n_threads):
+    h = _c_u64(hashes)
+    out = np.zeros((h.size + 31) // 32, np.uint32)
+    used = lib().oracle_find_mt(_u32p(words), num_blocks, _u64p(h), h.size,
+                                _u32p(out), n_threads)
+    return out, int(used)
+
+
+def insert_mt(words, num_blocks, hashes, n_threads) -> int:
+    h = _c_u64(hashes)
+    return int(lib().oracle_insert_mt(_u32p(words), num_blocks, _u64p(h),
+                                      h.size, n_threads))
+
+
+def num_cores() -> int:
+    return int(lib().oracle_num_cores())

@@ -1,0 +1,102 @@
+/*
+ * Scalar reference ("oracle") for split block Bloom filters (Apple,
+ * "Split block Bloom filters", arXiv 2101.01719).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This header and sbbf_oracle.c are used by the
+ * test suite, by the smoke check and by the benchmark's CPU-baseline leg.
+ * The product library (the CUDA path) never includes, links or calls it, and
+ * it shares no header, table or helper with that path.
+ *
+ * Layout (shared by convention only, restated independently on each side):
+ *   a filter of B blocks is B*8 little-endian uint32 words; block b occupies
+ *   words [8b, 8b+8); lane i of block b is word 8b+i; bit j of a lane is
+ *   (1u << j).  This is how the appendix figure stores one __m256i per block.
+ *
+ * Lookup results are packed LSB-first: bit (k % 32) of word (k / 32) is the
+ * answer for hash k; bits past the last hash are zero.
+ */
+#ifndef SBBF_ORACLE_H
+#define SBBF_ORACLE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Appendix figure, block_index: high 32 bits of the hash, range-reduced to
+ * [0, num_blocks) by a 32x32->64 multiply and a 32-bit right shift. */
+uint64_t oracle_block_index(uint64_t hash, uint32_t num_blocks);
+
+/* Intro (multiply-shift hashing into [0,32)) and appendix figure, make_mask:
+ * mask[i] = 1 << ((s_i * x mod 2^32) >> 27) for the eight odd seeds s_i. */
+void oracle_make_mask(uint32_t x, uint32_t mask[8]);
+
+/* The eight seeds in lane order 0..7 (copied out for tests). */
+void oracle_seeds(uint32_t out[8]);
+
+/* Appendix figure, add_hash, applied to hashes[0..n) in order. */
+void oracle_insert(uint32_t *words, uint32_t num_blocks,
+                   const uint64_t *hashes, size_t n);
+
+/* add_hash restricted to blocks in [lo, hi): keys whose block falls outside
+ * are skipped; sub_words holds blocks lo..hi-1 (word 8*(b-lo)+i). */
+void oracle_insert_block_range(uint32_t *sub_words, uint32_t num_blocks,
+                               const uint64_t *hashes, size_t n,
+                               uint64_t lo, uint64_t hi);
+
+/* Appendix figure, find_hash for one hash: 1 iff every mask bit is set. */
+int oracle_find_one(const uint32_t *words, uint32_t num_blocks, uint64_t hash);
+
+/* find_hash over hashes[0..n) into a packed bitmask of (n+31)/32 words. */
+void oracle_find(const uint32_t *words, uint32_t num_blocks,
+                 const uint64_t *hashes, size_t n, uint32_t *out_bits);
+
+/* Word-wise OR of src into dst (union of two filters with equal B). */
+void oracle_union(uint32_t *dst, const uint32_t *src, size_t n_words);
+
+/* Several filters in one word arena.  Filter t holds num_blocks[t] blocks
+ * starting at block base_block[t] of the arena.  A hash with ids[k] >=
+ * n_filters is skipped (insert) or answers 0 (find); the return value counts
+ * such hashes. */
+uint64_t oracle_multi_insert(uint32_t *arena, const uint64_t *base_block,
+                             const uint32_t *num_blocks, uint32_t n_filters,
+                             const uint64_t *hashes, const uint32_t *ids,
+                             size_t n);
+uint64_t oracle_multi_find(const uint32_t *arena, const uint64_t *base_block,
+                           const uint32_t *num_blocks, uint32_t n_filters,
+                           const uint64_t *hashes, const uint32_t *ids,
+                           size_t n, uint32_t *out_bits);
+
+/* False positive rate approximation (FPR analysis): sum over i of the
+ * Poisson(a) probability of i keys in a block times (1-(1-1/32)^i)^8. */
+double oracle_fpr_poisson(double a);
+
+/* Standard Bloom filter FPR (1 - e^{-k/bits_per_key})^k, for the paper's
+ * comparison claims only. */
+double oracle_fpr_standard(double bits_per_key, double k);
+
+/* splitmix64 (Steele, Lea, Flood, OOPSLA 2014) in counter form: output i of
+ * the stream seeded with `seed` is mix(seed + (i+1)*0x9E3779B97F4A7C15). */
+uint64_t oracle_splitmix64_at(uint64_t seed, uint64_t i);
+void oracle_splitmix64_fill(uint64_t seed, uint64_t start, size_t n,
+                            uint64_t *out);
+
+/* Multi-threaded drivers used only to time the oracle on all host cores.
+ * They call the scalar functions above on disjoint pieces of the work:
+ * lookups by contiguous chunks of 32-hash groups, inserts by block range.
+ * The return value is the number of threads actually used. */
+int oracle_find_mt(const uint32_t *words, uint32_t num_blocks,
+                   const uint64_t *hashes, size_t n, uint32_t *out_bits,
+                   int n_threads);
+int oracle_insert_mt(uint32_t *words, uint32_t num_blocks,
+                     const uint64_t *hashes, size_t n, int n_threads);
+
+/* Number of online host cores. */
+int oracle_num_cores(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

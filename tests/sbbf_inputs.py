@@ -1,0 +1,90 @@
+"""Seeded synthetic inputs shared by the oracle-side and GPU-side tests.
+
+This module holds no arithmetic of the filter itself.  It only produces
+64-bit hash values (splitmix64, Steele/Lea/Flood 2014, in counter form) and
+mixes them into query streams by the recipe below, so that the same bytes can
+be handed to the CPU oracle and to the CUDA library.  The CUDA library and the
+oracle each carry their own splitmix64 for sizes that cannot be materialised
+on the host; tests pin all three against the published reference sequence.
+
+Stream seeds: ``0x5BBF000000000000 | (cfg << 8) | role`` with roles
+0 = inserted hashes, 1 = fresh lookup hashes, 2 = member selector,
+3 = filter sizes, 4 = order / shuffles, 5 = arrivals, 6 = request sizes.
+
+Query recipe (member fraction f): query j is a member when
+``(r_j >> 32) < round(f * 2^32)`` with r_j the role-2 stream; a member is
+``inserted[((r_j & 0xffffffff) * n_inserted) >> 32]``, otherwise the fresh
+role-1 value j.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+ROLE_INSERT, ROLE_FRESH, ROLE_MEMBER, ROLE_SIZES, ROLE_ORDER = 0, 1, 2, 3, 4
+ROLE_ARRIVAL, ROLE_REQSIZE = 5, 6
+
+
+def stream_seed(cfg: int, role: int) -> int:
+    return 0x5BBF000000000000 | (cfg << 8) | role
+
+
+def splitmix64(seed: int, start: int, n: int) -> np.ndarray:
+    """Outputs start..start+n-1 of the splitmix64 stream seeded with `seed`."""
+    with np.errstate(over="ignore"):
+        i = np.arange(start + 1, start + n + 1, dtype=np.uint64)
+        z = np.uint64(seed) + i * GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def stream(cfg: int, role: int, n: int, start: int = 0) -> np.ndarray:
+    return splitmix64(stream_seed(cfg, role), start, n)
+
+
+def member_threshold(frac: float) -> int:
+    return int(round(frac * 2.0**32))
+
+
+def queries(cfg: int, inserted: np.ndarray, n_queries: int, frac: float,
+            start: int = 0) -> np.ndarray:
+    """Query hashes start..start+n_queries-1 by the recipe in the docstring."""
+    r = stream(cfg, ROLE_MEMBER, n_queries, start)
+    fresh = stream(cfg, ROLE_FRESH, n_queries, start)
+    thr = np.uint64(member_threshold(frac))
+    member = (r >> np.uint64(32)) < thr
+    with np.errstate(over="ignore"):
+        idx = ((r & np.uint64(0xFFFFFFFF)) * np.uint64(len(inserted))) >> np.uint64(32)
+    out = fresh.copy()
+    out[member] = inserted[idx[member].astype(np.int64)]
+    return out
+
+
+def query_is_member(cfg: int, n_queries: int, frac: float, start: int = 0):
+    r = stream(cfg, ROLE_MEMBER, n_queries, start)
+    return (r >> np.uint64(32)) < np.uint64(member_threshold(frac))
+
+
+def uniform01(cfg: int, role: int, n: int, start: int = 0) -> np.ndarray:
+    """Uniform doubles in [0,1) from the top 53 bits of a stream."""
+    return (stream(cfg, role, n, start) >> np.uint64(11)).astype(np.float64) * 2.0**-53
+
+
+def multi_filter_sizes(cfg: int, n_filters: int, lo: float, hi: float,
+                       bits_per_key: float):
+    """Key counts log-uniform in [lo, hi] (rounded) and blocks sized at
+    bits_per_key, rounded up to whole 256-bit blocks."""
+    u = uniform01(cfg, ROLE_SIZES, n_filters)
+    n_keys = np.rint(np.exp(np.log(lo) + u * (np.log(hi) - np.log(lo)))).astype(np.int64)
+    blocks = np.ceil(n_keys * bits_per_key / 256.0).astype(np.int64)
+    blocks = np.maximum(blocks, 1)
+    return n_keys, blocks
+
+
+def permutation(cfg: int, n: int, start: int = 0) -> np.ndarray:
+    """A seeded permutation of 0..n-1 (argsort of a role-4 stream)."""
+    return np.argsort(stream(cfg, ROLE_ORDER, n, start), kind="stable")
