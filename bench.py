@@ -1,0 +1,416 @@
+"""Benchmark: split block Bloom filter insert + lookup throughput on GB300.
+
+One step = one pass of the hot path over one batch of the workload: clear the
+filter, insert the batch of hashes (appendix add_hash for each), look up the
+batch of queries (appendix find_hash for each, packed bitmask out).  The
+default workload is 1M hashes into a 32768-block (1 MiB) filter and 256M
+lookups, half of them members (the paper's 1M-element size with a lookup
+batch far larger than L2).  Inputs are seeded splitmix64 streams generated on
+the device before the timed region; the lookup stream (2 GiB) is larger than
+L2, so no flush is needed between steps.
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle instead (a
+bounded sample of the same workload on the host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SBBF insert/lookup Gkeys/s"
+UNIT = "Gkeys/s"
+FALLBACK_HBM_GBS = 6800.0
+DOMINANT_KERNEL = "find_kernel"
+# Algorithmic HBM bytes per lookup with an L2-resident filter: the 8-byte
+# hash read once plus its 1/8-byte share of the packed result.
+LOOKUP_HBM_BYTES_L2_RESIDENT = 8.0 + 1.0 / 8.0
+# ... and with a filter larger than L2: plus one 32-byte block read.
+LOOKUP_HBM_BYTES_HBM_RESIDENT = 8.0 + 32.0 + 1.0 / 8.0
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=600)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="sbbf_32768blk_1M_ins_256M_lookup")
+    p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--cpu-seconds", type=float, default=12.0,
+                   help="approximate CPU work for the oracle baseline")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args(argv)
+
+
+# ---- distributed plumbing (one process per GPU; units sharded by rank) -----
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def init_dist(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend)
+    return dist if world > 1 else None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, value: float, device=None) -> float:
+    """Largest value over all ranks (timing only; no data-path collective)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(units_per_rank: list[int], seconds_max: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return sum(units_per_rank) / seconds_max
+
+
+# ---- measured peaks, clocks, profile figures --------------------------------
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", self.gpu_id],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def stop(self):
+        if self.proc is None:
+            return self
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        self.lines = [l for l in out.splitlines() if l.strip()]
+        return self
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower() in ("active", "1", "0x1"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_sources_digest() -> str:
+    """Digest of the CUDA sources; a stored ncu figure applies only while the
+    kernels are unchanged."""
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2101_01719_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(name.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, or None if absent or taken on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    digest = kernel_sources_digest()
+    for line in lines:
+        parts = line.split()
+        if len(parts) >= 4 and parts[0] == workload and parts[1] == DOMINANT_KERNEL:
+            if parts[2] == digest:
+                return float(parts[3])
+    return None
+
+
+# ---- our arm ----------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2101_01719_gb300 as sb
+    from paper_2101_01719_gb300 import workloads as wl
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = init_dist(world, "nccl")
+    w = wl.WORKLOADS[args.workload]
+    if w.n_insert > w.insert_batch:
+        raise SystemExit("bench workload must insert in one batch per step")
+    stream = torch.cuda.current_stream()
+
+    # Inputs resident in HBM before timing; each rank takes its own slice of
+    # the lookup stream (units sharded by rank, no data-path collective).
+    ins = wl.gen_inserts(w, 0, w.n_insert, device=dev)
+    qry = wl.gen_queries(w, rank * w.n_lookup, w.n_lookup, device=dev)
+    out = torch.empty(sb.out_words(w.n_lookup), dtype=torch.int32, device=dev)
+    f = sb.Filter(w.num_blocks, device=dev)
+    torch.cuda.synchronize()
+
+    def step():
+        f.clear()
+        f.insert(ins)
+        f.find(qry, out=out)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    # Per-kernel events for the roofline (same stream as the launches).
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    props = torch.cuda.get_device_properties(dev)
+    uuid = str(getattr(props, "uuid", ""))
+    gpu_id = uuid if uuid.startswith("GPU-") else ("GPU-" + uuid if uuid else str(local))
+    sampler = ClockSampler(gpu_id).start()
+    time.sleep(0.3)
+
+    barrier(dist)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for s in range(args.steps):
+        e = ev[s]
+        e[0].record(stream)
+        f.clear()
+        e[1].record(stream)
+        f.insert(ins)
+        e[2].record(stream)
+        f.find(qry, out=out)
+        e[3].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    sampler.stop()
+    elapsed_ms = t0.elapsed_time(t1)
+    slowest_ms = max_over_ranks(dist, elapsed_ms, dev)
+
+    insert_ms = statistics.mean(ev[s][1].elapsed_time(ev[s][2]) for s in range(args.steps))
+    find_ms = statistics.mean(ev[s][2].elapsed_time(ev[s][3]) for s in range(args.steps))
+    keys_per_step = w.n_insert + w.n_lookup
+    value = aggregate([keys_per_step * args.steps] * world, slowest_ms / 1e3) / 1e9
+
+    # correctness spot-check of the timed output (members must hit)
+    hits = int(sb.count_bits(out, w.n_lookup).item())
+
+    # end to end through the host-buffer C-ABI calls (pinned host memory)
+    e2e = None
+    if args.e2e_steps > 0:
+        h_ins = ins.cpu().pin_memory()
+        h_q = qry.cpu().pin_memory()
+        h_out = torch.empty(sb.out_words(w.n_lookup), dtype=torch.int32).pin_memory()
+        pipe = sb.HostPipe(1 << 24)
+        f.clear()
+        pipe.insert(f, h_ins)
+        pipe.find(f, h_q, h_out)  # warm-up
+        barrier(dist)
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            f.clear()
+            pipe.insert(f, h_ins)
+            pipe.find(f, h_q, h_out)
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(dist, time.perf_counter() - a, dev)
+        assert np.array_equal(h_out.numpy(), out.cpu().numpy()), "host path result differs"
+        e2e = {"value": aggregate([keys_per_step * args.e2e_steps] * world, e2e_s) / 1e9,
+               "unit": UNIT, "h2d_bytes_per_step": 8 * keys_per_step,
+               "d2h_bytes_per_step": 4 * sb.out_words(w.n_lookup)}
+        del h_ins, h_q, h_out, pipe
+
+    peak, peak_kind = measured_peaks()
+    l2_bytes = props.L2_cache_size if hasattr(props, "L2_cache_size") else 126 * 2**20
+    per_key = (LOOKUP_HBM_BYTES_L2_RESIDENT if w.filter_bytes < l2_bytes / 2
+               else LOOKUP_HBM_BYTES_HBM_RESIDENT)
+    achieved = per_key * w.n_lookup / (find_ms / 1e3) / 1e9
+    traffic = profiled_traffic(w.name)
+    clocks = sampler.summary()
+
+    if rank != 0:
+        return None
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3),
+        "ms_per_step": round(slowest_ms / args.steps, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (seeded splitmix64 hashes generated on the device)",
+        "config": {"workload": w.name, "num_blocks": w.num_blocks,
+                   "filter_bytes": w.filter_bytes, "n_insert": w.n_insert,
+                   "n_lookup": w.n_lookup, "member_frac": w.member_frac,
+                   "l2": "inputs larger than L2 (%.1f GiB lookup stream per step)"
+                         % (8 * w.n_lookup / 2**30),
+                   "parallelism": "independent replicas, lookups sharded by rank"
+                                  if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": DOMINANT_KERNEL,
+                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                     "bytes_per_key": per_key, "traffic": traffic},
+        "rows": {"insert_gkeys_s": round(w.n_insert / (insert_ms / 1e3) / 1e9, 3),
+                 "lookup_gkeys_s": round(w.n_lookup / (find_ms / 1e3) / 1e9, 3),
+                 "insert_ms": round(insert_ms, 5), "lookup_ms": round(find_ms, 5),
+                 "lookup_hits": hits, "lookup_hit_frac": round(hits / w.n_lookup, 5)},
+        "e2e": e2e,
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+    return line
+
+
+# ---- the CPU oracle (baseline / reference arm) ---------------------------------
+
+def cpu_baseline(w, seconds: float, steps: int = 1):
+    """Time the oracle (scalar C, all host cores) on a bounded sample of the
+    workload: the full insert batch, then lookups over a sample of the query
+    stream repeated until about `seconds` of CPU time per step."""
+    import numpy as np
+
+    import oracle
+
+    cores = oracle.num_cores()
+    keys = oracle.splitmix64_fill(0x5BBF000000000000 | (w.cfg << 8), 0, w.n_insert)
+    sample = min(w.n_lookup, 1 << 24)
+    # the query sample by the same recipe as the device generator
+    thr = int(round(w.member_frac * 2.0**32))
+    r = oracle.splitmix64_fill(0x5BBF000000000000 | (w.cfg << 8) | 2, 0, sample)
+    fresh = oracle.splitmix64_fill(0x5BBF000000000000 | (w.cfg << 8) | 1, 0, sample)
+    with np.errstate(over="ignore"):
+        idx = ((r & np.uint64(0xFFFFFFFF)) * np.uint64(w.n_insert)) >> np.uint64(32)
+    q = np.where((r >> np.uint64(32)) < np.uint64(thr), keys[idx.astype(np.int64)], fresh)
+    f = oracle.new_filter(w.num_blocks)
+    t_ins = t_find = 0.0
+    n_ins = n_find = 0
+    used = cores
+    for _ in range(steps):
+        f[:] = 0
+        a = time.perf_counter()
+        oracle.insert_mt(f, w.num_blocks, keys, cores)
+        t_ins += time.perf_counter() - a
+        n_ins += w.n_insert
+        a = time.perf_counter()
+        _, used = oracle.find_mt(f, w.num_blocks, q[: 1 << 20], cores)
+        probe = time.perf_counter() - a
+        reps = max(1, int(seconds / steps / max(probe * 16, 1e-6)))
+        a = time.perf_counter()
+        for _ in range(reps):
+            _, used = oracle.find_mt(f, w.num_blocks, q, cores)
+        t_find += time.perf_counter() - a
+        n_find += reps * sample
+    value = (n_ins + n_find) / (t_ins + t_find) / 1e9
+    return {"value": round(value, 5), "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": "%d inserts + %d lookups (%d x a %d-query prefix of the lookup stream), "
+                      "scalar C oracle on %d threads" % (n_ins, n_find, n_find // sample,
+                                                          sample, used),
+            "insert_mkeys_s": round(n_ins / t_ins / 1e6, 2),
+            "lookup_mkeys_s": round(n_find / t_find / 1e6, 2)}
+
+
+def run_reference(args):
+    from paper_2101_01719_gb300 import workloads as wl
+
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None  # rank 0 alone runs the CPU oracle
+    w = wl.WORKLOADS[args.workload]
+    per_step = args.cpu_seconds / max(1, args.steps + args.warmup) * 2
+    cpu_baseline(w, per_step, steps=max(args.warmup, 1))  # warm-up
+    a = time.perf_counter()
+    cb = cpu_baseline(w, per_step, steps=args.steps)
+    elapsed = time.perf_counter() - a
+    return {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 1),
+            "ms_per_step": round(1e3 * elapsed / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (seeded splitmix64 hashes)",
+            "config": {"workload": w.name, "num_blocks": w.num_blocks,
+                       "n_insert": w.n_insert, "n_lookup": w.n_lookup,
+                       "member_frac": w.member_frac},
+            "cpu_baseline": {"value": cb["value"], "unit": UNIT, "cores": cb["cores"],
+                             "kind": "oracle", "sample": cb["sample"]},
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        line = run_reference(args)
+    else:
+        line = run_ours(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    rank, world, _ = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        if dist.is_initialized():
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

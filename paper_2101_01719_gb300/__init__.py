@@ -1,0 +1,18 @@
+"""GB300 (sm_103a) split block Bloom filters: batched insert and lookup of
+64-bit hash values (Apple, "Split block Bloom filters", arXiv 2101.01719).
+
+The compute runs in ``libsbbf.so`` (hand-written CUDA behind the C ABI in
+``include/sbbf.h``); this package is its thin Python binding.
+"""
+from .sbbf import (  # noqa: F401
+    Filter,
+    HostPipe,
+    SbbfError,
+    check,
+    count_bits,
+    fill_queries,
+    fill_splitmix64,
+    lib,
+    out_words,
+    stream_handle,
+)

@@ -1,0 +1,63 @@
+// Host-side helpers shared by the library's translation units: status
+// bookkeeping, device properties and launch sizing.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "sbbf.h"
+
+namespace sbbf {
+
+// Records a failing CUDA call for sbbf_last_cuda_error() and maps it.
+sbbf_status record_cuda(cudaError_t e);
+
+#define SBBF_CUDA(call)                                   \
+  do {                                                    \
+    cudaError_t _e = (call);                              \
+    if (_e != cudaSuccess) return ::sbbf::record_cuda(_e); \
+  } while (0)
+
+// Checks the launch just enqueued.
+inline sbbf_status launch_status() {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SBBF_OK : record_cuda(e);
+}
+
+// Streaming multiprocessors of the current device (cached per device).
+int sm_count();
+int current_device();
+
+// Resident CTAs per SM of `kernel` at `threads` threads and `smem` bytes of
+// dynamic shared memory (cached by the caller in a static).
+template <typename K>
+int occupancy(K kernel, int threads, size_t smem = 0) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) !=
+          cudaSuccess ||
+      n < 1)
+    n = 1;
+  return n;
+}
+
+// Grid for `work_items` independent items, each CTA taking `per_cta`, capped
+// at `resident` CTAs per SM on every SM (the kernels loop over the rest).
+inline unsigned grid_for(uint64_t work_items, uint64_t per_cta, int resident) {
+  uint64_t want = (work_items + per_cta - 1) / per_cta;
+  uint64_t cap = static_cast<uint64_t>(sm_count()) * static_cast<uint64_t>(resident);
+  if (want > cap) want = cap;
+  if (want < 1) want = 1;
+  return static_cast<unsigned>(want);
+}
+
+}  // namespace sbbf
+
+// The single-filter handle (opaque to callers).
+struct sbbf_filter {
+  uint32_t *words;      // device, num_blocks * 8 uint32
+  uint32_t num_blocks;
+  int device;
+  int owns;             // 1: allocated by the library
+};

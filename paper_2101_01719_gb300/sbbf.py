@@ -1,0 +1,236 @@
+"""Thin Python binding of ``libsbbf.so`` (ctypes).
+
+Argument marshalling only: every step of insert, lookup and union runs in the
+library's CUDA kernels.  PyTorch supplies device memory (filters created here
+are backed by a torch tensor and wrapped with ``sbbf_wrap``) and streams
+(``torch.cuda.current_stream()`` unless a stream is passed).  There is no CPU
+fallback: if the library is missing or fails to load, every call raises.
+
+Tensors passed in must be CUDA tensors on the filter's device; a tensor used on
+a stream other than the one it was allocated on must be kept alive by the
+caller (``Tensor.record_stream``) until the work completes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsbbf.so")
+
+SBBF_OK, SBBF_EINVAL, SBBF_ENOMEM, SBBF_ECUDA, SBBF_EBUSY, SBBF_ETIMEOUT, SBBF_ERANGE = range(7)
+
+_lib = None
+_lock = threading.Lock()
+
+_c = ctypes
+_P = _c.c_void_p
+_u32, _u64, _sz, _int = _c.c_uint32, _c.c_uint64, _c.c_size_t, _c.c_int
+
+# name -> (restype, argtypes); every symbol declared in include/sbbf.h.
+SIGNATURES = {
+    "sbbf_status_string": (_c.c_char_p, [_int]),
+    "sbbf_last_cuda_error": (_int, []),
+    "sbbf_version": (_u32, []),
+    "sbbf_create": (_int, [_u32, _c.POINTER(_P)]),
+    "sbbf_wrap": (_int, [_P, _u32, _c.POINTER(_P)]),
+    "sbbf_create_from_host": (_int, [_P, _u32, _c.POINTER(_P)]),
+    "sbbf_destroy": (_int, [_P]),
+    "sbbf_num_blocks": (_u32, [_P]),
+    "sbbf_device_words": (_int, [_P, _c.POINTER(_P), _c.POINTER(_sz)]),
+    "sbbf_clear": (_int, [_P, _P]),
+    "sbbf_insert_hashes": (_int, [_P, _P, _sz, _P]),
+    "sbbf_find_hashes": (_int, [_P, _P, _sz, _P, _P]),
+    "sbbf_union": (_int, [_P, _P, _P]),
+    "sbbf_copy_to_host": (_int, [_P, _P, _sz, _P]),
+    "sbbf_host_pipe_create": (_int, [_sz, _c.POINTER(_P)]),
+    "sbbf_host_pipe_destroy": (_int, [_P]),
+    "sbbf_insert_hashes_host": (_int, [_P, _P, _P, _sz, _P]),
+    "sbbf_find_hashes_host": (_int, [_P, _P, _P, _sz, _P, _P]),
+    "sbbf_fill_splitmix64": (_int, [_P, _sz, _u64, _u64, _P]),
+    "sbbf_fill_queries": (_int, [_P, _sz, _u64, _u64, _u64, _u64, _u64, _u64, _u64, _P]),
+    "sbbf_count_bits": (_int, [_P, _sz, _P, _P]),
+}
+
+
+class SbbfError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        msg = "%s failed: %s" % (what, lib().sbbf_status_string(status).decode())
+        if status == SBBF_ECUDA:
+            msg += " (cudaError %d)" % lib().sbbf_last_cuda_error()
+        super().__init__(msg)
+
+
+def lib():
+    """The loaded ``libsbbf.so`` (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    "libsbbf.so is not built (%s); run paper_2101_01719_gb300.build.build()"
+                    % LIB_PATH)
+            L = _c.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def check(status: int, what: str) -> None:
+    if status != SBBF_OK:
+        raise SbbfError(status, what)
+
+
+def stream_handle(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _hashes_ptr(t: torch.Tensor, device) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("hashes must be a CUDA tensor")
+    if t.dtype not in (torch.int64, torch.uint64):
+        raise TypeError("hashes must be int64 or uint64 (64-bit hash values)")
+    if not t.is_contiguous():
+        raise ValueError("hashes must be contiguous")
+    if device is not None and t.device != device:
+        raise ValueError("hashes are on %s, filter on %s" % (t.device, device))
+    return t.data_ptr()
+
+
+def out_words(n: int) -> int:
+    """Words of packed lookup output for n hashes."""
+    return (n + 31) // 32
+
+
+class Filter:
+    """A split block Bloom filter of ``num_blocks`` 256-bit blocks whose words
+    live in a torch tensor (``self.words``, int32, ``num_blocks * 8``)."""
+
+    def __init__(self, num_blocks: int, device=None, words: torch.Tensor | None = None):
+        if num_blocks <= 0 or num_blocks >= 2**32:
+            raise ValueError("num_blocks must be in [1, 2^32)")
+        if words is None:
+            dev = (torch.device("cuda", torch.cuda.current_device()) if device is None
+                   else torch.device(device))
+            words = torch.zeros(num_blocks * 8, dtype=torch.int32, device=dev)
+        if words.numel() != num_blocks * 8 or not words.is_cuda or not words.is_contiguous():
+            raise ValueError("words must be a contiguous CUDA tensor of num_blocks*8 int32")
+        self.words = words
+        self.num_blocks = int(num_blocks)
+        self.device = words.device
+        h = _P()
+        with torch.cuda.device(self.device):
+            check(lib().sbbf_wrap(words.data_ptr(), num_blocks, _c.byref(h)), "sbbf_wrap")
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.sbbf_destroy(h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def clear(self, stream=None):
+        with torch.cuda.device(self.device):
+            check(lib().sbbf_clear(self._h, stream_handle(stream)), "sbbf_clear")
+        return self
+
+    def insert(self, hashes: torch.Tensor, stream=None):
+        ptr = _hashes_ptr(hashes, self.device)
+        with torch.cuda.device(self.device):
+            check(lib().sbbf_insert_hashes(self._h, ptr, hashes.numel(), stream_handle(stream)),
+                  "sbbf_insert_hashes")
+        return self
+
+    def find(self, hashes: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        n = hashes.numel()
+        ptr = _hashes_ptr(hashes, self.device)
+        if out is None:
+            out = torch.empty(out_words(n), dtype=torch.int32, device=self.device)
+        elif out.numel() < out_words(n) or not out.is_cuda or out.element_size() != 4:
+            raise ValueError("out must be a CUDA int32 tensor of (n+31)//32 words")
+        with torch.cuda.device(self.device):
+            check(lib().sbbf_find_hashes(self._h, ptr, n, out.data_ptr(), stream_handle(stream)),
+                  "sbbf_find_hashes")
+        return out
+
+    def union_(self, other: "Filter", stream=None):
+        with torch.cuda.device(self.device):
+            check(lib().sbbf_union(self._h, other._h, stream_handle(stream)), "sbbf_union")
+        return self
+
+    def to_numpy(self):
+        import numpy as np
+        return self.words.cpu().numpy().view(np.uint32)
+
+
+class HostPipe:
+    """Staging buffers and streams for host-memory insert/lookup calls."""
+
+    def __init__(self, chunk_hashes: int = 1 << 24):
+        h = _P()
+        check(lib().sbbf_host_pipe_create(chunk_hashes, _c.byref(h)), "sbbf_host_pipe_create")
+        self._h = h
+        self.chunk = chunk_hashes
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.sbbf_host_pipe_destroy(h)
+            self._h = None
+
+    def insert(self, f: Filter, h_hashes: torch.Tensor, stream=None):
+        assert not h_hashes.is_cuda and h_hashes.is_contiguous() and h_hashes.element_size() == 8
+        with torch.cuda.device(f.device):
+            check(lib().sbbf_insert_hashes_host(f.handle, self._h, h_hashes.data_ptr(),
+                                                h_hashes.numel(), stream_handle(stream)),
+                  "sbbf_insert_hashes_host")
+
+    def find(self, f: Filter, h_hashes: torch.Tensor, h_out: torch.Tensor, stream=None):
+        assert not h_hashes.is_cuda and h_hashes.is_contiguous() and h_hashes.element_size() == 8
+        assert not h_out.is_cuda and h_out.numel() >= out_words(h_hashes.numel())
+        with torch.cuda.device(f.device):
+            check(lib().sbbf_find_hashes_host(f.handle, self._h, h_hashes.data_ptr(),
+                                              h_hashes.numel(), h_out.data_ptr(),
+                                              stream_handle(stream)),
+                  "sbbf_find_hashes_host")
+        return h_out
+
+
+# ---- synthetic inputs ------------------------------------------------------
+
+def fill_splitmix64(out: torch.Tensor, seed: int, start: int = 0, stream=None):
+    """out[k] = splitmix64 output (start + k) of `seed` (int64 view of the bits)."""
+    assert out.is_cuda and out.element_size() == 8 and out.is_contiguous()
+    check(lib().sbbf_fill_splitmix64(out.data_ptr(), out.numel(), seed & (2**64 - 1),
+                                     start, stream_handle(stream)), "sbbf_fill_splitmix64")
+    return out
+
+
+def fill_queries(out: torch.Tensor, start: int, ins_seed: int, ins_start: int, n_inserted: int,
+                 fresh_seed: int, member_seed: int, member_threshold: int, stream=None):
+    assert out.is_cuda and out.element_size() == 8 and out.is_contiguous()
+    check(lib().sbbf_fill_queries(out.data_ptr(), out.numel(), start, ins_seed, ins_start,
+                                  n_inserted, fresh_seed, member_seed, member_threshold,
+                                  stream_handle(stream)), "sbbf_fill_queries")
+    return out
+
+
+def count_bits(bits: torch.Tensor, n: int, stream=None) -> torch.Tensor:
+    """Device count of set bits among the first n bits of a packed result."""
+    cnt = torch.empty(1, dtype=torch.int64, device=bits.device)
+    check(lib().sbbf_count_bits(bits.data_ptr(), n, cnt.data_ptr(), stream_handle(stream)),
+          "sbbf_count_bits")
+    return cnt

@@ -88,3 +88,59 @@ def multi_filter_sizes(cfg: int, n_filters: int, lo: float, hi: float,
 def permutation(cfg: int, n: int, start: int = 0) -> np.ndarray:
     """A seeded permutation of 0..n-1 (argsort of a role-4 stream)."""
     return np.argsort(stream(cfg, ROLE_ORDER, n, start), kind="stable")
+
+
+def workload_queries(cfg: int, n_inserted: int, frac: float, prefix: int, start: int,
+                     n: int) -> np.ndarray:
+    """Lookup hashes start..start+n-1 of a single-filter workload: indices
+    below `prefix` are inserted hashes in order; the rest follow the query
+    recipe indexed from `prefix`, members being inserted hash
+    ((r & 0xffffffff) * n_inserted) >> 32 regenerated from the role-0 stream."""
+    j = np.arange(start, start + n, dtype=np.int64)
+    out = np.empty(n, np.uint64)
+    pre = j < prefix
+    if pre.any():
+        out[pre] = stream(cfg, ROLE_INSERT, int(pre.sum()), int(j[pre][0]))
+    rest = ~pre
+    if rest.any():
+        k0 = int(j[rest][0]) - prefix
+        m = int(rest.sum())
+        r = stream(cfg, ROLE_MEMBER, m, k0)
+        fresh = stream(cfg, ROLE_FRESH, m, k0)
+        member = (r >> np.uint64(32)) < np.uint64(member_threshold(frac))
+        with np.errstate(over="ignore"):
+            idx = ((r & np.uint64(0xFFFFFFFF)) * np.uint64(n_inserted)) >> np.uint64(32)
+        vals = fresh.copy()
+        if member.any():
+            seed = np.uint64(stream_seed(cfg, ROLE_INSERT))
+            vals[member] = _splitmix64_at(seed, idx[member])
+        out[rest] = vals
+    return out
+
+
+def sampled_queries(cfg: int, n_inserted: int, frac: float, prefix: int,
+                    idx: np.ndarray) -> np.ndarray:
+    """Lookup hashes at arbitrary indices idx (same recipe as workload_queries)."""
+    idx = np.asarray(idx, dtype=np.uint64)
+    out = np.empty(idx.size, np.uint64)
+    pre = idx < np.uint64(prefix)
+    out[pre] = _splitmix64_at(np.uint64(stream_seed(cfg, ROLE_INSERT)), idx[pre])
+    k = idx[~pre] - np.uint64(prefix)
+    r = _splitmix64_at(np.uint64(stream_seed(cfg, ROLE_MEMBER)), k)
+    fresh = _splitmix64_at(np.uint64(stream_seed(cfg, ROLE_FRESH)), k)
+    member = (r >> np.uint64(32)) < np.uint64(member_threshold(frac))
+    with np.errstate(over="ignore"):
+        midx = ((r & np.uint64(0xFFFFFFFF)) * np.uint64(n_inserted)) >> np.uint64(32)
+    vals = fresh
+    vals[member] = _splitmix64_at(np.uint64(stream_seed(cfg, ROLE_INSERT)), midx[member])
+    out[~pre] = vals
+    return out
+
+
+def _splitmix64_at(seed, i):
+    """splitmix64 outputs at arbitrary indices i (uint64 array)."""
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + (np.asarray(i, np.uint64) + np.uint64(1)) * GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))

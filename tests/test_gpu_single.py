@@ -1,0 +1,301 @@
+"""GPU parity: the CUDA single-filter path against the CPU oracle, bit for bit.
+
+Inputs are seeded splitmix64 streams (tests/sbbf_inputs.py or the library's
+device generator, itself checked against the host copy here).  Filter words
+and packed lookup results must be identical to the oracle's: the method is
+integer-only, so the tolerance is zero.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2101_01719_gb300 as sb
+from paper_2101_01719_gb300 import sbbf as abi
+from paper_2101_01719_gb300 import workloads as wl
+import sbbf_inputs as inp
+from gpu_util import bit_at, bits_np, dev, to_dev, u64_np
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_filter(B, keys):
+    f = oracle.new_filter(B)
+    oracle.insert(f, B, keys)
+    return f
+
+
+SIZES = [(1, 0), (1, 1), (3, 63), (7, 64), (4096, 65), (4096, 100_003), (32768, 1_000_001),
+         (1_000_003, 777_777), (2**22 + 5, 2_000_000)]
+
+
+@pytest.mark.parametrize("B,n", SIZES)
+def test_insert_and_find_parity(B, n):
+    keys = inp.stream(100 + B % 97, 0, n)
+    q = np.concatenate([inp.stream(100 + B % 97, 1, 3 * n + 17), keys[: n // 2]])
+    f = sb.Filter(B)
+    f.insert(to_dev(keys))
+    bits = f.find(to_dev(q))
+    ref = _oracle_filter(B, keys)
+    assert np.array_equal(f.to_numpy(), ref)
+    ref_bits = oracle.find(ref, B, q)
+    got = bits_np(bits)
+    assert got.size == ref_bits.size
+    assert np.array_equal(got, ref_bits)
+
+
+@pytest.mark.parametrize("offset", [1, 3])
+def test_unaligned_hash_pointers(offset):
+    """8-byte but not 16-byte aligned hash arrays take the scalar-load path."""
+    B, n = 5000, 100_001
+    keys = inp.stream(120, 0, n + offset)
+    q = inp.stream(120, 1, 50_001 + offset)
+    dk, dq = to_dev(keys), to_dev(q)
+    f = sb.Filter(B)
+    f.insert(dk[offset:])
+    bits = f.find(dq[offset:])
+    ref = _oracle_filter(B, keys[offset:])
+    assert np.array_equal(f.to_numpy(), ref)
+    assert np.array_equal(bits_np(bits), oracle.find(ref, B, q[offset:]))
+
+
+def test_ragged_tails_every_residue():
+    B = 257
+    keys = inp.stream(121, 0, 5000)
+    ref = _oracle_filter(B, keys)
+    f = sb.Filter(B)
+    f.insert(to_dev(keys))
+    assert np.array_equal(f.to_numpy(), ref)
+    q_all = inp.stream(121, 1, 300)
+    for n in list(range(0, 130)) + [191, 192, 193, 255, 256, 257]:
+        q = np.concatenate([q_all[: n // 2], keys[: n - n // 2]])
+        out = torch.full((sb.out_words(n) + 2,), -1, dtype=torch.int32, device=dev())
+        f.find(to_dev(q), out=out)
+        got = bits_np(out)
+        assert np.array_equal(got[: sb.out_words(n)], oracle.find(ref, B, q))
+        assert (got[sb.out_words(n):] == 0xFFFFFFFF).all()  # nothing written past the end
+
+
+def test_order_and_duplicates_do_not_matter():
+    B = 3001
+    keys = inp.stream(122, 0, 400_000)
+    perm = inp.permutation(122, keys.size)
+    dup = np.concatenate([keys[perm], keys[:100_000], keys[::7]])
+    f1, f2 = sb.Filter(B), sb.Filter(B)
+    f1.insert(to_dev(keys))
+    f2.insert(to_dev(dup))
+    assert np.array_equal(f1.to_numpy(), f2.to_numpy())
+    assert np.array_equal(f1.to_numpy(), _oracle_filter(B, keys))
+
+
+def test_concurrent_streams_insert():
+    B = 2048
+    keys = inp.stream(123, 0, 2_000_000)
+    dk = to_dev(keys)
+    f = sb.Filter(B)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    f.insert(dk[:1_000_000], stream=s1)
+    f.insert(dk[1_000_000:], stream=s2)
+    torch.cuda.synchronize()
+    assert np.array_equal(f.to_numpy(), _oracle_filter(B, keys))
+
+
+def test_union_and_clear():
+    B = 12345
+    a, b = inp.stream(124, 0, 200_000), inp.stream(124, 1, 150_000)
+    fa, fb = sb.Filter(B), sb.Filter(B)
+    fa.insert(to_dev(a))
+    fb.insert(to_dev(b))
+    fa.union_(fb)
+    ref = oracle.union(_oracle_filter(B, a), _oracle_filter(B, b))
+    assert np.array_equal(fa.to_numpy(), ref)
+    fa.union_(fa)  # self-union is a no-op
+    assert np.array_equal(fa.to_numpy(), ref)
+    with pytest.raises(sb.SbbfError):
+        fa.union_(sb.Filter(B + 1))
+    fa.clear()
+    assert not fa.to_numpy().any()
+
+
+def test_library_owned_filter_roundtrip():
+    """sbbf_create / sbbf_create_from_host / sbbf_copy_to_host through the C ABI."""
+    L = abi.lib()
+    B = 777
+    keys = inp.stream(125, 0, 30_000)
+    ref = _oracle_filter(B, keys)
+    h = ctypes.c_void_p()
+    assert L.sbbf_create(B, ctypes.byref(h)) == 0
+    try:
+        dk = to_dev(keys)
+        s = torch.cuda.current_stream().cuda_stream
+        assert L.sbbf_insert_hashes(h, dk.data_ptr(), keys.size, s) == 0
+        host = np.zeros(8 * B, np.uint32)
+        assert L.sbbf_copy_to_host(h, host.ctypes.data, host.nbytes, s) == 0
+        assert np.array_equal(host, ref)
+        small = np.zeros(8 * B - 1, np.uint32)
+        assert L.sbbf_copy_to_host(h, small.ctypes.data, small.nbytes, s) == abi.SBBF_EINVAL
+        assert L.sbbf_num_blocks(h) == B
+        ptr, nbytes = ctypes.c_void_p(), ctypes.c_size_t()
+        assert L.sbbf_device_words(h, ctypes.byref(ptr), ctypes.byref(nbytes)) == 0
+        assert nbytes.value == 32 * B and ptr.value % 256 == 0
+    finally:
+        assert L.sbbf_destroy(h) == 0
+    g = ctypes.c_void_p()
+    assert L.sbbf_create_from_host(ref.ctypes.data, B, ctypes.byref(g)) == 0
+    try:
+        q = np.concatenate([keys[:1000], inp.stream(125, 1, 5000)])
+        dq = to_dev(q)
+        out = torch.empty(sb.out_words(q.size), dtype=torch.int32, device=dev())
+        s = torch.cuda.current_stream().cuda_stream
+        assert L.sbbf_find_hashes(g, dq.data_ptr(), q.size, out.data_ptr(), s) == 0
+        assert np.array_equal(bits_np(out), oracle.find(ref, B, q))
+    finally:
+        L.sbbf_destroy(g)
+
+
+def test_argument_errors_on_device():
+    L = abi.lib()
+    f = sb.Filter(64)
+    keys = to_dev(inp.stream(126, 0, 100))
+    s = torch.cuda.current_stream().cuda_stream
+    assert L.sbbf_insert_hashes(f.handle, keys.data_ptr() + 4, 10, s) == abi.SBBF_EINVAL
+    out = torch.empty(4, dtype=torch.int32, device=dev())
+    assert L.sbbf_find_hashes(f.handle, keys.data_ptr(), 10, out.data_ptr() + 2, s) == \
+        abi.SBBF_EINVAL
+    assert L.sbbf_find_hashes(f.handle, keys.data_ptr(), 10, None, s) == abi.SBBF_EINVAL
+    assert L.sbbf_insert_hashes(f.handle, None, 0, s) == abi.SBBF_OK  # n == 0 no-op
+    with pytest.raises(TypeError):
+        f.insert(keys.to(torch.int32))
+
+
+def test_device_generators_match_host_copy():
+    n = 1_000_003
+    d = torch.empty(n, dtype=torch.int64, device=dev())
+    sb.fill_splitmix64(d, 1234567, 0)
+    got = u64_np(d)
+    assert int(got[0]) == 6457827717110365317  # published splitmix64 reference output
+    assert np.array_equal(got, inp.splitmix64(1234567, 0, n))
+    sb.fill_splitmix64(d[:1000], 99, 5_000_000_000)
+    assert np.array_equal(u64_np(d[:1000]), inp.splitmix64(99, 5_000_000_000, 1000))
+    for w in (wl.C0, wl.C1, wl.C2):
+        start = 99_000 if w is wl.C0 else 123_456_789
+        q = wl.gen_queries(w, start, 100_000)
+        exp = inp.workload_queries(w.cfg, w.n_insert, w.member_frac, w.member_prefix, start,
+                                   100_000)
+        assert np.array_equal(u64_np(q), exp)
+        ins = wl.gen_inserts(w, 77, 1000)
+        assert np.array_equal(u64_np(ins), inp.stream(w.cfg, 0, 1000, 77))
+
+
+def test_count_bits():
+    bits = to_dev(inp.stream(127, 0, 1000)).view(torch.int32)
+    words = bits_np(bits)
+    for n in (0, 1, 31, 33, 2000 - 5, 2000 * 32):
+        c = int(sb.count_bits(bits, n).item())
+        exp = sum(int(bit_at(words, k)) for k in range(n)) if n < 5000 else \
+            int(np.unpackbits(words.view(np.uint8)).sum())
+        assert c == exp
+
+
+def test_host_pipe_parity():
+    B = 32768
+    n = 3 * 4096 + 77
+    keys = inp.stream(128, 0, n)
+    q = np.concatenate([inp.stream(128, 1, n), keys])
+    hk = torch.from_numpy(keys.view(np.int64)).pin_memory()
+    hq = torch.from_numpy(q.view(np.int64)).pin_memory()
+    out = torch.zeros(sb.out_words(q.size), dtype=torch.int32).pin_memory()
+    pipe = sb.HostPipe(4096)
+    f = sb.Filter(B)
+    pipe.insert(f, hk)
+    pipe.find(f, hq, out)
+    ref = _oracle_filter(B, keys)
+    assert np.array_equal(f.to_numpy(), ref)
+    assert np.array_equal(out.numpy().view(np.uint32), oracle.find(ref, B, q))
+    # pageable host memory works too
+    out2 = torch.zeros_like(out, device="cpu")
+    pipe.find(f, torch.from_numpy(q.view(np.int64)), out2)
+    assert np.array_equal(out2.numpy(), out.numpy())
+
+
+def test_config_c0_full():
+    """100k hashes in 4096 blocks; look up the 100k (all hit) then 1M fresh;
+    bit-exact, and the measured FPR within the binomial interval."""
+    w = wl.C0
+    f = sb.Filter(w.num_blocks)
+    wl.build_filter(w, f)
+    q = wl.gen_queries(w, 0, w.n_lookup)
+    bits = bits_np(f.find(q))
+    keys = inp.stream(w.cfg, 0, w.n_insert)
+    ref = _oracle_filter(w.num_blocks, keys)
+    assert np.array_equal(f.to_numpy(), ref)
+    qh = u64_np(q)
+    ref_bits = oracle.find(ref, w.num_blocks, qh)
+    assert np.array_equal(bits, ref_bits)
+    hit = np.unpackbits(bits.view(np.uint8), bitorder="little")[: w.n_lookup].astype(bool)
+    assert hit[: w.n_insert].all()
+    fresh = ~np.isin(qh[w.n_insert:], keys)
+    fp = int(hit[w.n_insert:][fresh].sum())
+    p = oracle.fpr_poisson(w.n_insert / w.num_blocks)
+    nq = int(fresh.sum())
+    assert abs(fp / nq - p) <= 5 * np.sqrt(p * (1 - p) / nq) + 0.02 * p
+
+
+def _sampled_lookup_check(w, f, ref, q_dev, bits_dev, start, n, n_samples, seed):
+    """Compare n_samples random lookups of a chunk against the oracle, one by
+    one, regenerating each query on the host."""
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(n, size=min(n_samples, n), replace=False))
+    qs = inp.sampled_queries(w.cfg, w.n_insert, w.member_frac, w.member_prefix,
+                             (idx + start).astype(np.uint64))
+    got_q = u64_np(q_dev)[idx] if q_dev is not None else None
+    if got_q is not None:
+        assert np.array_equal(got_q, qs)
+    ref_bits = oracle.find(ref, w.num_blocks, qs)
+    exp = bit_at(ref_bits, np.arange(idx.size))
+    got = bit_at(bits_np(bits_dev), idx)
+    assert np.array_equal(got, exp)
+
+
+def test_config_c1_full_size():
+    """1M hashes into 32768 blocks; 256M lookups in one launch (the benchmark's
+    launch); words bit-exact; the first 8M lookups compared in full and 1M
+    sampled ones across the whole batch; members always hit."""
+    w = wl.C1
+    f = sb.Filter(w.num_blocks)
+    wl.build_filter(w, f)
+    keys = inp.stream(w.cfg, 0, w.n_insert)
+    ref = _oracle_filter(w.num_blocks, keys)
+    assert np.array_equal(f.to_numpy(), ref)
+    q = wl.gen_queries(w, 0, w.n_lookup)
+    bits = f.find(q)
+    head = 8 * 2**20
+    qh = u64_np(q[:head])
+    assert np.array_equal(qh, inp.workload_queries(w.cfg, w.n_insert, w.member_frac, 0, 0, head))
+    assert np.array_equal(bits_np(bits[: head // 32]), oracle.find(ref, w.num_blocks, qh))
+    _sampled_lookup_check(w, f, ref, None, bits, 0, w.n_lookup, 1 << 20, 5)
+    member = inp.query_is_member(w.cfg, head, w.member_frac)
+    hit = np.unpackbits(bits_np(bits[: head // 32]).view(np.uint8), bitorder="little").astype(bool)
+    assert hit[member].all()
+
+
+def test_config_c2_full_size():
+    """100M hashes into 4,194,304 blocks in 16M batches: words bit-exact; 1B
+    lookups: first 4M in full and 1M sampled."""
+    w = wl.C2
+    f = sb.Filter(w.num_blocks)
+    wl.build_filter(w, f)
+    keys = inp.stream(w.cfg, 0, w.n_insert)
+    ref = oracle.new_filter(w.num_blocks)
+    oracle.insert_mt(ref, w.num_blocks, keys, 8)
+    del keys
+    assert np.array_equal(f.to_numpy(), ref)
+    q = wl.gen_queries(w, 0, w.n_lookup)
+    bits = f.find(q)
+    head = 4 * 2**20
+    qh = u64_np(q[:head])
+    assert np.array_equal(bits_np(bits[: head // 32]), oracle.find(ref, w.num_blocks, qh))
+    _sampled_lookup_check(w, f, ref, None, bits, 0, w.n_lookup, 1 << 20, 6)
