@@ -37,6 +37,10 @@ DOMINANT_KERNEL = "find_kernel"
 LOOKUP_HBM_BYTES_L2_RESIDENT = 8.0 + 1.0 / 8.0
 # ... and with a filter larger than L2: plus one 32-byte block read.
 LOOKUP_HBM_BYTES_HBM_RESIDENT = 8.0 + 32.0 + 1.0 / 8.0
+# Insert: the hash, plus a 32-byte block read and written back when the
+# filter does not stay in L2.
+INSERT_HBM_BYTES_L2_RESIDENT = 8.0
+INSERT_HBM_BYTES_HBM_RESIDENT = 8.0 + 32.0 + 32.0
 
 
 def parse_args(argv=None):
@@ -200,9 +204,9 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     dist = init_dist(world, "nccl")
     w = wl.WORKLOADS[args.workload]
-    if w.n_insert > w.insert_batch:
-        raise SystemExit("bench workload must insert in one batch per step")
     stream = torch.cuda.current_stream()
+    batches = [(s, min(w.insert_batch, w.n_insert - s))
+               for s in range(0, w.n_insert, w.insert_batch)]
 
     # Inputs resident in HBM before timing; each rank takes its own slice of
     # the lookup stream (units sharded by rank, no data-path collective).
@@ -212,9 +216,13 @@ def run_ours(args):
     f = sb.Filter(w.num_blocks, device=dev)
     torch.cuda.synchronize()
 
+    def insert_all():
+        for s0, cnt in batches:
+            f.insert(ins[s0:s0 + cnt])
+
     def step():
         f.clear()
-        f.insert(ins)
+        insert_all()
         f.find(qry, out=out)
 
     for _ in range(max(args.warmup, 3)):
@@ -239,7 +247,7 @@ def run_ours(args):
         e[0].record(stream)
         f.clear()
         e[1].record(stream)
-        f.insert(ins)
+        insert_all()
         e[2].record(stream)
         f.find(qry, out=out)
         e[3].record(stream)
@@ -267,7 +275,7 @@ def run_ours(args):
         pipe = sb.HostPipe(1 << 24)
         f.clear()
         pipe.insert(f, h_ins)
-        pipe.find(f, h_q, h_out)  # warm-up
+        pipe.find(f, h_q, h_out)  # warm-up (one call per step: the pipe chunks internally)
         barrier(dist)
         torch.cuda.synchronize()
         a = time.perf_counter()
@@ -285,9 +293,11 @@ def run_ours(args):
 
     peak, peak_kind = measured_peaks()
     l2_bytes = props.L2_cache_size if hasattr(props, "L2_cache_size") else 126 * 2**20
-    per_key = (LOOKUP_HBM_BYTES_L2_RESIDENT if w.filter_bytes < l2_bytes / 2
-               else LOOKUP_HBM_BYTES_HBM_RESIDENT)
+    l2_resident = w.filter_bytes < l2_bytes / 2
+    per_key = LOOKUP_HBM_BYTES_L2_RESIDENT if l2_resident else LOOKUP_HBM_BYTES_HBM_RESIDENT
     achieved = per_key * w.n_lookup / (find_ms / 1e3) / 1e9
+    ins_per_key = INSERT_HBM_BYTES_L2_RESIDENT if l2_resident else INSERT_HBM_BYTES_HBM_RESIDENT
+    ins_achieved = ins_per_key * w.n_insert / (insert_ms / 1e3) / 1e9
     traffic = profiled_traffic(w.name)
     clocks = sampler.summary()
 
@@ -309,13 +319,16 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": DOMINANT_KERNEL,
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-                     "bytes_per_key": per_key, "traffic": traffic},
+                     "bytes_per_key": per_key, "traffic": traffic,
+                     "insert": {"achieved": round(ins_achieved, 1), "unit": "GB/s",
+                                "frac": round(ins_achieved / peak, 4),
+                                "bytes_per_key": ins_per_key}},
         "rows": {"insert_gkeys_s": round(w.n_insert / (insert_ms / 1e3) / 1e9, 3),
                  "lookup_gkeys_s": round(w.n_lookup / (find_ms / 1e3) / 1e9, 3),
                  "insert_ms": round(insert_ms, 5), "lookup_ms": round(find_ms, 5),
                  "lookup_hits": hits, "lookup_hit_frac": round(hits / w.n_lookup, 5)},
         "e2e": e2e,
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": (2 + len(batches)) * args.steps,
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:

@@ -183,10 +183,157 @@ sbbf_status sbbf_fill_queries(uint64_t *d_out, size_t n, uint64_t start,
                               uint64_t member_seed, uint64_t member_threshold,
                               sbbf_stream_t stream);
 
+/* Query streams for several filters in the segment layout: query k (global
+ * index, k in [0, n)) belongs to the filter t with d_q_offsets[t] <= k <
+ * d_q_offsets[t+1]; with r = output k of member_seed it is a member when
+ * (r >> 32) < member_threshold and filter t has inserted keys, namely output
+ * (d_ins_offsets[t] + (((r & 0xffffffff) * n_t) >> 32)) of ins_seed with
+ * n_t = d_ins_offsets[t+1] - d_ins_offsets[t]; otherwise output k of
+ * fresh_seed.  Offsets as for the segment form (n_filters + 1 entries each).
+ */
+sbbf_status sbbf_fill_segment_queries(uint64_t *d_out, size_t n,
+                                      const uint64_t *d_q_offsets,
+                                      const uint64_t *d_ins_offsets,
+                                      uint32_t n_filters, uint64_t ins_seed,
+                                      uint64_t fresh_seed, uint64_t member_seed,
+                                      uint64_t member_threshold,
+                                      sbbf_stream_t stream);
+
+/* d_ids[k] = the filter t with d_offsets[t] <= k < d_offsets[t+1], k < n. */
+sbbf_status sbbf_fill_segment_ids(uint32_t *d_ids, size_t n,
+                                  const uint64_t *d_offsets, uint32_t n_filters,
+                                  sbbf_stream_t stream);
+
 /* Number of set bits in the packed bitmask d_bits over its first n bits,
  * written to *d_count (uint64, device) -- used to count lookup hits. */
 sbbf_status sbbf_count_bits(const uint32_t *d_bits, size_t n,
                             unsigned long long *d_count, sbbf_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Many filters in one arena (batched form; not in the paper).
+ *
+ * Filter t of a set is the plain filter of num_blocks[t] blocks whose block 0
+ * is arena block base[t] = num_blocks[0] + ... + num_blocks[t-1]; each filter
+ * keeps the paper's block selection (with its own num_blocks) and mask, so a
+ * filter's words equal those of a single filter given the same hashes.
+ *
+ * Keys name their filter in one of two forms:
+ *   tagged:   d_ids[k] is key k's filter (uint32); a key whose id is
+ *             >= n_filters is skipped by inserts, answers 0 in lookups and is
+ *             counted (see sbbf_multi_invalid_count); it never faults;
+ *   segments: keys are grouped by filter: filter t's keys are
+ *             d_hashes[d_offsets[t] .. d_offsets[t+1]) with d_offsets a device
+ *             array of n_filters + 1 non-decreasing uint64, d_offsets[0] = 0
+ *             and d_offsets[n_filters] = n.  Offsets that break this contract
+ *             assign keys to unspecified filters of the set but never access
+ *             memory outside the arena.
+ * Lookup answers are packed by key index k over the whole batch, exactly as
+ * for a single filter.  Each batch is one persistent launch whatever the
+ * number of filters.
+ * ---------------------------------------------------------------------- */
+
+typedef struct sbbf_multi_set sbbf_multi_t;
+
+enum { SBBF_OP_INSERT = 0, SBBF_OP_FIND = 1 };
+enum { SBBF_FORM_SEGMENTS = 0, SBBF_FORM_TAGGED = 1 };
+
+/* Create n_filters empty filters with h_num_blocks[t] >= 1 blocks each
+ * (host array) in one library-owned, zero-filled device arena (synchronous).
+ * Errors: SBBF_EINVAL (NULL, n_filters == 0, a zero size), SBBF_ENOMEM,
+ * SBBF_ECUDA. */
+sbbf_status sbbf_multi_create(const uint32_t *h_num_blocks, uint32_t n_filters,
+                              sbbf_multi_t **out);
+sbbf_status sbbf_multi_destroy(sbbf_multi_t *m);
+uint32_t sbbf_multi_num_filters(const sbbf_multi_t *m);
+
+/* First arena block and size of filter id.  Errors: SBBF_EINVAL. */
+sbbf_status sbbf_multi_filter_info(const sbbf_multi_t *m, uint32_t id,
+                                   uint64_t *base_block, uint32_t *num_blocks);
+
+/* Device address and byte size of the whole arena. */
+sbbf_status sbbf_multi_device_words(const sbbf_multi_t *m, uint32_t **d_words,
+                                    size_t *bytes);
+
+sbbf_status sbbf_multi_clear(sbbf_multi_t *m, sbbf_stream_t stream);
+
+/* Copy the whole arena (total blocks * 32 bytes) to host memory h_words of
+ * at least that many bytes; synchronises the stream.  Errors: SBBF_EINVAL,
+ * SBBF_ECUDA. */
+sbbf_status sbbf_multi_copy_to_host(const sbbf_multi_t *m, uint32_t *h_words,
+                                    size_t bytes, sbbf_stream_t stream);
+
+/* Tagged form.  d_hashes 8-byte aligned, d_ids 4-byte aligned, n keys. */
+sbbf_status sbbf_multi_insert(sbbf_multi_t *m, const uint64_t *d_hashes,
+                              const uint32_t *d_ids, size_t n,
+                              sbbf_stream_t stream);
+sbbf_status sbbf_multi_find(const sbbf_multi_t *m, const uint64_t *d_hashes,
+                            const uint32_t *d_ids, size_t n,
+                            uint32_t *d_out_bits, sbbf_stream_t stream);
+
+/* Segment form (d_offsets 8-byte aligned, n = d_offsets[n_filters]). */
+sbbf_status sbbf_multi_insert_segments(sbbf_multi_t *m, const uint64_t *d_hashes,
+                                       const uint64_t *d_offsets, size_t n,
+                                       sbbf_stream_t stream);
+sbbf_status sbbf_multi_find_segments(const sbbf_multi_t *m,
+                                     const uint64_t *d_hashes,
+                                     const uint64_t *d_offsets, size_t n,
+                                     uint32_t *d_out_bits, sbbf_stream_t stream);
+
+/* Per-filter form: one plain single-filter launch per non-empty filter, with
+ * HOST offsets h_offsets[0..n_filters] (same contract as d_offsets).  The
+ * same results as the segment form; for lookups every h_offsets[t] must be a
+ * multiple of 32 so that each filter's answers start a fresh output word
+ * (SBBF_EINVAL otherwise).  This is the launch-per-filter baseline that the
+ * batched form is measured against. */
+sbbf_status sbbf_multi_insert_each(sbbf_multi_t *m, const uint64_t *d_hashes,
+                                   const uint64_t *h_offsets,
+                                   sbbf_stream_t stream);
+sbbf_status sbbf_multi_find_each(const sbbf_multi_t *m, const uint64_t *d_hashes,
+                                 const uint64_t *h_offsets, uint32_t *d_out_bits,
+                                 sbbf_stream_t stream);
+
+/* Number of tagged keys with an invalid id seen since the last call; resets
+ * the count.  Synchronises the stream.  Errors: SBBF_EINVAL, SBBF_ECUDA. */
+sbbf_status sbbf_multi_invalid_count(sbbf_multi_t *m, uint64_t *count,
+                                     sbbf_stream_t stream);
+
+/* Launch shape used for (op, form): CTA size (128/256/512), lanes per key
+ * (1 or 8) and loads in flight per warp (1/2/4).  Shapes never change
+ * results, only speed. */
+sbbf_status sbbf_multi_get_tuning(const sbbf_multi_t *m, int op, int form,
+                                  int *threads, int *lanes, int *unroll);
+sbbf_status sbbf_multi_set_tuning(sbbf_multi_t *m, int op, int form,
+                                  int threads, int lanes, int unroll);
+
+/* Autotune (op, form) on a prefix (at most 2^24 keys) of a real batch:
+ * every candidate shape runs on the sample, its result (lookup bits, or the
+ * arena words it inserts into a scratch copy of the touched filters) is
+ * compared with the default shape's result and discarded on any difference;
+ * the fastest verified shape is kept for the set and cached per (GPU, op,
+ * form, size class).  The set's filters are not modified.  d_offsets_or_ids
+ * is the batch's d_offsets (segments) or d_ids (tagged).  *best_ms (may be
+ * NULL) receives the winner's sample time, or -1 when the cache answered.
+ * Synchronous.  Errors: SBBF_EINVAL, SBBF_ENOMEM (scratch), SBBF_ECUDA. */
+sbbf_status sbbf_multi_tune(sbbf_multi_t *m, int op, int form,
+                            const uint64_t *d_hashes,
+                            const void *d_offsets_or_ids, size_t n,
+                            sbbf_stream_t stream, float *best_ms);
+
+/* A CUDA graph holding one batched segment-form insert followed by one
+ * batched segment-form lookup on the set, with the set's current tuned
+ * shapes (tune before creating it).  Each launch updates the two kernels'
+ * arguments in the instantiated graph and launches it on stream: inserts of
+ * the batch land before its lookups run.  Either part may be empty
+ * (n_ins == 0 or n_q == 0). */
+typedef struct sbbf_multi_graph sbbf_multi_graph_t;
+sbbf_status sbbf_multi_graph_create(sbbf_multi_t *m, sbbf_multi_graph_t **out);
+sbbf_status sbbf_multi_graph_destroy(sbbf_multi_graph_t *g);
+sbbf_status sbbf_multi_graph_launch(sbbf_multi_graph_t *g,
+                                    const uint64_t *d_ins,
+                                    const uint64_t *d_ins_offsets, size_t n_ins,
+                                    const uint64_t *d_q,
+                                    const uint64_t *d_q_offsets, size_t n_q,
+                                    uint32_t *d_out_bits, sbbf_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -5,12 +5,19 @@ The compute runs in ``libsbbf.so`` (hand-written CUDA behind the C ABI in
 ``include/sbbf.h``); this package is its thin Python binding.
 """
 from .sbbf import (  # noqa: F401
+    FORM_SEGMENTS,
+    FORM_TAGGED,
+    OP_FIND,
+    OP_INSERT,
     Filter,
     HostPipe,
+    MultiFilter,
     SbbfError,
     check,
     count_bits,
     fill_queries,
+    fill_segment_ids,
+    fill_segment_queries,
     fill_splitmix64,
     lib,
     out_words,

@@ -103,10 +103,30 @@ __device__ __forceinline__ void load_block(const uint32_t* p, uint64_t pol,
       : "l"(p), "l"(pol));
 }
 
+// One 32-bit lane word of a block.
+__device__ __forceinline__ uint32_t load_word(const uint32_t* p, uint64_t pol) {
+  uint32_t w;
+  asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(w) : "l"(p), "l"(pol));
+  return w;
+}
+
 // Fire-and-forget atomic OR performed at L2.
 __device__ __forceinline__ void red_or(uint32_t* p, uint32_t v) {
   asm volatile("red.relaxed.gpu.global.or.b32 [%0], %1;" ::"l"(p), "r"(v)
                : "memory");
+}
+
+__device__ __forceinline__ void red_or64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.relaxed.gpu.global.or.b64 [%0], %1;" ::"l"(p), "l"(v)
+               : "memory");
+}
+
+// Mask bits of two adjacent lanes packed little-endian into one 64-bit word
+// (the lower lane in the low half).
+__device__ __forceinline__ unsigned long long mask_pair(uint32_t x, uint32_t s_lo,
+                                                        uint32_t s_hi) {
+  return (static_cast<unsigned long long>(1u << bit_index(x, s_hi)) << 32) |
+         (1u << bit_index(x, s_lo));
 }
 
 __device__ __forceinline__ void store_stream(uint32_t* p, uint32_t v) {

@@ -47,6 +47,46 @@ __global__ void fill_queries_kernel(uint64_t* __restrict__ out, uint64_t n, uint
   }
 }
 
+// Last t with offsets[t] <= k (offsets[0] = 0 <= k < offsets[n_filters]).
+__device__ __forceinline__ uint32_t segment_of(const uint64_t* offsets, uint32_t n_filters,
+                                               uint64_t k) {
+  uint32_t lo = 0, hi = n_filters;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (offsets[mid] <= k) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void fill_segment_queries_kernel(uint64_t* __restrict__ out, uint64_t n,
+                                            const uint64_t* __restrict__ q_off,
+                                            const uint64_t* __restrict__ ins_off,
+                                            uint32_t n_filters, uint64_t ins_seed,
+                                            uint64_t fresh_seed, uint64_t member_seed,
+                                            uint64_t threshold) {
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t k = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < n;
+       k += stride) {
+    const uint32_t t = segment_of(q_off, n_filters, k);
+    const uint64_t r = splitmix64_at(member_seed, k);
+    const uint64_t s0 = ins_off[t], n_t = ins_off[t + 1] - s0;
+    uint64_t q;
+    if ((r >> 32) < threshold && n_t > 0)
+      q = splitmix64_at(ins_seed, s0 + (((r & 0xFFFFFFFFull) * n_t) >> 32));
+    else
+      q = splitmix64_at(fresh_seed, k);
+    out[k] = q;
+  }
+}
+
+__global__ void fill_segment_ids_kernel(uint32_t* __restrict__ ids, uint64_t n,
+                                        const uint64_t* __restrict__ off, uint32_t n_filters) {
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t k = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < n;
+       k += stride)
+    ids[k] = segment_of(off, n_filters, k);
+}
+
 __global__ void count_bits_kernel(const uint32_t* __restrict__ bits, uint64_t n,
                                   unsigned long long* __restrict__ count) {
   const uint64_t n_words = (n + 31) / 32;
@@ -89,6 +129,30 @@ sbbf_status sbbf_fill_queries(uint64_t* d_out, size_t n, uint64_t start, uint64_
   fill_queries_kernel<<<grid_for(n, 256, occ), 256, 0, stream>>>(
       d_out, n, start, ins_seed, ins_start, n_inserted, fresh_seed, member_seed,
       member_threshold);
+  return launch_status();
+}
+
+sbbf_status sbbf_fill_segment_queries(uint64_t* d_out, size_t n, const uint64_t* d_q_offsets,
+                                      const uint64_t* d_ins_offsets, uint32_t n_filters,
+                                      uint64_t ins_seed, uint64_t fresh_seed,
+                                      uint64_t member_seed, uint64_t member_threshold,
+                                      sbbf_stream_t stream) {
+  if (n == 0) return SBBF_OK;
+  if (!d_out || !d_q_offsets || !d_ins_offsets || n_filters == 0) return SBBF_EINVAL;
+  static int occ = occupancy(fill_segment_queries_kernel, 256);
+  fill_segment_queries_kernel<<<grid_for(n, 256, occ), 256, 0, stream>>>(
+      d_out, n, d_q_offsets, d_ins_offsets, n_filters, ins_seed, fresh_seed, member_seed,
+      member_threshold);
+  return launch_status();
+}
+
+sbbf_status sbbf_fill_segment_ids(uint32_t* d_ids, size_t n, const uint64_t* d_offsets,
+                                  uint32_t n_filters, sbbf_stream_t stream) {
+  if (n == 0) return SBBF_OK;
+  if (!d_ids || !d_offsets || n_filters == 0) return SBBF_EINVAL;
+  static int occ = occupancy(fill_segment_ids_kernel, 256);
+  fill_segment_ids_kernel<<<grid_for(n, 256, occ), 256, 0, stream>>>(d_ids, n, d_offsets,
+                                                                     n_filters);
   return launch_status();
 }
 

@@ -1,0 +1,278 @@
+// Insert and lookup kernels, generic over how a key finds its block.
+//
+// A "resolver" maps key k with hash h to a global block index in the word
+// arena (or kNoBlock64 to skip the key):
+//   OneFilter    one filter of num_blocks blocks at block 0 (appendix
+//                block_index);
+//   Segments     several filters in one arena; keys grouped by filter,
+//                filter t owning keys [offsets[t], offsets[t+1]);
+//   Tagged       several filters; key k names its filter in ids[k].
+// For several filters, filter t is the plain filter of dir[t].num_blocks
+// blocks whose block 0 is arena block dir[t].base, so every filter keeps the
+// paper's block selection and mask.
+//
+// Warp work unit: 64 consecutive keys, two per lane (one 16-byte load when
+// the hash array is 16-byte aligned).
+//
+// Insert, 8 lanes per key (kLanes8): in 16 rounds each group of eight lanes
+// takes one key; lane j ORs lane j's mask bit into word j of the block with
+// red.or.b32, so one warp instruction covers four whole 32-byte sectors.
+// Insert, 1 lane per key: each lane issues four red.or.b64 for its own key.
+//
+// Lookup, 1 lane per key: one 256-bit load per key, all eight lanes tested
+// in registers, 64 answers packed by two OR reductions; U 64-key groups in
+// flight per warp.  Lookup, 8 lanes per key: lane j loads word j of the
+// block; a ballot gathers the eight tests.
+#pragma once
+
+#include <cstdint>
+
+#include "sbbf_device.cuh"
+
+namespace sbbf {
+
+constexpr uint64_t kNoBlock64 = ~0ull;
+constexpr int kMaxThreads = 512;
+
+// Directory entry of one filter in an arena (16 bytes).
+struct FilterRef {
+  uint64_t base;        // first block of the filter in the arena
+  uint32_t num_blocks;  // blocks of the filter (>= 1)
+  uint32_t reserved;
+};
+
+__device__ __forceinline__ FilterRef load_ref(const FilterRef* dir, uint32_t t) {
+  const uint4 v = __ldg(reinterpret_cast<const uint4*>(dir) + t);
+  FilterRef r;
+  r.base = (static_cast<uint64_t>(v.y) << 32) | v.x;
+  r.num_blocks = v.z;
+  r.reserved = v.w;
+  return r;
+}
+
+struct OneFilter {
+  uint32_t num_blocks;
+  __device__ __forceinline__ void begin_chunk(uint64_t) {}
+  __device__ __forceinline__ uint64_t block(uint64_t, uint64_t h) const {
+    return block_of(h, num_blocks);
+  }
+  __device__ __forceinline__ void finish() const {}
+};
+
+struct Segments {
+  const uint64_t* offsets;  // n_filters + 1 non-decreasing key offsets
+  const FilterRef* dir;
+  uint32_t n_filters;
+  uint32_t t0;              // filter of the current chunk's first key
+
+  // Last t with offsets[t] <= k (k < offsets[n_filters]).
+  __device__ __forceinline__ void begin_chunk(uint64_t k) {
+    uint32_t lo = 0, hi = n_filters;  // offsets[lo] <= k < offsets[hi]
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (__ldg(offsets + mid) <= k) lo = mid; else hi = mid;
+    }
+    t0 = lo;
+  }
+  __device__ __forceinline__ uint64_t block(uint64_t k, uint64_t h) const {
+    uint32_t t = t0;
+    while (t + 1 < n_filters && __ldg(offsets + t + 1) <= k) ++t;  // segment boundaries
+    const FilterRef r = load_ref(dir, t);
+    return r.base + block_of(h, r.num_blocks);
+  }
+  __device__ __forceinline__ void finish() const {}
+};
+
+struct Tagged {
+  const uint32_t* ids;
+  const FilterRef* dir;
+  uint32_t n_filters;
+  unsigned long long* invalid;  // device count of keys whose id >= n_filters
+  uint32_t bad;
+
+  __device__ __forceinline__ void begin_chunk(uint64_t) {}
+  __device__ __forceinline__ uint64_t block(uint64_t k, uint64_t h) {
+    const uint32_t t = __ldg(ids + k);
+    if (t >= n_filters) {
+      ++bad;
+      return kNoBlock64;
+    }
+    const FilterRef r = load_ref(dir, t);
+    return r.base + block_of(h, r.num_blocks);
+  }
+  __device__ __forceinline__ void finish() const {
+    unsigned long long c = bad;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+    if (lane_id() == 0 && c) atomicAdd(invalid, c);
+  }
+};
+
+// Two consecutive hashes k, k+1 (zero past n).
+__device__ __forceinline__ void load_pair(const uint64_t* __restrict__ hashes, uint64_t k,
+                                          uint64_t n, bool vec, uint64_t pol, uint64_t& h0,
+                                          uint64_t& h1) {
+  if (vec && k + 1 < n) {
+    load_keys2(hashes + k, pol, h0, h1);
+  } else {
+    h0 = k < n ? load_key1(hashes + k, pol) : 0;
+    h1 = k + 1 < n ? load_key1(hashes + k + 1, pol) : 0;
+  }
+}
+
+__device__ __forceinline__ void warp_span(uint64_t& warp, uint64_t& n_warps) {
+  warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  n_warps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+}
+
+// ---- insert ----------------------------------------------------------------
+
+template <class R, bool kLanes8>
+__global__ void __launch_bounds__(kMaxThreads)
+    insert_kernel(uint32_t* __restrict__ words, R res, const uint64_t* __restrict__ hashes,
+                  uint64_t n) {
+  const unsigned lane = lane_id();
+  uint64_t warp, n_warps;
+  warp_span(warp, n_warps);
+  const uint64_t n_groups = (n + 63) >> 6;
+  const uint64_t pol = policy_evict_first();
+  const bool vec = (reinterpret_cast<uintptr_t>(hashes) & 15) == 0;
+  const uint32_t seed = lane_seed(lane & 7);
+  uint32_t* const word_j = words + (lane & 7);
+  const int group_base = static_cast<int>(lane & ~7u);
+
+  for (uint64_t g = warp; g < n_groups; g += n_warps) {
+    const uint64_t k = g * 64 + 2 * lane;
+    uint64_t h0, h1;
+    load_pair(hashes, k, n, vec, pol, h0, h1);
+    res.begin_chunk(g * 64);
+    const uint64_t b0 = k < n ? res.block(k, h0) : kNoBlock64;
+    const uint64_t b1 = k + 1 < n ? res.block(k + 1, h1) : kNoBlock64;
+    if (kLanes8) {
+      const uint32_t x0 = static_cast<uint32_t>(h0), x1 = static_cast<uint32_t>(h1);
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const int src = group_base + (r >> 1);
+        const uint32_t x = __shfl_sync(0xFFFFFFFFu, (r & 1) ? x1 : x0, src);
+        const uint64_t b = __shfl_sync(0xFFFFFFFFu, (r & 1) ? b1 : b0, src);
+        if (b != kNoBlock64) red_or(word_j + 8ull * b, 1u << bit_index(x, seed));
+      }
+    } else {
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const uint64_t b = s ? b1 : b0;
+        const uint32_t x = static_cast<uint32_t>(s ? h1 : h0);
+        if (b == kNoBlock64) continue;
+        unsigned long long* p = reinterpret_cast<unsigned long long*>(words + 8ull * b);
+        red_or64(p + 0, mask_pair(x, SBBF_SEED0, SBBF_SEED1));
+        red_or64(p + 1, mask_pair(x, SBBF_SEED2, SBBF_SEED3));
+        red_or64(p + 2, mask_pair(x, SBBF_SEED4, SBBF_SEED5));
+        red_or64(p + 3, mask_pair(x, SBBF_SEED6, SBBF_SEED7));
+      }
+    }
+  }
+  res.finish();
+}
+
+// ---- lookup ----------------------------------------------------------------
+
+template <class R, bool kLanes8, int U>
+__global__ void __launch_bounds__(kMaxThreads)
+    find_kernel(const uint32_t* __restrict__ words, R res, const uint64_t* __restrict__ hashes,
+                uint64_t n, uint32_t* __restrict__ out) {
+  const unsigned lane = lane_id();
+  uint64_t warp, n_warps;
+  warp_span(warp, n_warps);
+  const uint64_t n_groups = (n + 63) >> 6;
+  const uint64_t n_out = (n + 31) >> 5;
+  const uint64_t pk = policy_evict_first();
+  const uint64_t pf = policy_evict_last();
+  const bool vec = (reinterpret_cast<uintptr_t>(hashes) & 15) == 0;
+
+  if (!kLanes8) {
+    for (uint64_t g0 = warp * U; g0 < n_groups; g0 += n_warps * U) {
+      uint64_t h[U][2], b[U][2];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        load_pair(hashes, (g0 + u) * 64 + 2 * lane, n, vec, pk, h[u][0], h[u][1]);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        res.begin_chunk((g0 + u) * 64 < n ? (g0 + u) * 64 : 0);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const uint64_t k = (g0 + u) * 64 + 2 * lane + s;
+          b[u][s] = k < n ? res.block(k, h[u][s]) : kNoBlock64;
+        }
+      }
+      uint32_t w[U][2][8];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          if (b[u][s] != kNoBlock64) {
+            load_block(words + 8ull * b[u][s], pf, w[u][s]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) w[u][s][i] = 0;
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint32_t r0 = block_has(w[u][0], static_cast<uint32_t>(h[u][0]));
+        const uint32_t r1 = block_has(w[u][1], static_cast<uint32_t>(h[u][1]));
+        const uint32_t v = (r0 | (r1 << 1)) << (2 * (lane & 15));
+        const uint32_t lo = __reduce_or_sync(0xFFFFFFFFu, lane < 16 ? v : 0u);
+        const uint32_t hi = __reduce_or_sync(0xFFFFFFFFu, lane >= 16 ? v : 0u);
+        const uint64_t word = 2 * (g0 + u);
+        if (lane == 0 && word < n_out) store_stream(out + word, lo);
+        if (lane == 1 && word + 1 < n_out) store_stream(out + word + 1, hi);
+      }
+    }
+  } else {
+    const uint32_t seed = lane_seed(lane & 7);
+    const unsigned j = lane & 7;
+    const unsigned grp = lane >> 3;
+    for (uint64_t g = warp; g < n_groups; g += n_warps) {
+      const uint64_t k = g * 64 + 2 * lane;
+      uint64_t h0, h1;
+      load_pair(hashes, k, n, vec, pk, h0, h1);
+      res.begin_chunk(g * 64);
+      const uint64_t b0 = k < n ? res.block(k, h0) : kNoBlock64;
+      const uint64_t b1 = k + 1 < n ? res.block(k + 1, h1) : kNoBlock64;
+      uint32_t lo = 0, hi = 0;
+#pragma unroll
+      for (int rb = 0; rb < 16; rb += U) {
+        uint32_t wv[U], xv[U];
+        bool ok[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {  // U rounds of loads in flight
+          const int r = rb + u;
+          const int src = static_cast<int>(grp * 8) + (r >> 1);
+          xv[u] = __shfl_sync(0xFFFFFFFFu, static_cast<uint32_t>((r & 1) ? h1 : h0), src);
+          const uint64_t bb = __shfl_sync(0xFFFFFFFFu, (r & 1) ? b1 : b0, src);
+          ok[u] = bb != kNoBlock64;
+          wv[u] = ok[u] ? load_word(words + 8ull * bb + j, pf) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int r = rb + u;
+          const bool bit = ok[u] && ((wv[u] >> bit_index(xv[u], seed)) & 1u);
+          const uint32_t vote = __ballot_sync(0xFFFFFFFFu, bit);
+          // key 16*grp + r: group 0/1 -> word 0 bits r / 16+r, group 2/3 -> word 1
+          const uint32_t h_g0 = (vote & 0x000000FFu) == 0x000000FFu;
+          const uint32_t h_g1 = (vote & 0x0000FF00u) == 0x0000FF00u;
+          const uint32_t h_g2 = (vote & 0x00FF0000u) == 0x00FF0000u;
+          const uint32_t h_g3 = (vote & 0xFF000000u) == 0xFF000000u;
+          lo |= (h_g0 << r) | (h_g1 << (16 + r));
+          hi |= (h_g2 << r) | (h_g3 << (16 + r));
+        }
+      }
+      const uint64_t word = 2 * g;
+      if (lane == 0 && word < n_out) store_stream(out + word, lo);
+      if (lane == 1 && word + 1 < n_out) store_stream(out + word + 1, hi);
+    }
+  }
+  res.finish();
+}
+
+}  // namespace sbbf

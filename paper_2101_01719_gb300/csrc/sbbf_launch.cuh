@@ -1,0 +1,79 @@
+// Host-side launch of the generic insert / lookup kernels with a tunable
+// shape: CTA size, lanes per key (1 or 8) and 64-key groups in flight per
+// warp (lookups, 1 lane per key) or rounds in flight (8 lanes per key).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <unordered_map>
+
+#include "sbbf_host.cuh"
+#include "sbbf_kernels.cuh"
+
+namespace sbbf {
+
+struct Tuning {
+  int threads;  // CTA size: 128, 256 or 512
+  int lanes;    // lanes per key: 1 or 8
+  int unroll;   // lookups: groups (lanes 1) or rounds (lanes 8) in flight: 1, 2, 4
+};
+
+constexpr Tuning kDefaultFind = {256, 1, 2};
+constexpr Tuning kDefaultInsert = {256, 8, 1};
+
+inline bool tuning_valid(const Tuning& t) {
+  return (t.threads == 128 || t.threads == 256 || t.threads == 512) &&
+         (t.lanes == 1 || t.lanes == 8) && (t.unroll == 1 || t.unroll == 2 || t.unroll == 4);
+}
+
+// Resident CTAs per SM for (kernel, CTA size), cached.
+inline int cached_occupancy(const void* func, int threads) {
+  static std::mutex mu;
+  static std::unordered_map<uint64_t, int> cache;
+  const uint64_t key = reinterpret_cast<uintptr_t>(func) ^ (static_cast<uint64_t>(threads) << 52);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, func, threads, 0) != cudaSuccess || n < 1)
+    n = 1;
+  cache[key] = n;
+  return n;
+}
+
+template <class R>
+sbbf_status launch_insert_t(const Tuning& t, uint32_t* words, R res, const uint64_t* hashes,
+                            uint64_t n, cudaStream_t s) {
+  if (n == 0) return SBBF_OK;
+  void (*k)(uint32_t*, R, const uint64_t*, uint64_t) =
+      t.lanes == 8 ? insert_kernel<R, true> : insert_kernel<R, false>;
+  const uint64_t groups = (n + 63) / 64;
+  const unsigned grid =
+      grid_for(groups, t.threads / 32, cached_occupancy(reinterpret_cast<const void*>(k), t.threads));
+  k<<<grid, t.threads, 0, s>>>(words, res, hashes, n);
+  return launch_status();
+}
+
+template <class R>
+sbbf_status launch_find_t(const Tuning& t, const uint32_t* words, R res, const uint64_t* hashes,
+                          uint64_t n, uint32_t* out, cudaStream_t s) {
+  if (n == 0) return SBBF_OK;
+  void (*k)(const uint32_t*, R, const uint64_t*, uint64_t, uint32_t*) = nullptr;
+  if (t.lanes == 8) {
+    k = t.unroll == 1 ? find_kernel<R, true, 1>
+        : t.unroll == 2 ? find_kernel<R, true, 2> : find_kernel<R, true, 4>;
+  } else {
+    k = t.unroll == 1 ? find_kernel<R, false, 1>
+        : t.unroll == 2 ? find_kernel<R, false, 2> : find_kernel<R, false, 4>;
+  }
+  const uint64_t groups = (n + 63) / 64;
+  const uint64_t per_warp = t.lanes == 8 ? 1 : static_cast<uint64_t>(t.unroll);
+  const unsigned grid = grid_for(groups, (t.threads / 32) * per_warp,
+                                 cached_occupancy(reinterpret_cast<const void*>(k), t.threads));
+  k<<<grid, t.threads, 0, s>>>(words, res, hashes, n, out);
+  return launch_status();
+}
+
+}  // namespace sbbf

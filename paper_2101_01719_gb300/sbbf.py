@@ -53,7 +53,33 @@ SIGNATURES = {
     "sbbf_fill_splitmix64": (_int, [_P, _sz, _u64, _u64, _P]),
     "sbbf_fill_queries": (_int, [_P, _sz, _u64, _u64, _u64, _u64, _u64, _u64, _u64, _P]),
     "sbbf_count_bits": (_int, [_P, _sz, _P, _P]),
+    "sbbf_fill_segment_queries": (_int, [_P, _sz, _P, _P, _u32, _u64, _u64, _u64, _u64, _P]),
+    "sbbf_fill_segment_ids": (_int, [_P, _sz, _P, _u32, _P]),
+    "sbbf_multi_create": (_int, [_P, _u32, _c.POINTER(_P)]),
+    "sbbf_multi_destroy": (_int, [_P]),
+    "sbbf_multi_num_filters": (_u32, [_P]),
+    "sbbf_multi_filter_info": (_int, [_P, _u32, _c.POINTER(_u64), _c.POINTER(_u32)]),
+    "sbbf_multi_device_words": (_int, [_P, _c.POINTER(_P), _c.POINTER(_sz)]),
+    "sbbf_multi_clear": (_int, [_P, _P]),
+    "sbbf_multi_copy_to_host": (_int, [_P, _P, _sz, _P]),
+    "sbbf_multi_insert": (_int, [_P, _P, _P, _sz, _P]),
+    "sbbf_multi_find": (_int, [_P, _P, _P, _sz, _P, _P]),
+    "sbbf_multi_insert_segments": (_int, [_P, _P, _P, _sz, _P]),
+    "sbbf_multi_find_segments": (_int, [_P, _P, _P, _sz, _P, _P]),
+    "sbbf_multi_insert_each": (_int, [_P, _P, _P, _P]),
+    "sbbf_multi_find_each": (_int, [_P, _P, _P, _P, _P]),
+    "sbbf_multi_invalid_count": (_int, [_P, _c.POINTER(_u64), _P]),
+    "sbbf_multi_get_tuning": (_int, [_P, _int, _int, _c.POINTER(_int), _c.POINTER(_int),
+                                     _c.POINTER(_int)]),
+    "sbbf_multi_set_tuning": (_int, [_P, _int, _int, _int, _int, _int]),
+    "sbbf_multi_tune": (_int, [_P, _int, _int, _P, _P, _sz, _P, _c.POINTER(_c.c_float)]),
+    "sbbf_multi_graph_create": (_int, [_P, _c.POINTER(_P)]),
+    "sbbf_multi_graph_destroy": (_int, [_P]),
+    "sbbf_multi_graph_launch": (_int, [_P, _P, _P, _sz, _P, _P, _sz, _P, _P]),
 }
+
+OP_INSERT, OP_FIND = 0, 1
+FORM_SEGMENTS, FORM_TAGGED = 0, 1
 
 
 class SbbfError(RuntimeError):
@@ -234,3 +260,181 @@ def count_bits(bits: torch.Tensor, n: int, stream=None) -> torch.Tensor:
     check(lib().sbbf_count_bits(bits.data_ptr(), n, cnt.data_ptr(), stream_handle(stream)),
           "sbbf_count_bits")
     return cnt
+
+
+def fill_segment_queries(out: torch.Tensor, q_offsets: torch.Tensor, ins_offsets: torch.Tensor,
+                         ins_seed: int, fresh_seed: int, member_seed: int,
+                         member_threshold: int, stream=None):
+    """Query streams of several filters in the segment layout (see sbbf.h)."""
+    assert out.is_cuda and out.element_size() == 8 and q_offsets.dtype == torch.int64
+    n_filters = q_offsets.numel() - 1
+    check(lib().sbbf_fill_segment_queries(out.data_ptr(), out.numel(), q_offsets.data_ptr(),
+                                          ins_offsets.data_ptr(), n_filters, ins_seed, fresh_seed,
+                                          member_seed, member_threshold, stream_handle(stream)),
+          "sbbf_fill_segment_queries")
+    return out
+
+
+def fill_segment_ids(out: torch.Tensor, offsets: torch.Tensor, stream=None):
+    """out[k] = filter of key k under the segment offsets (uint32 as int32)."""
+    assert out.is_cuda and out.element_size() == 4 and offsets.dtype == torch.int64
+    check(lib().sbbf_fill_segment_ids(out.data_ptr(), out.numel(), offsets.data_ptr(),
+                                      offsets.numel() - 1, stream_handle(stream)),
+          "sbbf_fill_segment_ids")
+    return out
+
+
+class MultiFilter:
+    """Many filters of uneven size in one library-owned device arena.
+
+    Keys reach filters by per-key ids (``ids=``, int32 tensor) or grouped per
+    filter by offsets (``offsets=``, int64 CUDA tensor of n_filters + 1)."""
+
+    def __init__(self, num_blocks, device=None):
+        import numpy as np
+        nb = np.ascontiguousarray(num_blocks, dtype=np.uint32)
+        if nb.ndim != 1 or nb.size == 0 or (nb == 0).any():
+            raise ValueError("num_blocks must be a non-empty list of sizes >= 1")
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
+            else torch.device(device)
+        self.num_blocks = nb
+        self.base = np.concatenate([[0], np.cumsum(nb.astype(np.uint64))[:-1]]).astype(np.uint64)
+        h = _P()
+        with torch.cuda.device(self.device):
+            check(lib().sbbf_multi_create(nb.ctypes.data, nb.size, _c.byref(h)),
+                  "sbbf_multi_create")
+        self._h = h
+        self._graph = None
+
+    def __del__(self):
+        g = getattr(self, "_graph", None)
+        if g and _lib is not None:
+            _lib.sbbf_multi_graph_destroy(g)
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.sbbf_multi_destroy(h)
+            self._h = None
+
+    @property
+    def n_filters(self) -> int:
+        return int(self.num_blocks.size)
+
+    @property
+    def total_blocks(self) -> int:
+        return int(self.num_blocks.astype("uint64").sum())
+
+    def _ctx(self):
+        return torch.cuda.device(self.device)
+
+    def clear(self, stream=None):
+        with self._ctx():
+            check(lib().sbbf_multi_clear(self._h, stream_handle(stream)), "sbbf_multi_clear")
+        return self
+
+    def to_numpy(self, stream=None):
+        import numpy as np
+        out = np.empty(self.total_blocks * 8, np.uint32)
+        with self._ctx():
+            check(lib().sbbf_multi_copy_to_host(self._h, out.ctypes.data, out.nbytes,
+                                                stream_handle(stream)), "sbbf_multi_copy_to_host")
+        return out
+
+    def filter_words(self, arena, t: int):
+        b = int(self.base[t])
+        return arena[8 * b: 8 * (b + int(self.num_blocks[t]))]
+
+    def insert(self, hashes, ids=None, offsets=None, stream=None):
+        ptr = _hashes_ptr(hashes, self.device)
+        n = hashes.numel()
+        with self._ctx():
+            if offsets is not None:
+                check(lib().sbbf_multi_insert_segments(self._h, ptr, offsets.data_ptr(), n,
+                                                       stream_handle(stream)),
+                      "sbbf_multi_insert_segments")
+            else:
+                check(lib().sbbf_multi_insert(self._h, ptr, ids.data_ptr(), n,
+                                              stream_handle(stream)), "sbbf_multi_insert")
+        return self
+
+    def find(self, hashes, ids=None, offsets=None, out=None, stream=None):
+        ptr = _hashes_ptr(hashes, self.device)
+        n = hashes.numel()
+        if out is None:
+            out = torch.empty(out_words(n), dtype=torch.int32, device=self.device)
+        with self._ctx():
+            if offsets is not None:
+                check(lib().sbbf_multi_find_segments(self._h, ptr, offsets.data_ptr(), n,
+                                                     out.data_ptr(), stream_handle(stream)),
+                      "sbbf_multi_find_segments")
+            else:
+                check(lib().sbbf_multi_find(self._h, ptr, ids.data_ptr(), n, out.data_ptr(),
+                                            stream_handle(stream)), "sbbf_multi_find")
+        return out
+
+    def insert_each(self, hashes, h_offsets, stream=None):
+        import numpy as np
+        ho = np.ascontiguousarray(h_offsets, dtype=np.uint64)
+        with self._ctx():
+            check(lib().sbbf_multi_insert_each(self._h, _hashes_ptr(hashes, self.device),
+                                               ho.ctypes.data, stream_handle(stream)),
+                  "sbbf_multi_insert_each")
+        return self
+
+    def find_each(self, hashes, h_offsets, out=None, stream=None):
+        import numpy as np
+        ho = np.ascontiguousarray(h_offsets, dtype=np.uint64)
+        n = hashes.numel()
+        if out is None:
+            out = torch.empty(out_words(n), dtype=torch.int32, device=self.device)
+        with self._ctx():
+            check(lib().sbbf_multi_find_each(self._h, _hashes_ptr(hashes, self.device),
+                                             ho.ctypes.data, out.data_ptr(),
+                                             stream_handle(stream)), "sbbf_multi_find_each")
+        return out
+
+    def invalid_count(self, stream=None) -> int:
+        v = _u64()
+        with self._ctx():
+            check(lib().sbbf_multi_invalid_count(self._h, _c.byref(v), stream_handle(stream)),
+                  "sbbf_multi_invalid_count")
+        return int(v.value)
+
+    def get_tuning(self, op: int, form: int):
+        t, l, u = _int(), _int(), _int()
+        check(lib().sbbf_multi_get_tuning(self._h, op, form, _c.byref(t), _c.byref(l),
+                                          _c.byref(u)), "sbbf_multi_get_tuning")
+        return {"threads": t.value, "lanes": l.value, "unroll": u.value}
+
+    def set_tuning(self, op: int, form: int, threads: int, lanes: int, unroll: int):
+        check(lib().sbbf_multi_set_tuning(self._h, op, form, threads, lanes, unroll),
+              "sbbf_multi_set_tuning")
+
+    def tune(self, op: int, hashes, ids=None, offsets=None, stream=None) -> float:
+        """Autotune the launch shape for (op, form) on a prefix of this batch."""
+        form = FORM_SEGMENTS if offsets is not None else FORM_TAGGED
+        aux = offsets if offsets is not None else ids
+        ms = _c.c_float()
+        with self._ctx():
+            check(lib().sbbf_multi_tune(self._h, op, form, _hashes_ptr(hashes, self.device),
+                                        aux.data_ptr(), hashes.numel(), stream_handle(stream),
+                                        _c.byref(ms)), "sbbf_multi_tune")
+        return float(ms.value)
+
+    def graph_launch(self, ins, ins_offsets, q, q_offsets, out, stream=None):
+        """Inserts then lookups of one batch as one CUDA graph launch."""
+        if self._graph is None:
+            g = _P()
+            with self._ctx():
+                check(lib().sbbf_multi_graph_create(self._h, _c.byref(g)),
+                      "sbbf_multi_graph_create")
+            self._graph = g
+        n_i = 0 if ins is None else ins.numel()
+        n_q = 0 if q is None else q.numel()
+        with self._ctx():
+            check(lib().sbbf_multi_graph_launch(
+                self._graph, ins.data_ptr() if n_i else None,
+                ins_offsets.data_ptr() if n_i else None, n_i,
+                q.data_ptr() if n_q else None, q_offsets.data_ptr() if n_q else None, n_q,
+                out.data_ptr() if n_q else None, stream_handle(stream)),
+                "sbbf_multi_graph_launch")
+        return out

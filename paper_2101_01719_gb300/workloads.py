@@ -107,3 +107,77 @@ def build_filter(w: SingleFilterWorkload, f: sbbf.Filter, scratch: torch.Tensor 
         gen_inserts(w, s, cnt, scratch, stream=stream)
         f.insert(scratch[:cnt], stream=stream)
     return f
+
+
+# ---- many filters ------------------------------------------------------------
+
+@dataclass(frozen=True)
+class MultiFilterWorkload:
+    """n_filters filters with key counts log-uniform in [lo, hi] (role 3),
+    sized at bits_per_key rounded up to whole 32-byte blocks.  Inserted keys
+    are the role-0 stream, concatenated in filter order; filter t gets
+    lookup_factor * n_t lookups rounded up to a multiple of 64 (so each
+    filter's answers start a fresh output word), a member_frac share of them
+    drawn from filter t's inserted keys."""
+    name: str
+    cfg: int
+    n_filters: int
+    lo: float
+    hi: float
+    bits_per_key: float
+    lookup_factor: int
+    member_frac: float
+
+    def sizes(self):
+        import numpy as np
+        u = _uniform01_host(seed(self.cfg, ROLE_SIZES), self.n_filters)
+        n_keys = np.rint(np.exp(np.log(self.lo) + u * (np.log(self.hi) - np.log(self.lo))))
+        n_keys = n_keys.astype(np.int64)
+        blocks = np.maximum(np.ceil(n_keys * self.bits_per_key / 256.0), 1).astype(np.int64)
+        return n_keys, blocks
+
+    def offsets(self):
+        """(insert offsets, lookup offsets), each n_filters + 1 int64 on the host."""
+        import numpy as np
+        n_keys, _ = self.sizes()
+        q = ((self.lookup_factor * n_keys + 63) // 64) * 64
+        ins = np.concatenate([[0], np.cumsum(n_keys)]).astype(np.int64)
+        qo = np.concatenate([[0], np.cumsum(q)]).astype(np.int64)
+        return ins, qo
+
+
+def _uniform01_host(sd: int, n: int):
+    """Uniform doubles in [0,1) from the top 53 bits of a splitmix64 stream."""
+    import numpy as np
+    with np.errstate(over="ignore"):
+        i = np.arange(1, n + 1, dtype=np.uint64)
+        z = np.uint64(sd) + i * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return (z >> np.uint64(11)).astype(np.float64) * 2.0**-53
+
+
+# 4096 filters, 1k..4M keys each at 10.5 bits/key; 4x lookups, half members.
+C3 = MultiFilterWorkload("sbbf_4096filters_1k-4M_keys_10.5bpk_4x_lookup", 3, 4096, 1e3, 4e6,
+                         10.5, 4, 0.5)
+# A smaller instance of the same recipe for quick checks.
+C3_SMALL = MultiFilterWorkload("sbbf_256filters_1k-200k_keys_10.5bpk_4x_lookup", 13, 256, 1e3,
+                               2e5, 10.5, 4, 0.5)
+MULTI_WORKLOADS = {w.name: w for w in (C3, C3_SMALL)}
+
+
+def gen_multi(w: MultiFilterWorkload, device=None, stream=None):
+    """Device tensors for workload w: inserted hashes, insert offsets, lookup
+    hashes, lookup offsets (offsets int64, n_filters + 1)."""
+    ins_off, q_off = w.offsets()
+    dev = device or "cuda"
+    d_ins_off = torch.from_numpy(ins_off).to(dev)
+    d_q_off = torch.from_numpy(q_off).to(dev)
+    ins = torch.empty(int(ins_off[-1]), dtype=torch.int64, device=dev)
+    sbbf.fill_splitmix64(ins, seed(w.cfg, ROLE_INSERT), 0, stream)
+    q = torch.empty(int(q_off[-1]), dtype=torch.int64, device=dev)
+    sbbf.fill_segment_queries(q, d_q_off, d_ins_off, seed(w.cfg, ROLE_INSERT),
+                              seed(w.cfg, ROLE_FRESH), seed(w.cfg, ROLE_MEMBER),
+                              member_threshold(w.member_frac), stream)
+    return ins, d_ins_off, q, d_q_off

@@ -144,3 +144,28 @@ def _splitmix64_at(seed, i):
         z = (z ^ (z >> np.uint64(30))) * _M1
         z = (z ^ (z >> np.uint64(27))) * _M2
         return z ^ (z >> np.uint64(31))
+
+
+def multi_offsets(n_keys: np.ndarray, lookup_factor: int):
+    q = ((lookup_factor * n_keys + 63) // 64) * 64
+    ins = np.concatenate([[0], np.cumsum(n_keys)]).astype(np.int64)
+    qo = np.concatenate([[0], np.cumsum(q)]).astype(np.int64)
+    return ins, qo
+
+
+def segment_queries(cfg: int, ins_off: np.ndarray, q_off: np.ndarray, frac: float,
+                    t: int) -> np.ndarray:
+    """Lookups of filter t in the segment layout: query k (global index) is a
+    member when (r_k >> 32) < threshold, namely inserted key
+    ins_off[t] + (((r_k & 0xffffffff) * n_t) >> 32), else fresh output k."""
+    k = np.arange(q_off[t], q_off[t + 1], dtype=np.uint64)
+    r = _splitmix64_at(np.uint64(stream_seed(cfg, ROLE_MEMBER)), k)
+    fresh = _splitmix64_at(np.uint64(stream_seed(cfg, ROLE_FRESH)), k)
+    n_t = int(ins_off[t + 1] - ins_off[t])
+    member = ((r >> np.uint64(32)) < np.uint64(member_threshold(frac))) & (n_t > 0)
+    with np.errstate(over="ignore"):
+        idx = np.uint64(ins_off[t]) + (((r & np.uint64(0xFFFFFFFF)) * np.uint64(n_t))
+                                       >> np.uint64(32))
+    out = fresh.copy()
+    out[member] = _splitmix64_at(np.uint64(stream_seed(cfg, ROLE_INSERT)), idx[member])
+    return out
