@@ -163,6 +163,44 @@ sbbf_status sbbf_find_hashes_host(const sbbf_t *f, sbbf_host_pipe_t *p,
                                   uint32_t *h_out_bits, sbbf_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Allocation-free lookup (the paper has no counterpart: it is an interface
+ * for callers that must not allocate device memory on this path -- a serving
+ * loop bound to a fixed device-memory budget, a framework whose caching
+ * allocator owns the device memory, or a latency-critical caller that cannot
+ * afford the device synchronisation of cudaFree).
+ * ---------------------------------------------------------------------- */
+
+/* Largest n_filters sbbf_multi_find_noalloc accepts. */
+#define SBBF_NOALLOC_MAX_FILTERS 65536u
+
+/* Tagged-form lookup (as sbbf_multi_find) over caller-owned memory, with no
+ * cudaMalloc, cudaFree or other allocating call.
+ *   d_arena        the filters' words, filter t at block offset
+ *                  d_num_blocks[0] + ... + d_num_blocks[t-1] (the layout of
+ *                  sbbf_multi_create), 32-byte aligned, at least
+ *                  sum(d_num_blocks) * 32 bytes (not checked);
+ *   d_num_blocks   n_filters uint32 sizes in device memory; a filter of 0
+ *                  blocks answers 0 and counts its keys as invalid;
+ *   d_hashes, d_ids, n, d_out_bits   as sbbf_multi_find;
+ *   d_invalid_count  device uint64 receiving the number of keys whose id is
+ *                  >= n_filters or names an empty filter (NULL: not reported).
+ * Its scratch (directory and counter) is one static device array of
+ * 256 + 16 * SBBF_NOALLOC_MAX_FILTERS bytes held by every GPU that loads the
+ * library until the process exits; each call overwrites it, so calls that
+ * overlap on the GPU race: issue them in order on one stream.  The first call
+ * on a device looks up that array's device address (with the device
+ * current); make that first call before any stream capture.  Asynchronous.
+ * Errors: SBBF_ERANGE (n_filters > SBBF_NOALLOC_MAX_FILTERS), SBBF_EINVAL
+ * (n_filters == 0, NULL or misaligned pointers), SBBF_ECUDA. */
+sbbf_status sbbf_multi_find_noalloc(const uint32_t *d_arena,
+                                    const uint32_t *d_num_blocks,
+                                    uint32_t n_filters, const uint64_t *d_hashes,
+                                    const uint32_t *d_ids, size_t n,
+                                    uint32_t *d_out_bits,
+                                    unsigned long long *d_invalid_count,
+                                    sbbf_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Synthetic inputs (not part of the method): splitmix64 in counter form,
  * Steele, Lea and Flood, OOPSLA 2014.  Output i of the stream with `seed` is
  * mix(seed + (i + 1) * 0x9E3779B97F4A7C15).

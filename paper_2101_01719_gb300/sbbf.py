@@ -76,6 +76,7 @@ SIGNATURES = {
     "sbbf_multi_graph_create": (_int, [_P, _c.POINTER(_P)]),
     "sbbf_multi_graph_destroy": (_int, [_P]),
     "sbbf_multi_graph_launch": (_int, [_P, _P, _P, _sz, _P, _P, _sz, _P, _P]),
+    "sbbf_multi_find_noalloc": (_int, [_P, _P, _u32, _P, _P, _sz, _P, _P, _P]),
 }
 
 OP_INSERT, OP_FIND = 0, 1
