@@ -397,8 +397,14 @@ def run_multi(args):
 
     def each_step(ev):
         m.clear()
+        if ev:
+            ev[0].record(stream)
         m.insert_each(ins, h_ins_off)
+        if ev:
+            ev[1].record(stream)
         m.find_each(q, h_q_off, out=out)
+        if ev:
+            ev[2].record(stream)
 
     warm = max(args.warmup, 3)
     props = torch.cuda.get_device_properties(dev)
@@ -409,7 +415,9 @@ def run_multi(args):
     sampler.stop()
     graph_out = out.clone()
     split_ms, ev = timed(split_step, args.steps, 1, marks=True)
-    each_ms, _ = timed(each_step, max(2, min(args.steps, 5)), 1)
+    each_ms, ev_each = timed(each_step, max(2, min(args.steps, 5)), 1, marks=True)
+    each_insert_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev_each)
+    each_find_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev_each)
     same = bool(torch.equal(out, graph_out))
     insert_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
     find_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
@@ -448,6 +456,8 @@ def run_multi(args):
                  "separate_launches_gkeys_s": round(keys_per_step * args.steps
                                                     / (split_ms / 1e3) / 1e9, 3),
                  "per_filter_launches_gkeys_s": round(each_value, 3),
+                 "per_filter_insert_gkeys_s": round(n_i / (each_insert_ms / 1e3) / 1e9, 3),
+                 "per_filter_lookup_gkeys_s": round(n_q / (each_find_ms / 1e3) / 1e9, 3),
                  "batched_over_per_filter": round(value / each_value, 3),
                  "identical_results": same},
         "gpu_launches": 3 * args.steps,

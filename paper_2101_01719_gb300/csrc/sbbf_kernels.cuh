@@ -51,6 +51,7 @@ __device__ __forceinline__ FilterRef load_ref(const FilterRef* dir, uint32_t t) 
 }
 
 struct OneFilter {
+  static constexpr int kMinBlocks = 3;
   uint32_t num_blocks;
   __device__ __forceinline__ void begin_chunk(uint64_t) {}
   __device__ __forceinline__ uint64_t block(uint64_t, uint64_t h) const {
@@ -60,23 +61,43 @@ struct OneFilter {
 };
 
 struct Segments {
+  static constexpr int kMinBlocks = 2;
   const uint64_t* offsets;  // n_filters + 1 non-decreasing key offsets
   const FilterRef* dir;
   uint32_t n_filters;
-  uint32_t t0;              // filter of the current chunk's first key
+  // Cached per warp (all lanes hold the same values): the filter of the
+  // current chunk's first key, its key range and its directory entry.
+  uint32_t t0;
+  uint64_t seg_lo, seg_hi;
+  FilterRef ref0;
 
-  // Last t with offsets[t] <= k (k < offsets[n_filters]).
+  // Makes t0 the last t with offsets[t] <= k (k < offsets[n_filters]).
+  // Chunks mostly stay in the same segment or move forward, so the cached
+  // range usually answers without any memory access.  The cache is valid
+  // when seg_lo < seg_hi (a found segment always contains its key).
   __device__ __forceinline__ void begin_chunk(uint64_t k) {
-    uint32_t lo = 0, hi = n_filters;  // offsets[lo] <= k < offsets[hi]
-    while (hi - lo > 1) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (__ldg(offsets + mid) <= k) lo = mid; else hi = mid;
+    if (k >= seg_lo && k < seg_hi) return;
+    uint32_t lo = 0, hi = n_filters;  // invariant: offsets[lo] <= k < offsets[hi]
+    bool found = false;
+    if (seg_lo < seg_hi && k >= seg_hi) {
+      lo = t0 + 1;  // offsets[t0 + 1] = seg_hi <= k
+      found = lo + 1 >= n_filters || __ldg(offsets + lo + 1) > k;  // the next segment
+    }
+    if (!found) {
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(offsets + mid) <= k) lo = mid; else hi = mid;
+      }
     }
     t0 = lo;
+    seg_lo = __ldg(offsets + t0);
+    seg_hi = __ldg(offsets + t0 + 1);
+    ref0 = load_ref(dir, t0);
   }
   __device__ __forceinline__ uint64_t block(uint64_t k, uint64_t h) const {
-    uint32_t t = t0;
-    while (t + 1 < n_filters && __ldg(offsets + t + 1) <= k) ++t;  // segment boundaries
+    if (k < seg_hi) return ref0.base + block_of(h, ref0.num_blocks);
+    uint32_t t = t0;  // a later segment within this chunk
+    while (t + 1 < n_filters && __ldg(offsets + t + 1) <= k) ++t;
     const FilterRef r = load_ref(dir, t);
     return r.base + block_of(h, r.num_blocks);
   }
@@ -84,6 +105,7 @@ struct Segments {
 };
 
 struct Tagged {
+  static constexpr int kMinBlocks = 3;
   const uint32_t* ids;
   const FilterRef* dir;
   uint32_t n_filters;
@@ -124,15 +146,74 @@ __device__ __forceinline__ void warp_span(uint64_t& warp, uint64_t& n_warps) {
   n_warps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
 }
 
+// ---- work scheduling -----------------------------------------------------------
+//
+// A warp processes one "unit" of 64-key groups at a time.  Static schedule
+// (tiles == nullptr): warp w takes units w, w + W, w + 2W, ... (W warps in the
+// grid).  Dynamic schedule (tiles != nullptr, zeroed before the launch): each
+// CTA takes the next tile of kTileRounds x (warps per CTA) consecutive units
+// from a global counter, so every CTA works on neighbouring keys in key order.
+// Keys grouped by filter then keep only a few filters in flight at any time,
+// which keeps them resident in L2 even when the whole arena is not.
+
+constexpr int kTileRounds = 8;
+
+// Every thread of the CTA calls next() until it returns false; in the
+// dynamic schedule all threads fetch the same tiles, so the two barriers per
+// tile are reached the same number of times by every thread.
+struct UnitIter {
+  uint64_t n_units;
+  unsigned long long* tiles;
+  uint64_t pos, step;  // static: next unit and stride; dynamic: tile start
+  int round;
+  unsigned wpc, wic;
+
+  __device__ __forceinline__ UnitIter(uint64_t n, unsigned long long* t) : n_units(n), tiles(t) {
+    wpc = blockDim.x >> 5;
+    wic = threadIdx.x >> 5;
+    if (tiles == nullptr) {
+      warp_span(pos, step);
+    } else {
+      pos = 0;
+      step = static_cast<uint64_t>(wpc) * kTileRounds;
+      round = kTileRounds;  // fetch a tile on the first call
+    }
+  }
+
+  __device__ __forceinline__ bool next(uint64_t& unit) {
+    if (tiles == nullptr) {
+      if (pos >= n_units) return false;
+      unit = pos;
+      pos += step;
+      return true;
+    }
+    __shared__ unsigned long long s_tile;
+    for (;;) {
+      if (round == kTileRounds) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(tiles, 1ull);
+        __syncthreads();
+        pos = s_tile * step;
+        __syncthreads();  // all have read s_tile before the next fetch
+        if (pos >= n_units) return false;
+        round = 0;
+      }
+      const uint64_t u = pos + static_cast<uint64_t>(round) * wpc + wic;
+      ++round;
+      if (u < n_units) {
+        unit = u;
+        return true;
+      }
+    }
+  }
+};
+
 // ---- insert ----------------------------------------------------------------
 
 template <class R, bool kLanes8>
 __global__ void __launch_bounds__(kMaxThreads)
     insert_kernel(uint32_t* __restrict__ words, R res, const uint64_t* __restrict__ hashes,
-                  uint64_t n) {
+                  uint64_t n, unsigned long long* __restrict__ tiles) {
   const unsigned lane = lane_id();
-  uint64_t warp, n_warps;
-  warp_span(warp, n_warps);
   const uint64_t n_groups = (n + 63) >> 6;
   const uint64_t pol = policy_evict_first();
   const bool vec = (reinterpret_cast<uintptr_t>(hashes) & 15) == 0;
@@ -140,7 +221,8 @@ __global__ void __launch_bounds__(kMaxThreads)
   uint32_t* const word_j = words + (lane & 7);
   const int group_base = static_cast<int>(lane & ~7u);
 
-  for (uint64_t g = warp; g < n_groups; g += n_warps) {
+  UnitIter it(n_groups, tiles);
+  for (uint64_t g; it.next(g);) {
     const uint64_t k = g * 64 + 2 * lane;
     uint64_t h0, h1;
     load_pair(hashes, k, n, vec, pol, h0, h1);
@@ -175,13 +257,20 @@ __global__ void __launch_bounds__(kMaxThreads)
 
 // ---- lookup ----------------------------------------------------------------
 
+// Register budget per shape: one-lane shapes with up to two groups in flight
+// are held to R::kMinBlocks 512-thread CTAs per SM (<= 42 registers at 3,
+// <= 64 at 2), which keeps occupancy high without spilling; the others may
+// use up to 128 registers so that their loads in flight do not spill.
+template <class R>
+constexpr int find_min_blocks(bool lanes8, int unroll) {
+  return (lanes8 || unroll >= 4) ? 1 : R::kMinBlocks;
+}
+
 template <class R, bool kLanes8, int U>
-__global__ void __launch_bounds__(kMaxThreads)
+__global__ void __launch_bounds__(kMaxThreads, find_min_blocks<R>(kLanes8, U))
     find_kernel(const uint32_t* __restrict__ words, R res, const uint64_t* __restrict__ hashes,
-                uint64_t n, uint32_t* __restrict__ out) {
+                uint64_t n, uint32_t* __restrict__ out, unsigned long long* __restrict__ tiles) {
   const unsigned lane = lane_id();
-  uint64_t warp, n_warps;
-  warp_span(warp, n_warps);
   const uint64_t n_groups = (n + 63) >> 6;
   const uint64_t n_out = (n + 31) >> 5;
   const uint64_t pk = policy_evict_first();
@@ -189,7 +278,11 @@ __global__ void __launch_bounds__(kMaxThreads)
   const bool vec = (reinterpret_cast<uintptr_t>(hashes) & 15) == 0;
 
   if (!kLanes8) {
-    for (uint64_t g0 = warp * U; g0 < n_groups; g0 += n_warps * U) {
+    // a unit is U consecutive groups, all loads issued before any test
+    const uint64_t n_units = (n_groups + U - 1) / U;
+    UnitIter it(n_units, tiles);
+    for (uint64_t unit; it.next(unit);) {
+      const uint64_t g0 = unit * U;
       uint64_t h[U][2], b[U][2];
 #pragma unroll
       for (int u = 0; u < U; ++u)
@@ -232,7 +325,8 @@ __global__ void __launch_bounds__(kMaxThreads)
     const uint32_t seed = lane_seed(lane & 7);
     const unsigned j = lane & 7;
     const unsigned grp = lane >> 3;
-    for (uint64_t g = warp; g < n_groups; g += n_warps) {
+    UnitIter it(n_groups, tiles);
+    for (uint64_t g; it.next(g);) {
       const uint64_t k = g * 64 + 2 * lane;
       uint64_t h0, h1;
       load_pair(hashes, k, n, vec, pk, h0, h1);
@@ -240,7 +334,7 @@ __global__ void __launch_bounds__(kMaxThreads)
       const uint64_t b0 = k < n ? res.block(k, h0) : kNoBlock64;
       const uint64_t b1 = k + 1 < n ? res.block(k + 1, h1) : kNoBlock64;
       uint32_t lo = 0, hi = 0;
-#pragma unroll
+#pragma unroll 4
       for (int rb = 0; rb < 16; rb += U) {
         uint32_t wv[U], xv[U];
         bool ok[U];

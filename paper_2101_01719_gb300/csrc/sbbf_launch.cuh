@@ -43,24 +43,26 @@ inline int cached_occupancy(const void* func, int threads) {
   return n;
 }
 
+// With `tiles` (a device counter), the launch uses the dynamic in-order
+// schedule: the counter is zeroed on the stream first.
 template <class R>
 sbbf_status launch_insert_t(const Tuning& t, uint32_t* words, R res, const uint64_t* hashes,
-                            uint64_t n, cudaStream_t s) {
+                            uint64_t n, cudaStream_t s, unsigned long long* tiles = nullptr) {
   if (n == 0) return SBBF_OK;
-  void (*k)(uint32_t*, R, const uint64_t*, uint64_t) =
+  void (*k)(uint32_t*, R, const uint64_t*, uint64_t, unsigned long long*) =
       t.lanes == 8 ? insert_kernel<R, true> : insert_kernel<R, false>;
   const uint64_t groups = (n + 63) / 64;
   const unsigned grid =
       grid_for(groups, t.threads / 32, cached_occupancy(reinterpret_cast<const void*>(k), t.threads));
-  k<<<grid, t.threads, 0, s>>>(words, res, hashes, n);
+  if (tiles) SBBF_CUDA(cudaMemsetAsync(tiles, 0, sizeof(unsigned long long), s));
+  k<<<grid, t.threads, 0, s>>>(words, res, hashes, n, tiles);
   return launch_status();
 }
 
 template <class R>
-sbbf_status launch_find_t(const Tuning& t, const uint32_t* words, R res, const uint64_t* hashes,
-                          uint64_t n, uint32_t* out, cudaStream_t s) {
-  if (n == 0) return SBBF_OK;
-  void (*k)(const uint32_t*, R, const uint64_t*, uint64_t, uint32_t*) = nullptr;
+auto find_kernel_for(const Tuning& t) {
+  void (*k)(const uint32_t*, R, const uint64_t*, uint64_t, uint32_t*, unsigned long long*) =
+      nullptr;
   if (t.lanes == 8) {
     k = t.unroll == 1 ? find_kernel<R, true, 1>
         : t.unroll == 2 ? find_kernel<R, true, 2> : find_kernel<R, true, 4>;
@@ -68,11 +70,25 @@ sbbf_status launch_find_t(const Tuning& t, const uint32_t* words, R res, const u
     k = t.unroll == 1 ? find_kernel<R, false, 1>
         : t.unroll == 2 ? find_kernel<R, false, 2> : find_kernel<R, false, 4>;
   }
+  return k;
+}
+
+// CTAs for a lookup launch of n keys with shape t.
+inline unsigned find_grid(const Tuning& t, uint64_t n, const void* k) {
   const uint64_t groups = (n + 63) / 64;
   const uint64_t per_warp = t.lanes == 8 ? 1 : static_cast<uint64_t>(t.unroll);
-  const unsigned grid = grid_for(groups, (t.threads / 32) * per_warp,
-                                 cached_occupancy(reinterpret_cast<const void*>(k), t.threads));
-  k<<<grid, t.threads, 0, s>>>(words, res, hashes, n, out);
+  return grid_for(groups, (t.threads / 32) * per_warp, cached_occupancy(k, t.threads));
+}
+
+template <class R>
+sbbf_status launch_find_t(const Tuning& t, const uint32_t* words, R res, const uint64_t* hashes,
+                          uint64_t n, uint32_t* out, cudaStream_t s,
+                          unsigned long long* tiles = nullptr) {
+  if (n == 0) return SBBF_OK;
+  auto k = find_kernel_for<R>(t);
+  const unsigned grid = find_grid(t, n, reinterpret_cast<const void*>(k));
+  if (tiles) SBBF_CUDA(cudaMemsetAsync(tiles, 0, sizeof(unsigned long long), s));
+  k<<<grid, t.threads, 0, s>>>(words, res, hashes, n, out, tiles);
   return launch_status();
 }
 

@@ -42,6 +42,7 @@ struct sbbf_multi_set {
   sbbf::FilterRef* d_dir;          // device directory
   std::vector<sbbf::FilterRef> h_dir;
   unsigned long long* d_invalid;   // keys with an id >= n_filters since the last read
+  unsigned long long* d_tiles;     // work counters of the in-order schedule: [0] insert, [1] find
   int device;
   sbbf::Tuning tune_find_seg, tune_insert_seg, tune_find_tag, tune_insert_tag;
 };
@@ -50,7 +51,7 @@ struct sbbf_multi_graph {
   sbbf_multi_t* m;
   cudaGraph_t graph;
   cudaGraphExec_t exec;
-  cudaGraphNode_t insert_node, find_node;
+  cudaGraphNode_t memset_node, insert_node, find_node;
   sbbf::Tuning ti, tf;
 };
 
@@ -72,7 +73,11 @@ __global__ void mismatch_kernel(const uint32_t* __restrict__ a, const uint32_t* 
 bool on_device(const sbbf_multi_t* m) { return m && m->device == current_device(); }
 
 Segments seg_resolver(const sbbf_multi_t* m, const uint64_t* d_offsets) {
-  return Segments{d_offsets, m->d_dir, m->n_filters, 0};
+  Segments r{};
+  r.offsets = d_offsets;
+  r.dir = m->d_dir;
+  r.n_filters = m->n_filters;
+  return r;  // empty cached range: the first chunk searches
 }
 
 Tagged tag_resolver(const sbbf_multi_t* m, const uint32_t* d_ids) {
@@ -216,6 +221,7 @@ sbbf_status sbbf_multi_create(const uint32_t* h_num_blocks, uint32_t n_filters, 
   cudaError_t e = cudaMalloc(&m->words, total * 32);
   if (e == cudaSuccess) e = cudaMalloc(&m->d_dir, sizeof(FilterRef) * n_filters);
   if (e == cudaSuccess) e = cudaMalloc(&m->d_invalid, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&m->d_tiles, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess)
     e = cudaMemcpy(m->d_dir, m->h_dir.data(), sizeof(FilterRef) * n_filters,
                    cudaMemcpyHostToDevice);
@@ -240,6 +246,7 @@ sbbf_status sbbf_multi_destroy(sbbf_multi_t* m) {
   if (m->words && (e2 = cudaFree(m->words)) != cudaSuccess) e = e2;
   if (m->d_dir && (e2 = cudaFree(m->d_dir)) != cudaSuccess) e = e2;
   if (m->d_invalid && (e2 = cudaFree(m->d_invalid)) != cudaSuccess) e = e2;
+  if (m->d_tiles && (e2 = cudaFree(m->d_tiles)) != cudaSuccess) e = e2;
   delete m;
   return e == cudaSuccess ? SBBF_OK : record_cuda(e);
 }
@@ -283,7 +290,8 @@ sbbf_status sbbf_multi_insert(sbbf_multi_t* m, const uint64_t* d_hashes, const u
   if (!d_hashes || !d_ids || (reinterpret_cast<uintptr_t>(d_hashes) & 7) ||
       (reinterpret_cast<uintptr_t>(d_ids) & 3))
     return SBBF_EINVAL;
-  return launch_insert_t(m->tune_insert_tag, m->words, tag_resolver(m, d_ids), d_hashes, n, stream);
+  return launch_insert_t(m->tune_insert_tag, m->words, tag_resolver(m, d_ids), d_hashes, n, stream,
+                         m->d_tiles);
 }
 
 sbbf_status sbbf_multi_find(const sbbf_multi_t* m, const uint64_t* d_hashes, const uint32_t* d_ids,
@@ -294,7 +302,7 @@ sbbf_status sbbf_multi_find(const sbbf_multi_t* m, const uint64_t* d_hashes, con
       (reinterpret_cast<uintptr_t>(d_ids) & 3) || (reinterpret_cast<uintptr_t>(d_out_bits) & 3))
     return SBBF_EINVAL;
   return launch_find_t(m->tune_find_tag, m->words, tag_resolver(m, d_ids), d_hashes, n,
-                       d_out_bits, stream);
+                       d_out_bits, stream, m->d_tiles + 1);
 }
 
 sbbf_status sbbf_multi_insert_segments(sbbf_multi_t* m, const uint64_t* d_hashes,
@@ -306,7 +314,7 @@ sbbf_status sbbf_multi_insert_segments(sbbf_multi_t* m, const uint64_t* d_hashes
       (reinterpret_cast<uintptr_t>(d_offsets) & 7))
     return SBBF_EINVAL;
   return launch_insert_t(m->tune_insert_seg, m->words, seg_resolver(m, d_offsets), d_hashes, n,
-                         stream);
+                         stream, m->d_tiles);
 }
 
 sbbf_status sbbf_multi_find_segments(const sbbf_multi_t* m, const uint64_t* d_hashes,
@@ -318,7 +326,7 @@ sbbf_status sbbf_multi_find_segments(const sbbf_multi_t* m, const uint64_t* d_ha
       (reinterpret_cast<uintptr_t>(d_offsets) & 7) || (reinterpret_cast<uintptr_t>(d_out_bits) & 3))
     return SBBF_EINVAL;
   return launch_find_t(m->tune_find_seg, m->words, seg_resolver(m, d_offsets), d_hashes, n,
-                       d_out_bits, stream);
+                       d_out_bits, stream, m->d_tiles + 1);
 }
 
 sbbf_status sbbf_multi_insert_each(sbbf_multi_t* m, const uint64_t* d_hashes,
@@ -412,8 +420,10 @@ sbbf_status sbbf_multi_tune(sbbf_multi_t* m, int op, int form, const uint64_t* d
     }
   }
   cudaStream_t s = stream;
-  DeviceBuf cnt;
+  DeviceBuf cnt, tiles;
   SBBF_CUDA(cnt.alloc(sizeof(unsigned long long)));
+  SBBF_CUDA(tiles.alloc(sizeof(unsigned long long)));
+  unsigned long long* tile_ctr = tiles.as<unsigned long long>();
 
   // Sample offsets (segment form): the prefix of n_s keys, clipped.
   DeviceBuf d_off_s;
@@ -444,8 +454,10 @@ sbbf_status sbbf_multi_tune(sbbf_multi_t* m, int op, int form, const uint64_t* d
     SBBF_CUDA(got.alloc(4 * words));
     auto run_into = [&](const Tuning& t, uint32_t* out) -> sbbf_status {
       return form == SBBF_FORM_SEGMENTS
-                 ? launch_find_t(t, m->words, seg_resolver(m, off_s), d_hashes, n_s, out, s)
-                 : launch_find_t(t, m->words, tag_resolver(m, ids), d_hashes, n_s, out, s);
+                 ? launch_find_t(t, m->words, seg_resolver(m, off_s), d_hashes, n_s, out, s,
+                                 tile_ctr)
+                 : launch_find_t(t, m->words, tag_resolver(m, ids), d_hashes, n_s, out, s,
+                                 tile_ctr);
     };
     st = run_into(kDefaultFind, ref.as<uint32_t>());
     if (st != SBBF_OK) return st;
@@ -467,8 +479,8 @@ sbbf_status sbbf_multi_tune(sbbf_multi_t* m, int op, int form, const uint64_t* d
     }
     auto run_into = [&](const Tuning& t, uint32_t* arena) -> sbbf_status {
       return form == SBBF_FORM_SEGMENTS
-                 ? launch_insert_t(t, arena, seg_resolver(m, off_s), d_hashes, n_s, s)
-                 : launch_insert_t(t, arena, tag_resolver(m, ids), d_hashes, n_s, s);
+                 ? launch_insert_t(t, arena, seg_resolver(m, off_s), d_hashes, n_s, s, tile_ctr)
+                 : launch_insert_t(t, arena, tag_resolver(m, ids), d_hashes, n_s, s, tile_ctr);
     };
     st = launch_clear(ref.as<uint32_t>(), n_words, s);
     if (st == SBBF_OK) st = run_into(kDefaultInsert, ref.as<uint32_t>());
@@ -516,31 +528,36 @@ sbbf_status sbbf_multi_graph_create(sbbf_multi_t* m, sbbf_multi_graph_t** out) {
   };
   cudaError_t e = cudaGraphCreate(&g->graph, 0);
   if (e != cudaSuccess) return fail(e);
+  // Both work counters are zeroed by a memset node ahead of the two kernels.
+  cudaMemsetParams mp = {};
+  mp.dst = m->d_tiles;
+  mp.value = 0;
+  mp.elementSize = 4;
+  mp.width = 4;  // 16 bytes: both 64-bit counters
+  mp.height = 1;
+  mp.pitch = 0;
+  e = cudaGraphAddMemsetNode(&g->memset_node, g->graph, nullptr, 0, &mp);
+  if (e != cudaSuccess) return fail(e);
   // Placeholder arguments; every launch sets the real ones.
   Segments r = seg_resolver(m, nullptr);
   uint32_t* words = m->words;
   const uint64_t* h = nullptr;
   uint64_t n = 0;
   uint32_t* o = nullptr;
-  void* iargs[] = {&words, &r, &h, &n};
-  void* fargs[] = {&words, &r, &h, &n, &o};
+  unsigned long long* ti = m->d_tiles;
+  unsigned long long* tf = m->d_tiles + 1;
+  void* iargs[] = {&words, &r, &h, &n, &ti};
+  void* fargs[] = {&words, &r, &h, &n, &o, &tf};
   cudaKernelNodeParams ip = {};
   ip.func = reinterpret_cast<void*>(g->ti.lanes == 8 ? insert_kernel<Segments, true>
                                                      : insert_kernel<Segments, false>);
   ip.gridDim = dim3(1);
   ip.blockDim = dim3(g->ti.threads);
   ip.kernelParams = iargs;
-  e = cudaGraphAddKernelNode(&g->insert_node, g->graph, nullptr, 0, &ip);
+  e = cudaGraphAddKernelNode(&g->insert_node, g->graph, &g->memset_node, 1, &ip);
   if (e != cudaSuccess) return fail(e);
-  void (*fk)(const uint32_t*, Segments, const uint64_t*, uint64_t, uint32_t*);
-  if (g->tf.lanes == 8)
-    fk = g->tf.unroll == 1 ? find_kernel<Segments, true, 1>
-         : g->tf.unroll == 2 ? find_kernel<Segments, true, 2> : find_kernel<Segments, true, 4>;
-  else
-    fk = g->tf.unroll == 1 ? find_kernel<Segments, false, 1>
-         : g->tf.unroll == 2 ? find_kernel<Segments, false, 2> : find_kernel<Segments, false, 4>;
   cudaKernelNodeParams fp = {};
-  fp.func = reinterpret_cast<void*>(fk);
+  fp.func = reinterpret_cast<void*>(find_kernel_for<Segments>(g->tf));
   fp.gridDim = dim3(1);
   fp.blockDim = dim3(g->tf.threads);
   fp.kernelParams = fargs;
@@ -579,17 +596,17 @@ sbbf_status sbbf_multi_graph_launch(sbbf_multi_graph_t* g, const uint64_t* d_ins
   const uint64_t* hq = d_q;
   uint64_t ni = n_ins, nq = n_q;
   uint32_t* o = d_out_bits;
-  void* iargs[] = {&words, &ri, &hi, &ni};
-  void* fargs[] = {&words, &rf, &hq, &nq, &o};
+  unsigned long long* ti = m->d_tiles;
+  unsigned long long* tf = m->d_tiles + 1;
+  void* iargs[] = {&words, &ri, &hi, &ni, &ti};
+  void* fargs[] = {&words, &rf, &hq, &nq, &o, &tf};
   cudaKernelNodeParams ip = {}, fp = {};
   SBBF_CUDA(cudaGraphKernelNodeGetParams(g->insert_node, &ip));
   SBBF_CUDA(cudaGraphKernelNodeGetParams(g->find_node, &fp));
   const int occ_i = cached_occupancy(ip.func, g->ti.threads);
-  const int occ_f = cached_occupancy(fp.func, g->tf.threads);
   // n == 0 launches one CTA whose loop body never runs.
   ip.gridDim = dim3(grid_for((ni + 63) / 64, g->ti.threads / 32, occ_i));
-  const uint64_t per_warp = g->tf.lanes == 8 ? 1 : g->tf.unroll;
-  fp.gridDim = dim3(grid_for((nq + 63) / 64, (g->tf.threads / 32) * per_warp, occ_f));
+  fp.gridDim = dim3(find_grid(g->tf, nq, fp.func));
   ip.kernelParams = iargs;
   fp.kernelParams = fargs;
   ip.extra = nullptr;

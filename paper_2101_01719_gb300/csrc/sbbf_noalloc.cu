@@ -36,6 +36,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 // Tagged form over a directory built on the device from caller sizes: an id
 // past the set or a filter of zero blocks is an invalid key (skipped, counted).
 struct TaggedDeviceDir {
+  static constexpr int kMinBlocks = 3;
   const uint32_t* ids;
   const FilterRef* dir;
   uint32_t n_filters;
@@ -171,7 +172,7 @@ extern "C" sbbf_status sbbf_multi_find_noalloc(const uint32_t* d_arena,
     const uint64_t groups = (n + 63) / 64;
     const TaggedDeviceDir res{d_ids, dir, n_filters, counter, 0};
     kernel<<<grid_for(groups, (256 / 32) * 2, occ), 256, 0, stream>>>(d_arena, res, d_hashes, n,
-                                                                      d_out_bits);
+                                                                      d_out_bits, nullptr);
     st = launch_status();
     if (st != SBBF_OK) return st;
   }
