@@ -54,6 +54,10 @@ def parse_args(argv=None):
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="approximate CPU work for the oracle baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--requests", type=int, default=0,
+                   help="serving workloads: requests per replay (0: the workload's count)")
+    p.add_argument("--serial-requests", type=int, default=100_000,
+                   help="serving workloads: requests in the serial-launch comparison")
     return p.parse_args(argv)
 
 
@@ -465,6 +469,83 @@ def run_multi(args):
     }
 
 
+# ---- serving: continuous batching vs serial per-request launches --------------
+
+def run_serving(args):
+    import numpy as np
+    import torch
+
+    import paper_2101_01719_gb300 as sb
+    from paper_2101_01719_gb300 import workloads as wl
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = wl.SERVING_WORKLOADS[args.workload]
+    n_req = args.requests or w.n_requests
+
+    def pct(lat_ns):
+        return {"p50_ms": round(float(np.percentile(lat_ns, 50)) / 1e6, 4),
+                "p99_ms": round(float(np.percentile(lat_ns, 99)) / 1e6, 4)}
+
+    def make_server(budget):
+        srv = sb.Server(budget, max_window_requests=4096, max_inflight_windows=2,
+                        max_window_keys=1 << 26, max_pending_requests=1 << 25, device=dev)
+        blocks = wl.prefill_server(w, srv, device=dev)
+        return srv, blocks
+
+    pool = torch.empty(w.pool_hashes, dtype=torch.int64, device=dev)
+    sb.fill_splitmix64(pool, wl.seed(w.cfg, wl.ROLE_FRESH), 0)
+    ring_words = 1 << 26
+    out = torch.zeros(ring_words + (1 << 16), dtype=torch.int32, device=dev)
+    srv, blocks = make_server(w.budget_bytes)
+    total_bytes = int(blocks.sum()) * 32
+
+    def replay(server, rate, serial=False, n=n_req):
+        op, filt, size, off, arr = w.requests(n, rate)
+        rec, _, _ = wl.request_records(op, filt, size, off, pool, out, ring_words)
+        a = time.perf_counter()
+        lat = server.replay(rec, arr, serial=serial)
+        wall = time.perf_counter() - a
+        keys = int(size.sum())
+        return {"requests": n, "keys": keys, "gkeys_s": round(keys / wall / 1e9, 3),
+                "wall_s": round(wall, 3), **pct(lat)}
+
+    warm = replay(srv, float("inf"), n=min(n_req, 20000))
+    sat = replay(srv, float("inf"))
+    mean_keys = sat["keys"] / sat["requests"]
+    cap_req_s = sat["gkeys_s"] * 1e9 / mean_keys
+    loads = {}
+    for f in (0.5, 0.8, 0.95):
+        loads[str(f)] = replay(srv, f * cap_req_s)
+    st = srv.stats()
+    n_serial = min(n_req, args.serial_requests)
+    serial = {"saturation": replay(srv, float("inf"), serial=True, n=n_serial),
+              "0.5": replay(srv, 0.5 * cap_req_s, serial=True, n=n_serial)}
+    batched_same = {"saturation": replay(srv, float("inf"), n=n_serial),
+                    "0.5": replay(srv, 0.5 * cap_req_s, n=n_serial)}
+    srv.close()
+    srv2, _ = make_server(total_bytes // 2)
+    evict = replay(srv2, 0.5 * cap_req_s, n=min(n_req, args.serial_requests))
+    evict["budget_bytes"] = total_bytes // 2
+    evict["stats"] = srv2.stats()
+    srv2.close()
+    return {
+        "metric": "SBBF serving keys/s; p50/p99 ms", "value": sat["gkeys_s"], "unit": UNIT,
+        "n_gpus": 1, "steps": len(loads) + 1, "warmup": 1, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (seeded splitmix64; Poisson arrivals)",
+        "config": {"workload": w.name, "n_filters": w.n_filters,
+                   "filter_bytes_total": total_bytes, "budget_bytes": w.budget_bytes,
+                   "requests": n_req, "lookup_frac": w.lookup_frac,
+                   "request_keys": [w.req_lo, w.req_hi], "payload": "device-resident pool",
+                   "capacity_req_s": round(cap_req_s, 1)},
+        "saturation": sat, "loads": loads, "stats": st,
+        "serial_per_request_launches": serial, "batched_same_requests": batched_same,
+        "half_budget": evict, "warmup_run": warm,
+    }
+
+
 # ---- the CPU oracle (baseline / reference arm) ---------------------------------
 
 def cpu_baseline(w, seconds: float, steps: int = 1):
@@ -546,6 +627,8 @@ def main(argv=None):
         line = run_reference(args)
     elif args.workload in wl.MULTI_WORKLOADS:
         line = run_multi(args)
+    elif args.workload in wl.SERVING_WORKLOADS:
+        line = run_serving(args)
     else:
         line = run_ours(args)
     if line is not None:

@@ -163,6 +163,100 @@ sbbf_status sbbf_find_hashes_host(const sbbf_t *f, sbbf_host_pipe_t *p,
                                   uint32_t *h_out_bits, sbbf_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Serving: resident filters, requests arriving over time, continuous batching
+ * under a device-memory budget (not in the paper).
+ *
+ * A scheduler thread owned by the server forms launch windows from the
+ * requests that have arrived (in arrival order, bounded by requests and
+ * hashes per window), admits each request only when its filter is resident
+ * within the budget (evicting the least recently used idle filter to pinned
+ * host memory when needed), and runs all requests of a window in one launch
+ * while the next window is being formed.  Results equal serial replay in
+ * arrival order: a lookup sees exactly the inserts on its filter that arrived
+ * before it (per filter, runs of inserts and runs of lookups execute as
+ * ordered phases).
+ * ---------------------------------------------------------------------- */
+
+typedef struct sbbf_server sbbf_server_t;
+
+typedef struct sbbf_server_config {
+  uint64_t budget_bytes;         /* device bytes for resident filters plus the
+                                    device-resident buffers of admitted requests */
+  uint32_t max_window_requests;  /* requests per launch window (slots) */
+  uint32_t max_inflight_windows; /* windows enqueued on the GPU at once */
+  uint64_t max_window_keys;      /* hashes per window (a larger single request
+                                    still forms a window of its own) */
+  uint64_t max_pending_requests; /* submitted, not yet admitted; beyond it
+                                    submit returns SBBF_EBUSY */
+} sbbf_server_config_t;
+
+typedef struct sbbf_request {
+  uint32_t op;                   /* SBBF_OP_INSERT or SBBF_OP_FIND */
+  uint32_t filter;               /* id from sbbf_server_add_filter */
+  uint64_t n;                    /* hashes */
+  const uint64_t *d_hashes;      /* device or pinned host memory, 8-byte
+                                    aligned, owned by the caller, unchanged
+                                    until the request completes */
+  uint32_t *d_out_bits;          /* lookups: (n + 31) / 32 words (device or
+                                    pinned host), written by completion */
+} sbbf_request_t;
+
+typedef struct sbbf_server_stats {
+  uint64_t windows, launches, phases, requests, keys;
+  uint64_t admissions, evictions, admission_waits;
+  uint64_t resident_bytes;
+} sbbf_server_stats_t;
+
+/* Start a server (its stream and scheduler thread) on the current device.
+ * Errors: SBBF_EINVAL (zero limits), SBBF_ENOMEM, SBBF_ECUDA. */
+sbbf_status sbbf_server_create(const sbbf_server_config_t *cfg,
+                               sbbf_server_t **out);
+/* Finish all submitted requests, stop the thread and free everything. */
+sbbf_status sbbf_server_destroy(sbbf_server_t *s);
+
+/* Register an empty filter of num_blocks blocks (not yet resident). */
+sbbf_status sbbf_server_add_filter(sbbf_server_t *s, uint32_t num_blocks,
+                                   uint32_t *id);
+
+/* Enqueue a request (thread-safe, non-blocking).  *ticket identifies it.
+ * Errors: SBBF_EINVAL, SBBF_EBUSY (queue full, or the filter plus the
+ * request's device buffers exceed the whole budget), or the server's sticky
+ * device error. */
+sbbf_status sbbf_server_submit(sbbf_server_t *s, const sbbf_request_t *r,
+                               uint64_t *ticket);
+/* *done = 1 once the request's results are in place. */
+sbbf_status sbbf_server_poll(sbbf_server_t *s, uint64_t ticket, int *done);
+/* Block until the request completes or timeout_ns passes (0: no limit).
+ * Errors: SBBF_ETIMEOUT, SBBF_EINVAL, a device error. */
+sbbf_status sbbf_server_wait(sbbf_server_t *s, uint64_t ticket,
+                             uint64_t timeout_ns);
+/* Block until no request is pending or running (timeout_ns 0: no limit). */
+sbbf_status sbbf_server_drain(sbbf_server_t *s, uint64_t timeout_ns);
+
+/* Insert d_hashes[0..n) into filter id outside any window (set-up before
+ * serving; drains first; synchronous). */
+sbbf_status sbbf_server_prefill(sbbf_server_t *s, uint32_t id,
+                                const uint64_t *d_hashes, size_t n);
+/* Copy filter id's words to host memory (drains first; synchronous). */
+sbbf_status sbbf_server_copy_filter(sbbf_server_t *s, uint32_t id,
+                                    uint32_t *h_words, size_t bytes);
+sbbf_status sbbf_server_stats(sbbf_server_t *s, sbbf_server_stats_t *out);
+
+/* Client-side replay: submit reqs[i] at arrival_ns[i] nanoseconds after the
+ * call starts (waiting for the clock; on a full queue, retrying), then wait
+ * for all; latency_ns[i] = completion - arrival.  Synchronous. */
+sbbf_status sbbf_server_replay(sbbf_server_t *s, const sbbf_request_t *reqs,
+                               const uint64_t *arrival_ns, size_t n,
+                               uint64_t *latency_ns);
+/* The same arrivals served one plain launch per request, in arrival order,
+ * on the server's filters and stream (the scheduler is paused meanwhile):
+ * the serial baseline for the batched server. */
+sbbf_status sbbf_server_replay_serial(sbbf_server_t *s,
+                                      const sbbf_request_t *reqs,
+                                      const uint64_t *arrival_ns, size_t n,
+                                      uint64_t *latency_ns);
+
+/* ------------------------------------------------------------------------
  * Allocation-free lookup (the paper has no counterpart: it is an interface
  * for callers that must not allocate device memory on this path -- a serving
  * loop bound to a fixed device-memory budget, a framework whose caching

@@ -12,6 +12,8 @@ from .sbbf import (  # noqa: F401
     Filter,
     HostPipe,
     MultiFilter,
+    REQUEST_DTYPE,
+    Server,
     SbbfError,
     check,
     count_bits,

@@ -77,6 +77,18 @@ SIGNATURES = {
     "sbbf_multi_graph_destroy": (_int, [_P]),
     "sbbf_multi_graph_launch": (_int, [_P, _P, _P, _sz, _P, _P, _sz, _P, _P]),
     "sbbf_multi_find_noalloc": (_int, [_P, _P, _u32, _P, _P, _sz, _P, _P, _P]),
+    "sbbf_server_create": (_int, [_P, _c.POINTER(_P)]),
+    "sbbf_server_destroy": (_int, [_P]),
+    "sbbf_server_add_filter": (_int, [_P, _u32, _c.POINTER(_u32)]),
+    "sbbf_server_submit": (_int, [_P, _P, _c.POINTER(_u64)]),
+    "sbbf_server_poll": (_int, [_P, _u64, _c.POINTER(_int)]),
+    "sbbf_server_wait": (_int, [_P, _u64, _u64]),
+    "sbbf_server_drain": (_int, [_P, _u64]),
+    "sbbf_server_prefill": (_int, [_P, _u32, _P, _sz]),
+    "sbbf_server_copy_filter": (_int, [_P, _u32, _P, _sz]),
+    "sbbf_server_stats": (_int, [_P, _P]),
+    "sbbf_server_replay": (_int, [_P, _P, _P, _sz, _P]),
+    "sbbf_server_replay_serial": (_int, [_P, _P, _P, _sz, _P]),
 }
 
 OP_INSERT, OP_FIND = 0, 1
@@ -439,3 +451,114 @@ class MultiFilter:
                 out.data_ptr() if n_q else None, stream_handle(stream)),
                 "sbbf_multi_graph_launch")
         return out
+
+
+# ---- serving -------------------------------------------------------------------
+
+class _ServerConfig(_c.Structure):
+    _fields_ = [("budget_bytes", _u64), ("max_window_requests", _u32),
+                ("max_inflight_windows", _u32), ("max_window_keys", _u64),
+                ("max_pending_requests", _u64)]
+
+
+class _Request(_c.Structure):
+    _fields_ = [("op", _u32), ("filter", _u32), ("n", _u64), ("d_hashes", _P),
+                ("d_out_bits", _P)]
+
+
+class _Stats(_c.Structure):
+    _fields_ = [(k, _u64) for k in ("windows", "launches", "phases", "requests", "keys",
+                                    "admissions", "evictions", "admission_waits",
+                                    "resident_bytes")]
+
+
+# numpy layout of sbbf_request_t (32 bytes)
+REQUEST_DTYPE = [("op", "<u4"), ("filter", "<u4"), ("n", "<u8"), ("hashes", "<u8"),
+                 ("out", "<u8")]
+
+
+class Server:
+    """Continuous-batching server over resident filters (see sbbf.h)."""
+
+    def __init__(self, budget_bytes: int, max_window_requests: int = 4096,
+                 max_inflight_windows: int = 2, max_window_keys: int = 1 << 26,
+                 max_pending_requests: int = 1 << 24, device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
+            else torch.device(device)
+        cfg = _ServerConfig(budget_bytes, max_window_requests, max_inflight_windows,
+                            max_window_keys, max_pending_requests)
+        h = _P()
+        with torch.cuda.device(self.device):
+            check(lib().sbbf_server_create(_c.byref(cfg), _c.byref(h)), "sbbf_server_create")
+        self._h = h
+        self.num_blocks = []
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            self._h = None
+            check(_lib.sbbf_server_destroy(h), "sbbf_server_destroy")
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_filter(self, num_blocks: int) -> int:
+        fid = _u32()
+        check(lib().sbbf_server_add_filter(self._h, num_blocks, _c.byref(fid)),
+              "sbbf_server_add_filter")
+        self.num_blocks.append(int(num_blocks))
+        return int(fid.value)
+
+    def prefill(self, fid: int, hashes: torch.Tensor):
+        with torch.cuda.device(self.device):
+            check(lib().sbbf_server_prefill(self._h, fid, _hashes_ptr(hashes, None),
+                                            hashes.numel()), "sbbf_server_prefill")
+
+    def submit(self, op: int, fid: int, hashes, out=None) -> int:
+        r = _Request(op, fid, hashes.numel(), hashes.data_ptr(),
+                     out.data_ptr() if out is not None else None)
+        t = _u64()
+        check(lib().sbbf_server_submit(self._h, _c.byref(r), _c.byref(t)), "sbbf_server_submit")
+        return int(t.value)
+
+    def poll(self, ticket: int) -> bool:
+        d = _int()
+        check(lib().sbbf_server_poll(self._h, ticket, _c.byref(d)), "sbbf_server_poll")
+        return bool(d.value)
+
+    def wait(self, ticket: int, timeout_ns: int = 0):
+        check(lib().sbbf_server_wait(self._h, ticket, timeout_ns), "sbbf_server_wait")
+
+    def wait_status(self, ticket: int, timeout_ns: int = 0) -> int:
+        return int(lib().sbbf_server_wait(self._h, ticket, timeout_ns))
+
+    def drain(self, timeout_ns: int = 0):
+        check(lib().sbbf_server_drain(self._h, timeout_ns), "sbbf_server_drain")
+
+    def filter_words(self, fid: int):
+        import numpy as np
+        out = np.empty(self.num_blocks[fid] * 8, np.uint32)
+        check(lib().sbbf_server_copy_filter(self._h, fid, out.ctypes.data, out.nbytes),
+              "sbbf_server_copy_filter")
+        return out
+
+    def stats(self) -> dict:
+        st = _Stats()
+        check(lib().sbbf_server_stats(self._h, _c.byref(st)), "sbbf_server_stats")
+        return {k: int(getattr(st, k)) for k, _ in _Stats._fields_}
+
+    def replay(self, reqs, arrival_ns, serial: bool = False):
+        """Submit a numpy array of REQUEST_DTYPE records at arrival_ns (uint64,
+        from the call's start) and return per-request latencies in ns."""
+        import numpy as np
+        reqs = np.ascontiguousarray(reqs)
+        arr = np.ascontiguousarray(arrival_ns, dtype=np.uint64)
+        lat = np.zeros(len(reqs), np.uint64)
+        fn = lib().sbbf_server_replay_serial if serial else lib().sbbf_server_replay
+        with torch.cuda.device(self.device):
+            check(fn(self._h, reqs.ctypes.data, arr.ctypes.data, len(reqs), lat.ctypes.data),
+                  "sbbf_server_replay_serial" if serial else "sbbf_server_replay")
+        return lat

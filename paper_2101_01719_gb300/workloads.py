@@ -181,3 +181,114 @@ def gen_multi(w: MultiFilterWorkload, device=None, stream=None):
                               seed(w.cfg, ROLE_FRESH), seed(w.cfg, ROLE_MEMBER),
                               member_threshold(w.member_frac), stream)
     return ins, d_ins_off, q, d_q_off
+
+
+# ---- serving -------------------------------------------------------------------
+
+@dataclass(frozen=True)
+class ServingWorkload:
+    """n_filters resident filters with byte sizes log-uniform in
+    [size_lo, size_hi] (role 3), each pre-filled to prefill_bits_per_key with
+    role-0 hashes (filter t takes the next m_t outputs); requests with sizes
+    log-uniform in [req_lo, req_hi] (role 6), a lookup_frac share lookups
+    (role 2), filters uniform (role 4), payloads slices of a pool of
+    pool_hashes role-1 hashes at uniform offsets (role 1 again, separate
+    index range) and Poisson arrivals (role 5)."""
+    name: str
+    cfg: int
+    n_filters: int
+    size_lo: float
+    size_hi: float
+    budget_bytes: int
+    n_requests: int
+    lookup_frac: float
+    req_lo: float
+    req_hi: float
+    prefill_bits_per_key: float
+    pool_hashes: int
+
+    def filter_blocks(self):
+        import numpy as np
+        u = _uniform01_host(seed(self.cfg, ROLE_SIZES), self.n_filters)
+        b = np.exp(np.log(self.size_lo) + u * (np.log(self.size_hi) - np.log(self.size_lo)))
+        return np.maximum(np.rint(b / 32.0), 1).astype(np.int64)
+
+    def prefill_counts(self):
+        import numpy as np
+        return np.floor(self.filter_blocks() * 256.0 / self.prefill_bits_per_key).astype(np.int64)
+
+    def requests(self, n: int, rate_per_s: float):
+        """(op, filter, size, pool offset, arrival ns) for the first n
+        requests at `rate_per_s` requests per second (inf: all at t=0)."""
+        import numpy as np
+        from . import sbbf as _s
+        sizes = np.rint(np.exp(np.log(self.req_lo) + _uniform01_host(
+            seed(self.cfg, ROLE_REQSIZE), n) * (np.log(self.req_hi) - np.log(self.req_lo))))
+        sizes = np.clip(sizes, 1, self.pool_hashes).astype(np.uint64)
+        op = np.where(_uniform01_host(seed(self.cfg, ROLE_MEMBER), n) < self.lookup_frac,
+                      _s.OP_FIND, _s.OP_INSERT).astype(np.uint32)
+        filt = np.floor(_uniform01_host(seed(self.cfg, ROLE_ORDER), n)
+                        * self.n_filters).astype(np.uint32)
+        span = (self.pool_hashes - sizes + 1).astype(np.float64)
+        off = np.floor(_uniform01_host(seed(self.cfg, ROLE_FRESH) ^ 0x5A5A, n) * span)
+        off = off.astype(np.uint64)
+        if np.isinf(rate_per_s):
+            arrival = np.zeros(n, np.uint64)
+        else:
+            gaps = -np.log1p(-_uniform01_host(seed(self.cfg, ROLE_ARRIVAL), n)) / rate_per_s
+            arrival = np.rint(np.cumsum(gaps) * 1e9).astype(np.uint64)
+        return op, filt, sizes, off, arrival
+
+
+C4 = ServingWorkload("sbbf_serve_256filters_128KiB-1GiB_70pct_lookup", 4, 256, 128 * 2**10,
+                     2**30, 80 * 10**9, 10_000_000, 0.7, 1, 1e6, 10.5, 1 << 27)
+C4_SMALL = ServingWorkload("sbbf_serve_32filters_4KiB-4MiB_70pct_lookup", 14, 32, 4 * 2**10,
+                           4 * 2**20, 64 * 2**20, 20_000, 0.7, 1, 2e4, 10.5, 1 << 22)
+SERVING_WORKLOADS = {w.name: w for w in (C4, C4_SMALL)}
+
+
+def request_records(op, filt, sizes, off, pool: torch.Tensor, out: torch.Tensor,
+                    ring_words: int | None = None):
+    """REQUEST_DTYPE records pointing into the hash pool and an output area:
+    lookups get consecutive 32-byte-aligned output slices (wrapping around
+    after ring_words words when given)."""
+    import numpy as np
+    from . import sbbf as _s
+    n = len(op)
+    rec = np.zeros(n, dtype=_s.REQUEST_DTYPE)
+    rec["op"], rec["filter"], rec["n"] = op, filt, sizes
+    rec["hashes"] = np.uint64(pool.data_ptr()) + off * np.uint64(8)
+    words = ((sizes + np.uint64(31)) // np.uint64(32) + np.uint64(7)) // np.uint64(8) * np.uint64(8)
+    words = np.where(op == _s.OP_FIND, words, 0).astype(np.uint64)
+    start = np.concatenate([[0], np.cumsum(words)[:-1]]).astype(np.uint64)
+    if ring_words:
+        start = start % np.uint64(ring_words)
+        over = start + words > np.uint64(ring_words)
+        start[over] = 0
+    rec["out"] = np.where(op == _s.OP_FIND, np.uint64(out.data_ptr()) + start * np.uint64(4), 0)
+    return rec, start, words
+
+
+def gen_inserts_seeded(sd: int, start: int, n: int, device=None, out=None, stream=None):
+    """splitmix64 outputs start..start+n-1 of seed sd (device int64)."""
+    if out is None:
+        out = torch.empty(n, dtype=torch.int64, device=device or "cuda")
+    sbbf.fill_splitmix64(out[:n], sd, start, stream)
+    return out[:n]
+
+
+def prefill_server(w: ServingWorkload, srv, chunk: int = 1 << 28, device=None):
+    """Register w's filters on srv and pre-fill each one; returns the blocks."""
+    import numpy as np
+    blocks = w.filter_blocks()
+    counts = w.prefill_counts()
+    start = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    buf = torch.empty(min(chunk, int(counts.max()) or 1), dtype=torch.int64,
+                      device=device or "cuda")
+    for t, b in enumerate(blocks):
+        fid = srv.add_filter(int(b))
+        for s0 in range(0, int(counts[t]), chunk):
+            c = min(chunk, int(counts[t]) - s0)
+            srv.prefill(fid, gen_inserts_seeded(seed(w.cfg, ROLE_INSERT), int(start[t]) + s0, c,
+                                                out=buf))
+    return blocks
