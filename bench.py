@@ -54,6 +54,8 @@ def parse_args(argv=None):
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="approximate CPU work for the oracle baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--eager", action="store_true",
+                   help="launch each kernel from Python instead of replaying CUDA graphs")
     p.add_argument("--requests", type=int, default=0,
                    help="serving workloads: requests per replay (0: the workload's count)")
     p.add_argument("--serial-requests", type=int, default=100_000,
@@ -96,6 +98,12 @@ def max_over_ranks(dist, value: float, device=None) -> float:
 def aggregate(units_per_rank: list[int], seconds_max: float) -> float:
     """Whole-job throughput: every rank's units over the slowest rank's time."""
     return sum(units_per_rank) / seconds_max
+
+
+def lookup_slice_start(rank: int, n_lookup: int) -> int:
+    """First lookup index of a rank: ranks take disjoint slices of the query
+    stream (weak scaling, each rank a replica of the filter)."""
+    return rank * n_lookup
 
 
 # ---- measured peaks, clocks, profile figures --------------------------------
@@ -215,7 +223,7 @@ def run_ours(args):
     # Inputs resident in HBM before timing; each rank takes its own slice of
     # the lookup stream (units sharded by rank, no data-path collective).
     ins = wl.gen_inserts(w, 0, w.n_insert, device=dev)
-    qry = wl.gen_queries(w, rank * w.n_lookup, w.n_lookup, device=dev)
+    qry = wl.gen_queries(w, lookup_slice_start(rank, w.n_lookup), w.n_lookup, device=dev)
     out = torch.empty(sb.out_words(w.n_lookup), dtype=torch.int32, device=dev)
     f = sb.Filter(w.num_blocks, device=dev)
     torch.cuda.synchronize()
@@ -233,8 +241,24 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
 
-    # Per-kernel events for the roofline (same stream as the launches).
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    # The step and its parts as CUDA graphs: replays carry no host launch
+    # overhead, which otherwise dominates the small workloads.
+    graphs = {}
+    if not args.eager:
+        for name, fn in (("step", step), ("insert", insert_all),
+                         ("find", lambda: f.find(qry, out=out))):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                fn()
+            graphs[name] = g
+        torch.cuda.synchronize()
+
+    def run_step():
+        if graphs:
+            graphs["step"].replay()
+        else:
+            step()
+
     props = torch.cuda.get_device_properties(dev)
     uuid = str(getattr(props, "uuid", ""))
     gpu_id = uuid if uuid.startswith("GPU-") else ("GPU-" + uuid if uuid else str(local))
@@ -246,15 +270,8 @@ def run_ours(args):
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
-    for s in range(args.steps):
-        e = ev[s]
-        e[0].record(stream)
-        f.clear()
-        e[1].record(stream)
-        insert_all()
-        e[2].record(stream)
-        f.find(qry, out=out)
-        e[3].record(stream)
+    for _ in range(args.steps):
+        run_step()
     t1.record(stream)
     torch.cuda.synchronize()
     barrier(dist)
@@ -262,8 +279,24 @@ def run_ours(args):
     elapsed_ms = t0.elapsed_time(t1)
     slowest_ms = max_over_ranks(dist, elapsed_ms, dev)
 
-    insert_ms = statistics.mean(ev[s][1].elapsed_time(ev[s][2]) for s in range(args.steps))
-    find_ms = statistics.mean(ev[s][2].elapsed_time(ev[s][3]) for s in range(args.steps))
+    # Per-kernel durations (same stream as the launches), for the roofline.
+    def per_call_ms(fn, reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    reps = max(3, min(args.steps, 50))
+    if graphs:
+        insert_ms = per_call_ms(graphs["insert"].replay, reps)
+        find_ms = per_call_ms(graphs["find"].replay, reps)
+    else:
+        insert_ms = per_call_ms(insert_all, reps)
+        find_ms = per_call_ms(lambda: f.find(qry, out=out), reps)
     keys_per_step = w.n_insert + w.n_lookup
     value = aggregate([keys_per_step * args.steps] * world, slowest_ms / 1e3) / 1e9
 
@@ -315,6 +348,7 @@ def run_ours(args):
         "data": "synthetic (seeded splitmix64 hashes generated on the device)",
         "config": {"workload": w.name, "num_blocks": w.num_blocks,
                    "filter_bytes": w.filter_bytes, "n_insert": w.n_insert,
+                   "launch": "eager" if args.eager else "CUDA graph of the step",
                    "n_lookup": w.n_lookup, "member_frac": w.member_frac,
                    "l2": "inputs larger than L2 (%.1f GiB lookup stream per step)"
                          % (8 * w.n_lookup / 2**30),

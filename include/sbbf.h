@@ -203,7 +203,7 @@ typedef struct sbbf_request {
 
 typedef struct sbbf_server_stats {
   uint64_t windows, launches, phases, requests, keys;
-  uint64_t admissions, evictions, admission_waits;
+  uint64_t admissions, evictions, writebacks, admission_waits;
   uint64_t resident_bytes;
 } sbbf_server_stats_t;
 

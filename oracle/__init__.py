@@ -61,6 +61,7 @@ def lib():
                 "oracle_seeds": (None, [P32]),
                 "oracle_insert": (None, [P32, u32, P64, sz]),
                 "oracle_insert_block_range": (None, [P32, u32, P64, sz, u64, u64]),
+                "oracle_insert_block_ranges": (None, [P32, u32, P64, sz, P64, P64, sz]),
                 "oracle_find_one": (i32, [P32, u32, u64]),
                 "oracle_find": (None, [P32, u32, P64, sz, P32]),
                 "oracle_union": (None, [P32, P32, sz]),
@@ -129,6 +130,17 @@ def insert_block_range(sub_words, num_blocks, hashes, lo, hi):
     lib().oracle_insert_block_range(_u32p(sub_words), num_blocks, _u64p(h),
                                     h.size, lo, hi)
     return sub_words
+
+
+def insert_block_ranges(out_words, num_blocks, hashes, lo, hi):
+    """Blocks of sorted disjoint ranges [lo[r], hi[r]) after inserting hashes,
+    ORed into out_words (the ranges' blocks one after another)."""
+    h = _c_u64(hashes)
+    lo_, hi_ = _c_u64(lo), _c_u64(hi)
+    assert out_words.dtype == np.uint32 and out_words.size == 8 * int((hi_ - lo_).sum())
+    lib().oracle_insert_block_ranges(_u32p(out_words), num_blocks, _u64p(h), h.size,
+                                     _u64p(lo_), _u64p(hi_), lo_.size)
+    return out_words
 
 
 def find_one(words, num_blocks, h) -> bool:

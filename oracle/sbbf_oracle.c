@@ -87,6 +87,35 @@ void oracle_insert_block_range(uint32_t *sub_words, uint32_t num_blocks,
   }
 }
 
+/* add_hash restricted to several sorted, disjoint block ranges; the output
+ * holds the ranges' blocks one after another. */
+void oracle_insert_block_ranges(uint32_t *out_words, uint32_t num_blocks,
+                                const uint64_t *hashes, size_t n,
+                                const uint64_t *lo, const uint64_t *hi,
+                                size_t n_ranges) {
+  if (n_ranges == 0) return;
+  uint64_t *first = (uint64_t *)malloc(n_ranges * sizeof(uint64_t));
+  uint64_t acc = 0;
+  for (size_t r = 0; r < n_ranges; ++r) {
+    first[r] = acc;
+    acc += hi[r] - lo[r];
+  }
+  for (size_t k = 0; k < n; ++k) {
+    uint64_t b = oracle_block_index(hashes[k], num_blocks);
+    if (b < lo[0]) continue;
+    size_t a = 0, z = n_ranges; /* last r with lo[r] <= b: in [a, z) */
+    while (z - a > 1) {
+      size_t mid = (a + z) / 2;
+      if (lo[mid] <= b) a = mid; else z = mid;
+    }
+    if (b >= hi[a]) continue;
+    uint32_t mask[8];
+    oracle_make_mask((uint32_t)hashes[k], mask);
+    for (int i = 0; i < 8; ++i) out_words[8 * (first[a] + b - lo[a]) + i] |= mask[i];
+  }
+  free(first);
+}
+
 /* Appendix, find_hash: true iff (~block & mask) == 0, i.e. every lane's mask
  * bit is set in the block. */
 int oracle_find_one(const uint32_t *words, uint32_t num_blocks,

@@ -46,6 +46,13 @@ void oracle_insert_block_range(uint32_t *sub_words, uint32_t num_blocks,
                                const uint64_t *hashes, size_t n,
                                uint64_t lo, uint64_t hi);
 
+/* add_hash restricted to n_ranges sorted, disjoint block ranges
+ * [lo[r], hi[r]); out_words holds the ranges' blocks one after another. */
+void oracle_insert_block_ranges(uint32_t *out_words, uint32_t num_blocks,
+                                const uint64_t *hashes, size_t n,
+                                const uint64_t *lo, const uint64_t *hi,
+                                size_t n_ranges);
+
 /* Appendix figure, find_hash for one hash: 1 iff every mask bit is set. */
 int oracle_find_one(const uint32_t *words, uint32_t num_blocks, uint64_t hash);
 

@@ -156,6 +156,8 @@ struct FilterState {
   uint32_t* d_words = nullptr;  // device copy while resident
   uint32_t* h_words = nullptr;  // pinned host copy after an eviction
   bool written = false;         // ever inserted into
+  bool host_valid = false;      // h_words equals the current contents
+  uint64_t pending = 0;         // queued requests not yet in a window
   uint64_t last_use = 0;        // window sequence number of its last use
   uint64_t bytes() const { return static_cast<uint64_t>(num_blocks) * 32; }
 };
@@ -207,7 +209,7 @@ namespace {
 // memory; both stream-ordered after all earlier work.
 sbbf_status evict(sbbf_server_t* s, uint32_t f) {
   FilterState& st = s->filters[f];
-  if (st.written) {
+  if (st.written && !st.host_valid) {  // write back only what changed since admission
     if (!st.h_words) {
       cudaError_t e = cudaMallocHost(&st.h_words, st.bytes());
       if (e != cudaSuccess) {
@@ -217,6 +219,8 @@ sbbf_status evict(sbbf_server_t* s, uint32_t f) {
     }
     SBBF_CUDA(cudaMemcpyAsync(st.h_words, st.d_words, st.bytes(), cudaMemcpyDeviceToHost,
                               s->stream));
+    st.host_valid = true;
+    ++s->stats.writebacks;
   }
   SBBF_CUDA(cudaFreeAsync(st.d_words, s->stream));
   st.d_words = nullptr;
@@ -234,6 +238,7 @@ sbbf_status admit(sbbf_server_t* s, uint32_t f) {
     return SBBF_ENOMEM;
   }
   if (st.written && st.h_words) {
+    // host_valid holds: the host copy was written back at the last eviction
     SBBF_CUDA(cudaMemcpyAsync(st.d_words, st.h_words, st.bytes(), cudaMemcpyHostToDevice,
                               s->stream));
   } else {
@@ -253,11 +258,21 @@ sbbf_status make_resident(sbbf_server_t* s, uint32_t f, uint64_t extra,
   FilterState& st = s->filters[f];
   const uint64_t need = (st.d_words ? 0 : st.bytes()) + extra;
   while (s->resident_bytes + s->inflight_bytes + need > s->cfg.budget_bytes) {
+    // Least recently used resident filter outside the forming window,
+    // preferring filters with no queued requests (they will not be needed
+    // back soon).
     int victim = -1;
     for (size_t i = 0; i < s->filters.size(); ++i) {
       const FilterState& c = s->filters[i];
       if (!c.d_words || in_window[i] || i == f) continue;
-      if (victim < 0 || c.last_use < s->filters[victim].last_use) victim = static_cast<int>(i);
+      if (victim < 0) {
+        victim = static_cast<int>(i);
+        continue;
+      }
+      const FilterState& v = s->filters[victim];
+      const bool c_idle = c.pending == 0, v_idle = v.pending == 0;
+      if ((c_idle && !v_idle) || (c_idle == v_idle && c.last_use < v.last_use))
+        victim = static_cast<int>(i);
     }
     if (victim < 0) return SBBF_EBUSY;
     sbbf_status rc = evict(s, static_cast<uint32_t>(victim));
@@ -310,6 +325,7 @@ sbbf_status launch_window(sbbf_server_t* s, bool* launched) {
     in_window[f] = 1;
     keys += p.req.n;
     bytes += p.dev_bytes;
+    --s->filters[f].pending;
     taken.push_back(p);
     it = s->pending.erase(it);
   }
@@ -326,7 +342,10 @@ sbbf_status launch_window(sbbf_server_t* s, bool* launched) {
     phase[i] = phase_of[f];
     n_phases = std::max(n_phases, phase[i] + 1);
     s->filters[f].last_use = seq;
-    if (taken[i].req.op == SBBF_OP_INSERT) s->filters[f].written = true;
+    if (taken[i].req.op == SBBF_OP_INSERT) {
+      s->filters[f].written = true;
+      s->filters[f].host_valid = false;
+    }
   }
   std::vector<size_t> order(taken.size());
   for (size_t i = 0; i < order.size(); ++i) order[i] = i;
@@ -535,7 +554,10 @@ sbbf_status sbbf_server_submit(sbbf_server_t* s, const sbbf_request_t* r, uint64
     p.ticket = s->done_ns.size();
     s->done_ns.push_back(r->n == 0 ? now_ns() : 0);
     s->status.push_back(SBBF_OK);
-    if (r->n > 0) s->pending.push_back(p);
+    if (r->n > 0) {
+      s->pending.push_back(p);
+      ++s->filters[r->filter].pending;
+    }
     *ticket = p.ticket;
   }
   s->cv.notify_all();
@@ -599,6 +621,7 @@ sbbf_status sbbf_server_prefill(sbbf_server_t* s, uint32_t id, const uint64_t* d
   if (rc != SBBF_OK) return rc;
   FilterState& f = s->filters[id];
   f.written = true;
+  f.host_valid = false;
   f.last_use = ++s->window_seq;
   rc = launch_insert(f.d_words, f.num_blocks, d_hashes, n, s->stream);
   if (rc != SBBF_OK) return rc;
@@ -693,6 +716,7 @@ sbbf_status sbbf_server_replay_serial(sbbf_server_t* s, const sbbf_request_t* re
     if (r.n) {
       if (r.op == SBBF_OP_INSERT) {
         f.written = true;
+        f.host_valid = false;
         rc = launch_insert(f.d_words, f.num_blocks, r.d_hashes, r.n, s->stream);
       } else {
         rc = launch_find(f.d_words, f.num_blocks, r.d_hashes, r.n, r.d_out_bits, s->stream);

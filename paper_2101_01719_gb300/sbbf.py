@@ -468,7 +468,8 @@ class _Request(_c.Structure):
 
 class _Stats(_c.Structure):
     _fields_ = [(k, _u64) for k in ("windows", "launches", "phases", "requests", "keys",
-                                    "admissions", "evictions", "admission_waits",
+                                    "admissions", "evictions", "writebacks",
+                                    "admission_waits",
                                     "resident_bytes")]
 
 

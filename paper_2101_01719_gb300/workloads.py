@@ -67,7 +67,12 @@ C2_11BPK = SingleFilterWorkload("sbbf_128906250blk_3G_ins_1G_lookup", 22,
                                 math.ceil(3_000_000_000 * 11 / 256), 3_000_000_000,
                                 256 * 2**20, 1_000_000_000, 0.1)
 
-WORKLOADS = {w.name: w for w in (C0, C1, C2, C2_BIG, C2_11BPK)}
+# The 134,217,728-byte filter with a 64M-lookup batch: a profiling-sized case
+# (about 1.5 GB on the device) of the same kernels.
+C2_PROFILE = SingleFilterWorkload("sbbf_4194304blk_100M_ins_64M_lookup", 2, 4_194_304,
+                                  100_000_000, 16_000_000, 64 * 2**20, 0.1)
+
+WORKLOADS = {w.name: w for w in (C0, C1, C2, C2_BIG, C2_11BPK, C2_PROFILE)}
 
 
 def gen_inserts(w: SingleFilterWorkload, start: int, n: int, out: torch.Tensor | None = None,

@@ -255,6 +255,19 @@ def test_block_range_insert_tiles_the_filter():
         assert np.array_equal(sub, full[8 * lo: 8 * hi])
 
 
+def test_block_ranges_insert_equals_full_insert():
+    B = 5003
+    keys = inp.stream(23, 0, 60000)
+    full = oracle.new_filter(B)
+    oracle.insert(full, B, keys)
+    lo = np.array([0, 7, 100, 2500, 4990], np.uint64)
+    hi = np.array([3, 8, 160, 3000, 5003], np.uint64)
+    out = np.zeros(8 * int((hi - lo).sum()), np.uint32)
+    oracle.insert_block_ranges(out, B, keys, lo, hi)
+    expect = np.concatenate([full[8 * int(a): 8 * int(b)] for a, b in zip(lo, hi)])
+    assert np.array_equal(out, expect)
+
+
 # ---- several filters in one arena -------------------------------------------
 
 def test_multi_filter_equals_separate_filters():
