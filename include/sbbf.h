@@ -118,6 +118,24 @@ sbbf_status sbbf_clear(sbbf_t *f, sbbf_stream_t stream);
 sbbf_status sbbf_insert_hashes(sbbf_t *f, const uint64_t *d_hashes, size_t n,
                                sbbf_stream_t stream);
 
+/* How sbbf_insert_hashes processes a batch.  Partitioned: the hashes are
+ * first grouped by filter slice (2^20 consecutive blocks) into a scratch
+ * buffer, then inserted slice by slice with each slice prefetched into L2,
+ * which turns random DRAM accesses into L2 hits for filters larger than L2;
+ * the filter is identical either way (OR commutes).  The scratch, 8 * n
+ * bytes plus 24 bytes per slice, is allocated with cudaMalloc (synchronous)
+ * when a batch needs more than the filter holds, kept by the filter and
+ * freed by sbbf_destroy; partitioned calls on one filter must therefore be
+ * ordered on one stream.
+ *   SBBF_PARTITION_AUTO (default): partition batches of at least 4Mi hashes
+ *     into filters of at least 256 MiB; if the scratch cannot be allocated,
+ *     insert unpartitioned;
+ *   SBBF_PARTITION_OFF: never partition;
+ *   SBBF_PARTITION_ON: always partition (SBBF_ENOMEM if no scratch).
+ * Errors: SBBF_EINVAL (NULL filter or unknown mode). */
+enum { SBBF_PARTITION_AUTO = 0, SBBF_PARTITION_OFF = 1, SBBF_PARTITION_ON = 2 };
+sbbf_status sbbf_set_partitioning(sbbf_t *f, int mode);
+
 /* Look up d_hashes[0..n) (appendix find_hash for each) into the packed
  * bitmask d_out_bits of (n + 31) / 32 words (caller-owned, 4-byte aligned).
  * Errors as sbbf_insert_hashes; d_out_bits NULL with n > 0 is SBBF_EINVAL. */
@@ -430,12 +448,15 @@ sbbf_status sbbf_multi_invalid_count(sbbf_multi_t *m, uint64_t *count,
                                      sbbf_stream_t stream);
 
 /* Launch shape used for (op, form): CTA size (128/256/512), lanes per key
- * (1 or 8) and loads in flight per warp (1/2/4).  Shapes never change
- * results, only speed. */
+ * (1 or 8), loads in flight per warp (1/2/4) and, for lookups, whether block
+ * loads bypass L1 allocation (0/1; ignored for inserts).  Shapes never
+ * change results, only speed. */
 sbbf_status sbbf_multi_get_tuning(const sbbf_multi_t *m, int op, int form,
-                                  int *threads, int *lanes, int *unroll);
+                                  int *threads, int *lanes, int *unroll,
+                                  int *l1_bypass);
 sbbf_status sbbf_multi_set_tuning(sbbf_multi_t *m, int op, int form,
-                                  int threads, int lanes, int unroll);
+                                  int threads, int lanes, int unroll,
+                                  int l1_bypass);
 
 /* Autotune (op, form) on a prefix (at most 2^24 keys) of a real batch:
  * every candidate shape runs on the sample, its result (lookup bits, or the

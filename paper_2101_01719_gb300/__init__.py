@@ -9,6 +9,9 @@ from .sbbf import (  # noqa: F401
     FORM_TAGGED,
     OP_FIND,
     OP_INSERT,
+    PARTITION_AUTO,
+    PARTITION_OFF,
+    PARTITION_ON,
     Filter,
     HostPipe,
     MultiFilter,

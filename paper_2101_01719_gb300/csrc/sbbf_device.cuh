@@ -103,6 +103,24 @@ __device__ __forceinline__ void load_block(const uint32_t* p, uint64_t pol,
       : "l"(p), "l"(pol));
 }
 
+// The same load without allocating in L1: for filters much larger than L1 the
+// L1 tag/fill work only costs data-pipe cycles.
+__device__ __forceinline__ void load_block_na(const uint32_t* p, uint64_t pol,
+                                              uint32_t w[8]) {
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], %9;"
+      : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]),
+        "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+      : "l"(p), "l"(pol));
+}
+
+__device__ __forceinline__ uint32_t load_word_na(const uint32_t* p, uint64_t pol) {
+  uint32_t w;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;"
+      : "=r"(w)
+      : "l"(p), "l"(pol));
+  return w;
+}
+
 // One 32-bit lane word of a block.
 __device__ __forceinline__ uint32_t load_word(const uint32_t* p, uint64_t pol) {
   uint32_t w;

@@ -60,4 +60,7 @@ struct sbbf_filter {
   uint32_t num_blocks;
   int device;
   int owns;             // 1: allocated by the library
+  int partition_mode;   // SBBF_PARTITION_*
+  void *scratch;        // partitioned-insert scratch (library-owned), or NULL
+  size_t scratch_bytes;
 };

@@ -209,48 +209,69 @@ struct UnitIter {
 
 // ---- insert ----------------------------------------------------------------
 
+// Inserts the 64-hash group g with eight lanes per key: in 16 rounds each
+// group of eight lanes takes one key and lane j ORs lane j's mask bit into
+// word j of the key's block.
+template <class R>
+__device__ __forceinline__ void insert_group8(uint32_t* __restrict__ words, R& res,
+                                              const uint64_t* __restrict__ hashes, uint64_t n,
+                                              bool vec, uint64_t pol, uint64_t g) {
+  const unsigned lane = lane_id();
+  const uint32_t seed = lane_seed(lane & 7);
+  uint32_t* const word_j = words + (lane & 7);
+  const int group_base = static_cast<int>(lane & ~7u);
+  const uint64_t k = g * 64 + 2 * lane;
+  uint64_t h0, h1;
+  load_pair(hashes, k, n, vec, pol, h0, h1);
+  res.begin_chunk(g * 64);
+  const uint64_t b0 = k < n ? res.block(k, h0) : kNoBlock64;
+  const uint64_t b1 = k + 1 < n ? res.block(k + 1, h1) : kNoBlock64;
+  const uint32_t x0 = static_cast<uint32_t>(h0), x1 = static_cast<uint32_t>(h1);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int src = group_base + (r >> 1);
+    const uint32_t x = __shfl_sync(0xFFFFFFFFu, (r & 1) ? x1 : x0, src);
+    const uint64_t b = __shfl_sync(0xFFFFFFFFu, (r & 1) ? b1 : b0, src);
+    if (b != kNoBlock64) red_or(word_j + 8ull * b, 1u << bit_index(x, seed));
+  }
+}
+
+// The same group with one lane per key: four red.or.b64 per key.
+template <class R>
+__device__ __forceinline__ void insert_group1(uint32_t* __restrict__ words, R& res,
+                                              const uint64_t* __restrict__ hashes, uint64_t n,
+                                              bool vec, uint64_t pol, uint64_t g) {
+  const unsigned lane = lane_id();
+  const uint64_t k = g * 64 + 2 * lane;
+  uint64_t h0, h1;
+  load_pair(hashes, k, n, vec, pol, h0, h1);
+  res.begin_chunk(g * 64);
+  const uint64_t b0 = k < n ? res.block(k, h0) : kNoBlock64;
+  const uint64_t b1 = k + 1 < n ? res.block(k + 1, h1) : kNoBlock64;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const uint64_t b = s ? b1 : b0;
+    const uint32_t x = static_cast<uint32_t>(s ? h1 : h0);
+    if (b == kNoBlock64) continue;
+    unsigned long long* p = reinterpret_cast<unsigned long long*>(words + 8ull * b);
+    red_or64(p + 0, mask_pair(x, SBBF_SEED0, SBBF_SEED1));
+    red_or64(p + 1, mask_pair(x, SBBF_SEED2, SBBF_SEED3));
+    red_or64(p + 2, mask_pair(x, SBBF_SEED4, SBBF_SEED5));
+    red_or64(p + 3, mask_pair(x, SBBF_SEED6, SBBF_SEED7));
+  }
+}
+
 template <class R, bool kLanes8>
 __global__ void __launch_bounds__(kMaxThreads)
     insert_kernel(uint32_t* __restrict__ words, R res, const uint64_t* __restrict__ hashes,
                   uint64_t n, unsigned long long* __restrict__ tiles) {
-  const unsigned lane = lane_id();
   const uint64_t n_groups = (n + 63) >> 6;
   const uint64_t pol = policy_evict_first();
   const bool vec = (reinterpret_cast<uintptr_t>(hashes) & 15) == 0;
-  const uint32_t seed = lane_seed(lane & 7);
-  uint32_t* const word_j = words + (lane & 7);
-  const int group_base = static_cast<int>(lane & ~7u);
-
   UnitIter it(n_groups, tiles);
   for (uint64_t g; it.next(g);) {
-    const uint64_t k = g * 64 + 2 * lane;
-    uint64_t h0, h1;
-    load_pair(hashes, k, n, vec, pol, h0, h1);
-    res.begin_chunk(g * 64);
-    const uint64_t b0 = k < n ? res.block(k, h0) : kNoBlock64;
-    const uint64_t b1 = k + 1 < n ? res.block(k + 1, h1) : kNoBlock64;
-    if (kLanes8) {
-      const uint32_t x0 = static_cast<uint32_t>(h0), x1 = static_cast<uint32_t>(h1);
-#pragma unroll
-      for (int r = 0; r < 16; ++r) {
-        const int src = group_base + (r >> 1);
-        const uint32_t x = __shfl_sync(0xFFFFFFFFu, (r & 1) ? x1 : x0, src);
-        const uint64_t b = __shfl_sync(0xFFFFFFFFu, (r & 1) ? b1 : b0, src);
-        if (b != kNoBlock64) red_or(word_j + 8ull * b, 1u << bit_index(x, seed));
-      }
-    } else {
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        const uint64_t b = s ? b1 : b0;
-        const uint32_t x = static_cast<uint32_t>(s ? h1 : h0);
-        if (b == kNoBlock64) continue;
-        unsigned long long* p = reinterpret_cast<unsigned long long*>(words + 8ull * b);
-        red_or64(p + 0, mask_pair(x, SBBF_SEED0, SBBF_SEED1));
-        red_or64(p + 1, mask_pair(x, SBBF_SEED2, SBBF_SEED3));
-        red_or64(p + 2, mask_pair(x, SBBF_SEED4, SBBF_SEED5));
-        red_or64(p + 3, mask_pair(x, SBBF_SEED6, SBBF_SEED7));
-      }
-    }
+    if (kLanes8) insert_group8(words, res, hashes, n, vec, pol, g);
+    else insert_group1(words, res, hashes, n, vec, pol, g);
   }
   res.finish();
 }
@@ -266,10 +287,11 @@ constexpr int find_min_blocks(bool lanes8, int unroll) {
   return (lanes8 || unroll >= 4) ? 1 : R::kMinBlocks;
 }
 
-template <class R, bool kLanes8, int U>
+template <class R, bool kLanes8, int U, bool kL1Bypass>
 __global__ void __launch_bounds__(kMaxThreads, find_min_blocks<R>(kLanes8, U))
     find_kernel(const uint32_t* __restrict__ words, R res, const uint64_t* __restrict__ hashes,
                 uint64_t n, uint32_t* __restrict__ out, unsigned long long* __restrict__ tiles) {
+  constexpr bool l1_bypass = kL1Bypass;  // block loads skip L1 allocation
   const unsigned lane = lane_id();
   const uint64_t n_groups = (n + 63) >> 6;
   const uint64_t n_out = (n + 31) >> 5;
@@ -302,7 +324,8 @@ __global__ void __launch_bounds__(kMaxThreads, find_min_blocks<R>(kLanes8, U))
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
           if (b[u][s] != kNoBlock64) {
-            load_block(words + 8ull * b[u][s], pf, w[u][s]);
+            if (l1_bypass) load_block_na(words + 8ull * b[u][s], pf, w[u][s]);
+            else load_block(words + 8ull * b[u][s], pf, w[u][s]);
           } else {
 #pragma unroll
             for (int i = 0; i < 8; ++i) w[u][s][i] = 0;
@@ -345,7 +368,9 @@ __global__ void __launch_bounds__(kMaxThreads, find_min_blocks<R>(kLanes8, U))
           xv[u] = __shfl_sync(0xFFFFFFFFu, static_cast<uint32_t>((r & 1) ? h1 : h0), src);
           const uint64_t bb = __shfl_sync(0xFFFFFFFFu, (r & 1) ? b1 : b0, src);
           ok[u] = bb != kNoBlock64;
-          wv[u] = ok[u] ? load_word(words + 8ull * bb + j, pf) : 0u;
+          wv[u] = !ok[u] ? 0u
+                  : l1_bypass ? load_word_na(words + 8ull * bb + j, pf)
+                              : load_word(words + 8ull * bb + j, pf);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {

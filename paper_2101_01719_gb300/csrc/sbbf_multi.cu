@@ -90,10 +90,11 @@ std::vector<Tuning> candidates(int op) {
   std::vector<Tuning> c;
   for (int threads : {128, 256, 512}) {
     if (op == 0) {
-      for (int lanes : {8, 1}) c.push_back(Tuning{threads, lanes, 1});
+      for (int lanes : {8, 1}) c.push_back(Tuning{threads, lanes, 1, 0});
     } else {
       for (int lanes : {1, 8})
-        for (int unroll : {1, 2, 4}) c.push_back(Tuning{threads, lanes, unroll});
+        for (int unroll : {1, 2, 4})
+          for (int l1 : {0, 1}) c.push_back(Tuning{threads, lanes, unroll, l1});
     }
   }
   return c;
@@ -353,7 +354,9 @@ sbbf_status sbbf_multi_find_each(const sbbf_multi_t* m, const uint64_t* d_hashes
     const uint64_t cnt = h_offsets[t + 1] - h_offsets[t];
     if (cnt == 0) continue;
     if (h_offsets[t] % 32) return SBBF_EINVAL;  // each filter's answers start a fresh word
-    sbbf_status st = launch_find_t(kDefaultFind, m->words + 8 * m->h_dir[t].base,
+    Tuning tf = kDefaultFind;
+    tf.l1_bypass = static_cast<uint64_t>(m->h_dir[t].num_blocks) * 32 > kL1BypassBytes;
+    sbbf_status st = launch_find_t(tf, m->words + 8 * m->h_dir[t].base,
                                    OneFilter{m->h_dir[t].num_blocks}, d_hashes + h_offsets[t], cnt,
                                    d_out_bits + h_offsets[t] / 32, stream);
     if (st != SBBF_OK) return st;
@@ -372,7 +375,7 @@ sbbf_status sbbf_multi_invalid_count(sbbf_multi_t* m, uint64_t* count, sbbf_stre
 }
 
 sbbf_status sbbf_multi_get_tuning(const sbbf_multi_t* m, int op, int form, int* threads,
-                                  int* lanes, int* unroll) {
+                                  int* lanes, int* unroll, int* l1_bypass) {
   if (!m || (op != SBBF_OP_INSERT && op != SBBF_OP_FIND) ||
       (form != SBBF_FORM_SEGMENTS && form != SBBF_FORM_TAGGED))
     return SBBF_EINVAL;
@@ -382,12 +385,13 @@ sbbf_status sbbf_multi_get_tuning(const sbbf_multi_t* m, int op, int form, int* 
   if (threads) *threads = t.threads;
   if (lanes) *lanes = t.lanes;
   if (unroll) *unroll = t.unroll;
+  if (l1_bypass) *l1_bypass = t.l1_bypass;
   return SBBF_OK;
 }
 
 sbbf_status sbbf_multi_set_tuning(sbbf_multi_t* m, int op, int form, int threads, int lanes,
-                                  int unroll) {
-  const Tuning t{threads, lanes, unroll};
+                                  int unroll, int l1_bypass) {
+  const Tuning t{threads, lanes, unroll, l1_bypass};
   if (!m || !tuning_valid(t) || (op != SBBF_OP_INSERT && op != SBBF_OP_FIND) ||
       (form != SBBF_FORM_SEGMENTS && form != SBBF_FORM_TAGGED))
     return SBBF_EINVAL;

@@ -160,10 +160,10 @@ extern "C" sbbf_status sbbf_multi_find_noalloc(const uint32_t* d_arena,
   st = launch_status();
   if (st != SBBF_OK) return st;
   if (n > 0) {
-    auto kernel = find_kernel<TaggedDeviceDir, false, 2>;
+    auto kernel = find_kernel<TaggedDeviceDir, false, 2, false>;
     static const int occ = [] {
       int v = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, find_kernel<TaggedDeviceDir, false, 2>,
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, find_kernel<TaggedDeviceDir, false, 2, false>,
                                                         256, 0) != cudaSuccess ||
           v < 1)
         v = 1;

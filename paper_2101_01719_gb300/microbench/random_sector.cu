@@ -48,6 +48,39 @@ __device__ __forceinline__ void load32(const uint32_t* p, uint32_t w[8]) {
                : "l"(p));
 }
 
+// Cache-path variants of the same 256-bit load: 0 = ld.global.nc (L1
+// allocating), 1 = ld.global.nc.L1::no_allocate, 2 = ld.global.cg (L2 only).
+template <int kPath>
+__device__ __forceinline__ void load32v(const uint32_t* p, uint32_t w[8]) {
+  if (kPath == 1) {
+    asm volatile("ld.global.nc.L1::no_allocate.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]),
+                   "=r"(w[6]), "=r"(w[7])
+                 : "l"(p));
+  } else if (kPath == 2) {
+    asm volatile("ld.global.cg.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]),
+                   "=r"(w[6]), "=r"(w[7])
+                 : "l"(p));
+  } else {
+    load32(p, w);
+  }
+}
+
+template <int U, int kPath>
+__global__ void read32p(const uint32_t* __restrict__ f, uint32_t nblk, int iters, uint32_t* out) {
+  const uint64_t t = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+  uint32_t acc = 0;
+  for (int i = 0; i < iters; ++i) {
+    uint32_t w[U][8];
+#pragma unroll
+    for (int u = 0; u < U; ++u) load32v<kPath>(f + 8ull * draw(t, i * U + u, nblk), w[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc ^= w[u][0] ^ w[u][7];
+  }
+  if (acc == 0x12345678u) out[0] = acc;
+}
+
 template <int U>
 __global__ void read32(const uint32_t* __restrict__ f, uint32_t nblk, int iters, uint32_t* out) {
   const uint64_t t = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
@@ -168,6 +201,25 @@ int main() {
     n = static_cast<double>(grid) * threads / 8 * 128;
     std::printf("red8   %10.1f MiB: %7.1f G blocks/s (8 x red.or.b32 per block)\n",
                 bytes / 1048576.0, n / ms / 1e6);
+  }
+  // cache-path variants on an L2-resident 1 MiB buffer
+  {
+    const uint32_t nblk = 32768;
+    const int threads = 256, grid = sms * 8;
+    const char* names[3] = {"nc (L1 alloc)", "nc L1::no_allocate", "cg (L2 only)"};
+    for (int path = 0; path < 3; ++path) {
+      for (int rep = 0; rep < 2; ++rep) {
+        CK(cudaEventRecord(a));
+        if (path == 0) read32p<4, 0><<<grid, threads>>>(f, nblk, 64, out);
+        if (path == 1) read32p<4, 1><<<grid, threads>>>(f, nblk, 64, out);
+        if (path == 2) read32p<4, 2><<<grid, threads>>>(f, nblk, 64, out);
+        CK(cudaEventRecord(b));
+        CK(cudaEventSynchronize(b));
+      }
+      CK(cudaEventElapsedTime(&ms, a, b));
+      const double n = static_cast<double>(grid) * threads * 64 * 4;
+      std::printf("read32 1 MiB, %-20s: %7.1f G blocks/s\n", names[path], n / ms / 1e6);
+    }
   }
   // shared memory (128 KiB per CTA) and distributed shared memory clusters
   const uint32_t snblk = 4096;

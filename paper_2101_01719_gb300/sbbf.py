@@ -43,6 +43,7 @@ SIGNATURES = {
     "sbbf_device_words": (_int, [_P, _c.POINTER(_P), _c.POINTER(_sz)]),
     "sbbf_clear": (_int, [_P, _P]),
     "sbbf_insert_hashes": (_int, [_P, _P, _sz, _P]),
+    "sbbf_set_partitioning": (_int, [_P, _int]),
     "sbbf_find_hashes": (_int, [_P, _P, _sz, _P, _P]),
     "sbbf_union": (_int, [_P, _P, _P]),
     "sbbf_copy_to_host": (_int, [_P, _P, _sz, _P]),
@@ -70,8 +71,8 @@ SIGNATURES = {
     "sbbf_multi_find_each": (_int, [_P, _P, _P, _P, _P]),
     "sbbf_multi_invalid_count": (_int, [_P, _c.POINTER(_u64), _P]),
     "sbbf_multi_get_tuning": (_int, [_P, _int, _int, _c.POINTER(_int), _c.POINTER(_int),
-                                     _c.POINTER(_int)]),
-    "sbbf_multi_set_tuning": (_int, [_P, _int, _int, _int, _int, _int]),
+                                     _c.POINTER(_int), _c.POINTER(_int)]),
+    "sbbf_multi_set_tuning": (_int, [_P, _int, _int, _int, _int, _int, _int]),
     "sbbf_multi_tune": (_int, [_P, _int, _int, _P, _P, _sz, _P, _c.POINTER(_c.c_float)]),
     "sbbf_multi_graph_create": (_int, [_P, _c.POINTER(_P)]),
     "sbbf_multi_graph_destroy": (_int, [_P]),
@@ -93,6 +94,7 @@ SIGNATURES = {
 
 OP_INSERT, OP_FIND = 0, 1
 FORM_SEGMENTS, FORM_TAGGED = 0, 1
+PARTITION_AUTO, PARTITION_OFF, PARTITION_ON = 0, 1, 2
 
 
 class SbbfError(RuntimeError):
@@ -184,6 +186,11 @@ class Filter:
     def clear(self, stream=None):
         with torch.cuda.device(self.device):
             check(lib().sbbf_clear(self._h, stream_handle(stream)), "sbbf_clear")
+        return self
+
+    def set_partitioning(self, mode: int):
+        """PARTITION_AUTO / PARTITION_OFF / PARTITION_ON (see sbbf.h)."""
+        check(lib().sbbf_set_partitioning(self._h, mode), "sbbf_set_partitioning")
         return self
 
     def insert(self, hashes: torch.Tensor, stream=None):
@@ -413,13 +420,14 @@ class MultiFilter:
         return int(v.value)
 
     def get_tuning(self, op: int, form: int):
-        t, l, u = _int(), _int(), _int()
+        t, l, u, b = _int(), _int(), _int(), _int()
         check(lib().sbbf_multi_get_tuning(self._h, op, form, _c.byref(t), _c.byref(l),
-                                          _c.byref(u)), "sbbf_multi_get_tuning")
-        return {"threads": t.value, "lanes": l.value, "unroll": u.value}
+                                          _c.byref(u), _c.byref(b)), "sbbf_multi_get_tuning")
+        return {"threads": t.value, "lanes": l.value, "unroll": u.value, "l1_bypass": b.value}
 
-    def set_tuning(self, op: int, form: int, threads: int, lanes: int, unroll: int):
-        check(lib().sbbf_multi_set_tuning(self._h, op, form, threads, lanes, unroll),
+    def set_tuning(self, op: int, form: int, threads: int, lanes: int, unroll: int,
+                   l1_bypass: int = 0):
+        check(lib().sbbf_multi_set_tuning(self._h, op, form, threads, lanes, unroll, l1_bypass),
               "sbbf_multi_set_tuning")
 
     def tune(self, op: int, hashes, ids=None, offsets=None, stream=None) -> float:

@@ -59,13 +59,13 @@ C1 = SingleFilterWorkload("sbbf_32768blk_1M_ins_256M_lookup", 1, 32768, 1_000_00
 # 100M hashes into 4,194,304 blocks (134,217,728 B) in 16M batches; 1B lookups, 10% members.
 C2 = SingleFilterWorkload("sbbf_4194304blk_100M_ins_1G_lookup", 2, 4_194_304, 100_000_000,
                           16_000_000, 1_000_000_000, 0.1)
-# 3B hashes into 2^30 blocks (32 GiB); 1B lookups, 10% members.
+# 3B hashes into 2^30 blocks (32 GiB) in one batch; 1B lookups, 10% members.
 C2_BIG = SingleFilterWorkload("sbbf_2^30blk_3G_ins_1G_lookup", 12, 2**30, 3_000_000_000,
-                              256 * 2**20, 1_000_000_000, 0.1)
-# 3B hashes at 11 bits/key: 128,906,250 blocks (4.125 GB).
+                              3_000_000_000, 1_000_000_000, 0.1)
+# 3B hashes at 11 bits/key: 128,906,250 blocks (4.125 GB), one batch.
 C2_11BPK = SingleFilterWorkload("sbbf_128906250blk_3G_ins_1G_lookup", 22,
                                 math.ceil(3_000_000_000 * 11 / 256), 3_000_000_000,
-                                256 * 2**20, 1_000_000_000, 0.1)
+                                3_000_000_000, 1_000_000_000, 0.1)
 
 # The 134,217,728-byte filter with a 64M-lookup batch: a profiling-sized case
 # (about 1.5 GB on the device) of the same kernels.

@@ -140,9 +140,10 @@ def test_every_launch_shape_is_bit_exact(form):
             m2.insert(ins, **kw_i)
             assert np.array_equal(m2.to_numpy(), ref_words), (threads, lanes)
             for unroll in (1, 2, 4):
-                m.set_tuning(sb.OP_FIND, form, threads, lanes, unroll)
-                got = bits_np(m.find(q, **kw_q))
-                assert np.array_equal(got, ref_bits), (threads, lanes, unroll)
+                for l1 in (0, 1):
+                    m.set_tuning(sb.OP_FIND, form, threads, lanes, unroll, l1)
+                    got = bits_np(m.find(q, **kw_q))
+                    assert np.array_equal(got, ref_bits), (threads, lanes, unroll, l1)
     with pytest.raises(sb.SbbfError):
         m.set_tuning(sb.OP_FIND, form, 96, 1, 1)
 
@@ -161,6 +162,7 @@ def test_autotuner_picks_a_verified_shape_and_leaves_filters_alone():
     for op, ms in ((sb.OP_INSERT, ms_i), (sb.OP_FIND, ms_f)):
         t = m.get_tuning(op, sb.FORM_SEGMENTS)
         assert t["threads"] in (128, 256, 512) and t["lanes"] in (1, 8)
+        assert t["l1_bypass"] in (0, 1)
         assert ms > 0 or ms == -1.0
     # a second tune of the same size class is answered from the cache
     assert m.tune(sb.OP_FIND, q, offsets=q_off) == -1.0
