@@ -118,18 +118,21 @@ sbbf_status sbbf_clear(sbbf_t *f, sbbf_stream_t stream);
 sbbf_status sbbf_insert_hashes(sbbf_t *f, const uint64_t *d_hashes, size_t n,
                                sbbf_stream_t stream);
 
-/* How sbbf_insert_hashes processes a batch.  Partitioned: the hashes are
- * first grouped by filter slice (2^20 consecutive blocks) into a scratch
- * buffer, then inserted slice by slice with each slice prefetched into L2,
- * which turns random DRAM accesses into L2 hits for filters larger than L2;
- * the filter is identical either way (OR commutes).  The scratch, 8 * n
- * bytes plus 24 bytes per slice, is allocated with cudaMalloc (synchronous)
- * when a batch needs more than the filter holds, kept by the filter and
- * freed by sbbf_destroy; partitioned calls on one filter must therefore be
- * ordered on one stream.
+/* How sbbf_insert_hashes and sbbf_find_hashes process a batch.
+ * Partitioned: the hashes are first grouped by filter slice (2^20
+ * consecutive blocks) into a scratch buffer, then processed slice by slice
+ * with each slice prefetched into L2, which turns random DRAM accesses into
+ * L2 hits for filters larger than L2.  Results are identical either way
+ * (inserts commute; a lookup's answer is set at its original position).  The
+ * scratch -- 8 bytes per hash for inserts, 12 for lookups (at most 2^31
+ * hashes at a time), plus 24 bytes per slice -- is allocated with cudaMalloc
+ * (synchronous) when a batch needs more than the filter holds, kept by the
+ * filter and freed by sbbf_destroy; partitioned calls on one filter must
+ * therefore be ordered on one stream.
  *   SBBF_PARTITION_AUTO (default): partition batches of at least 4Mi hashes
- *     into filters of at least 256 MiB; if the scratch cannot be allocated,
- *     insert unpartitioned;
+ *     into filters of at least 256 MiB when the batch has at least one hash
+ *     per block (inserts) or two (lookups); if the scratch cannot be
+ *     allocated, run unpartitioned;
  *   SBBF_PARTITION_OFF: never partition;
  *   SBBF_PARTITION_ON: always partition (SBBF_ENOMEM if no scratch).
  * Errors: SBBF_EINVAL (NULL filter or unknown mode). */

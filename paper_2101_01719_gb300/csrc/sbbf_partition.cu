@@ -210,15 +210,17 @@ __device__ __forceinline__ void cta_exclusive_scan(unsigned* vals, uint32_t n, u
 // counted per slice, counting-sorted into shared memory, each slice's run is
 // reserved in the output with one global add, and the sorted tile is written
 // out in order, so consecutive threads write consecutive output positions.
-template <bool kFew>
+template <bool kFew, bool kIndex>
 __global__ void __launch_bounds__(kPartThreads)
     scatter_kernel(const uint64_t* __restrict__ hashes, uint64_t n, uint32_t nb, uint32_t n_slices,
-                   unsigned long long* __restrict__ cursors, uint64_t* __restrict__ out) {
+                   unsigned long long* __restrict__ cursors, uint64_t* __restrict__ out,
+                   uint32_t* __restrict__ out_idx) {
   extern __shared__ unsigned long long smem[];
   uint64_t* s_keys = reinterpret_cast<uint64_t*>(smem);                      // kTileKeys
   unsigned long long* s_gbase = smem + kTileKeys;                             // n_slices
   unsigned* s_cnt = reinterpret_cast<unsigned*>(s_gbase + n_slices);          // n_slices
   unsigned* s_off = s_cnt + n_slices;                                         // n_slices
+  unsigned* s_idx = s_off + n_slices;  // kTileKeys original positions (kIndex)
   __shared__ unsigned warp_sums[32];
   const uint64_t pol = policy_evict_first();
   const bool vec = (reinterpret_cast<uintptr_t>(hashes) & 15) == 0;
@@ -250,14 +252,21 @@ __global__ void __launch_bounds__(kPartThreads)
 #pragma unroll
     for (int i = 0; i < kKeysPerThread; ++i) {
       const unsigned r = rank_warp<kFew>(s_cnt, n_slices, ok[i], p[i]);
-      if (ok[i]) s_keys[s_off[p[i]] + r] = h[i];
+      if (ok[i]) {
+        s_keys[s_off[p[i]] + r] = h[i];
+        if (kIndex)  // tile position of key i of this thread (see load_tile_keys)
+          s_idx[s_off[p[i]] + r] = (i / 2) * 2 * blockDim.x + 2 * threadIdx.x + (i % 2);
+      }
     }
     __syncthreads();
     for (uint32_t j = threadIdx.x; j < m; j += blockDim.x) {
       const uint64_t key = s_keys[j];
       const uint32_t q = slice_of(key, nb);
       const unsigned long long pos = s_gbase[q] + (j - s_off[q]);
-      if (pos < n) out[pos] = key;  // in range unless the input changed between the passes
+      if (pos < n) {  // in range unless the input changed between the passes
+        out[pos] = key;
+        if (kIndex) out_idx[pos] = static_cast<uint32_t>(t0 + s_idx[j]);
+      }
     }
     __syncthreads();
   }
@@ -349,76 +358,214 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Slice-ordered lookups of keys[0..n) (original positions idx[]), with the
+// same tile schedule and distributed prefetch as the sliced insert.  A key
+// found in the filter sets bit idx of `out` (zeroed beforehand) with one
+// atomicOr; misses write nothing.
+__global__ void __launch_bounds__(256)
+    sliced_find_kernel(const uint32_t* __restrict__ words, uint32_t nb,
+                       const uint64_t* __restrict__ keys, const uint32_t* __restrict__ idx,
+                       uint64_t n, const unsigned long long* __restrict__ offsets,
+                       uint32_t n_slices, unsigned long long* __restrict__ tiles,
+                       uint32_t* __restrict__ out) {
+  __shared__ unsigned long long s_tile;
+  const unsigned wpc = blockDim.x >> 5, wic = threadIdx.x >> 5, lane = lane_id();
+  const uint64_t n_groups = (n + 63) >> 6;
+  const uint64_t groups_per_tile = static_cast<uint64_t>(wpc) * kTileRounds;
+  const uint64_t keys_per_tile = groups_per_tile * 64;
+  const uint64_t pk = policy_evict_first();
+  const uint64_t pf = policy_evict_last();
+  const bool vec = (reinterpret_cast<uintptr_t>(keys) & 15) == 0;
+  if (wic == 0) {
+    uint64_t lo, hi, a, b;
+    slice_bytes(nb, 0, lo, hi);
+    share(lo, hi, blockIdx.x, gridDim.x, a, b);
+    prefetch_bytes(words, a, b);
+  }
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(tiles, 1ull);
+    __syncthreads();
+    const uint64_t g0 = s_tile * groups_per_tile;
+    __syncthreads();
+    if (g0 >= n_groups) break;
+    if (wic == 0) {
+      const uint64_t a0 = g0 * 64;
+      uint32_t lo = 0, hi = n_slices;  // last q with offsets[q] <= a0
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (offsets[mid] <= a0) lo = mid; else hi = mid;
+      }
+      const uint64_t q_first = offsets[lo], q_end = offsets[lo + 1];
+      const uint64_t n_tiles_q = (q_end - q_first + keys_per_tile - 1) / keys_per_tile;
+      if (n_tiles_q > 0 && lo + 1 < n_slices) {
+        uint64_t s_lo, s_hi, a, b;
+        slice_bytes(nb, lo + 1, s_lo, s_hi);
+        const uint64_t i = (a0 - q_first) / keys_per_tile;
+        share(s_lo, s_hi, i < n_tiles_q ? i : n_tiles_q - 1, n_tiles_q, a, b);
+        prefetch_bytes(words, a, b);
+      }
+    }
+    for (int r = 0; r < kTileRounds; ++r) {
+      const uint64_t g = g0 + static_cast<uint64_t>(r) * wpc + wic;
+      if (g >= n_groups) continue;
+      const uint64_t k = g * 64 + 2 * lane;
+      uint64_t h0, h1;
+      load_pair(keys, k, n, vec, pk, h0, h1);
+      uint32_t w0[8], w1[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) w0[i] = w1[i] = 0;
+      if (k < n) load_block_na(words + 8ull * block_of(h0, nb), pf, w0);
+      if (k + 1 < n) load_block_na(words + 8ull * block_of(h1, nb), pf, w1);
+      if (k < n && block_has(w0, static_cast<uint32_t>(h0))) {
+        const uint32_t j = idx[k];
+        atomicOr(out + (j >> 5), 1u << (j & 31));
+      }
+      if (k + 1 < n && block_has(w1, static_cast<uint32_t>(h1))) {
+        const uint32_t j = idx[k + 1];
+        atomicOr(out + (j >> 5), 1u << (j & 31));
+      }
+    }
+  }
+}
+
 inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
 
 }  // namespace
 
-// Scratch bytes for a partitioned insert of n keys into num_blocks blocks.
-uint64_t partition_scratch_bytes(uint32_t num_blocks, uint64_t n) {
+// Scratch bytes for a partitioned insert (or, with_index, lookup) of n keys
+// into num_blocks blocks.
+uint64_t partition_scratch_bytes(uint32_t num_blocks, uint64_t n, bool with_index) {
   const uint64_t s = (static_cast<uint64_t>(num_blocks) + (1ull << kSliceShift) - 1) >> kSliceShift;
-  return 3 * align256(8 * (s + 1)) + 256 + align256(8 * n);
+  return 3 * align256(8 * (s + 1)) + 256 + align256(8 * n) + (with_index ? align256(4 * n) : 0);
 }
 
-// Partitioned insert (see the file comment).  `scratch` holds at least
-// partition_scratch_bytes(num_blocks, n) bytes of device memory.
-sbbf_status launch_insert_partitioned(uint32_t* words, uint32_t num_blocks, const uint64_t* hashes,
-                                      uint64_t n, void* scratch, cudaStream_t s) {
-  if (n == 0) return SBBF_OK;
-  const uint32_t n_slices =
-      static_cast<uint32_t>((static_cast<uint64_t>(num_blocks) + (1ull << kSliceShift) - 1) >> kSliceShift);
-  if (n_slices == 0 || n_slices > kMaxSlices) return SBBF_EINVAL;
-  char* p = static_cast<char*>(scratch);
-  auto* counts = reinterpret_cast<unsigned long long*>(p);
-  p += align256(8 * (n_slices + 1));
-  auto* offsets = reinterpret_cast<unsigned long long*>(p);
-  p += align256(8 * (n_slices + 1));
-  auto* cursors = reinterpret_cast<unsigned long long*>(p);
-  p += align256(8 * (n_slices + 1));
-  auto* tiles = reinterpret_cast<unsigned long long*>(p);
-  p += 256;
-  auto* sorted = reinterpret_cast<uint64_t*>(p);
+// Largest batch a partitioned lookup handles in one pass (32-bit positions).
+constexpr uint64_t kMaxIndexedKeys = 1ull << 31;
 
-  SBBF_CUDA(cudaMemsetAsync(counts, 0, 8ull * n_slices, s));
+namespace {
+
+struct PartScratch {
+  unsigned long long *counts, *offsets, *cursors, *tiles;
+  uint64_t* sorted;
+  uint32_t* idx;
+};
+
+PartScratch carve(void* scratch, uint32_t n_slices, uint64_t n) {
+  PartScratch r;
+  char* p = static_cast<char*>(scratch);
+  r.counts = reinterpret_cast<unsigned long long*>(p);
+  p += align256(8 * (n_slices + 1));
+  r.offsets = reinterpret_cast<unsigned long long*>(p);
+  p += align256(8 * (n_slices + 1));
+  r.cursors = reinterpret_cast<unsigned long long*>(p);
+  p += align256(8 * (n_slices + 1));
+  r.tiles = reinterpret_cast<unsigned long long*>(p);
+  p += 256;
+  r.sorted = reinterpret_cast<uint64_t*>(p);
+  p += align256(8 * n);
+  r.idx = reinterpret_cast<uint32_t*>(p);
+  return r;
+}
+
+// Steps 1-3: counts, offsets and the slice-ordered keys (and positions).
+sbbf_status partition(const uint64_t* hashes, uint64_t n, uint32_t num_blocks, uint32_t n_slices,
+                      const PartScratch& ps, bool with_index, cudaStream_t s) {
+  SBBF_CUDA(cudaMemsetAsync(ps.counts, 0, 8ull * n_slices, s));
   const bool few = n_slices <= kFewSlices;
   const uint64_t tiles_n = (n + kTileKeys - 1) / kTileKeys;
   const size_t count_smem = 4ull * n_slices;
-  const size_t scatter_smem = 8ull * kTileKeys + 16ull * n_slices;
-  static int occ_count_few = occupancy(count_kernel<true>, kPartThreads, 4 * kFewSlices);
-  static int occ_count_many = occupancy(count_kernel<false>, kPartThreads, 4 * kMaxSlices);
-  static const bool smem_set = [] {
-    cudaFuncSetAttribute(scatter_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(8ull * kTileKeys + 16ull * kMaxSlices));
-    cudaFuncSetAttribute(scatter_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(8ull * kTileKeys + 16ull * kMaxSlices));
+  const size_t scatter_smem = 8ull * kTileKeys + 16ull * n_slices + (with_index ? 4ull * kTileKeys : 0);
+  const size_t max_smem = 12ull * kTileKeys + 16ull * kMaxSlices;
+  static const bool smem_set = [max_smem] {
+    cudaFuncSetAttribute(scatter_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(max_smem));
+    cudaFuncSetAttribute(scatter_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(max_smem));
+    cudaFuncSetAttribute(scatter_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(max_smem));
+    cudaFuncSetAttribute(scatter_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(max_smem));
     return true;
   }();
   (void)smem_set;
-  static int occ_scatter_few = occupancy(scatter_kernel<true>, kPartThreads,
-                                         8ull * kTileKeys + 16ull * kFewSlices);
-  static int occ_scatter_many = occupancy(scatter_kernel<false>, kPartThreads,
-                                          8ull * kTileKeys + 16ull * kMaxSlices);
+  static int occ_count_few = occupancy(count_kernel<true>, kPartThreads, 4 * kFewSlices);
+  static int occ_count_many = occupancy(count_kernel<false>, kPartThreads, 4 * kMaxSlices);
+  static int occ_scatter = occupancy(scatter_kernel<false, true>, kPartThreads, max_smem);
   if (few)
     count_kernel<true><<<grid_for(tiles_n, 1, occ_count_few), kPartThreads, count_smem, s>>>(
-        hashes, n, num_blocks, n_slices, counts);
+        hashes, n, num_blocks, n_slices, ps.counts);
   else
     count_kernel<false><<<grid_for(tiles_n, 1, occ_count_many), kPartThreads, count_smem, s>>>(
-        hashes, n, num_blocks, n_slices, counts);
+        hashes, n, num_blocks, n_slices, ps.counts);
   sbbf_status st = launch_status();
   if (st != SBBF_OK) return st;
-  scan_kernel<<<1, 1024, 0, s>>>(counts, n_slices, offsets, cursors);
+  scan_kernel<<<1, 1024, 0, s>>>(ps.counts, n_slices, ps.offsets, ps.cursors);
   if ((st = launch_status()) != SBBF_OK) return st;
-  if (few)
-    scatter_kernel<true><<<grid_for(tiles_n, 1, occ_scatter_few), kPartThreads, scatter_smem, s>>>(
-        hashes, n, num_blocks, n_slices, cursors, sorted);
+  const unsigned grid = grid_for(tiles_n, 1, occ_scatter);
+  if (few && with_index)
+    scatter_kernel<true, true><<<grid, kPartThreads, scatter_smem, s>>>(
+        hashes, n, num_blocks, n_slices, ps.cursors, ps.sorted, ps.idx);
+  else if (few)
+    scatter_kernel<true, false><<<grid, kPartThreads, scatter_smem, s>>>(
+        hashes, n, num_blocks, n_slices, ps.cursors, ps.sorted, nullptr);
+  else if (with_index)
+    scatter_kernel<false, true><<<grid, kPartThreads, scatter_smem, s>>>(
+        hashes, n, num_blocks, n_slices, ps.cursors, ps.sorted, ps.idx);
   else
-    scatter_kernel<false><<<grid_for(tiles_n, 1, occ_scatter_many), kPartThreads, scatter_smem,
-                            s>>>(hashes, n, num_blocks, n_slices, cursors, sorted);
-  if ((st = launch_status()) != SBBF_OK) return st;
-  SBBF_CUDA(cudaMemsetAsync(tiles, 0, 8, s));
+    scatter_kernel<false, false><<<grid, kPartThreads, scatter_smem, s>>>(
+        hashes, n, num_blocks, n_slices, ps.cursors, ps.sorted, nullptr);
+  return launch_status();
+}
+
+uint32_t slices_of(uint32_t num_blocks) {
+  return static_cast<uint32_t>((static_cast<uint64_t>(num_blocks) + (1ull << kSliceShift) - 1) >>
+                               kSliceShift);
+}
+
+}  // namespace
+
+// Partitioned insert (see the file comment).  `scratch` holds at least
+// partition_scratch_bytes(num_blocks, n, false) bytes of device memory.
+sbbf_status launch_insert_partitioned(uint32_t* words, uint32_t num_blocks, const uint64_t* hashes,
+                                      uint64_t n, void* scratch, cudaStream_t s) {
+  if (n == 0) return SBBF_OK;
+  const uint32_t n_slices = slices_of(num_blocks);
+  if (n_slices == 0 || n_slices > kMaxSlices) return SBBF_EINVAL;
+  const PartScratch ps = carve(scratch, n_slices, n);
+  sbbf_status st = partition(hashes, n, num_blocks, n_slices, ps, false, s);
+  if (st != SBBF_OK) return st;
+  SBBF_CUDA(cudaMemsetAsync(ps.tiles, 0, 8, s));
   static int occ_ins = occupancy(sliced_insert_kernel, 256);
   sliced_insert_kernel<<<grid_for((n + 63) / 64, 8, occ_ins), 256, 0, s>>>(
-      words, num_blocks, sorted, n, offsets, n_slices, tiles);
+      words, num_blocks, ps.sorted, n, ps.offsets, n_slices, ps.tiles);
   return launch_status();
+}
+
+// Partitioned lookup of d_hashes[0..n) into the packed bitmask d_out (the
+// same bits as the unpartitioned lookup).  `scratch` holds at least
+// partition_scratch_bytes(num_blocks, min(n, 2^31), true) bytes; batches
+// larger than 2^31 keys run in pieces of 2^31 (a multiple of 32).
+sbbf_status launch_find_partitioned(const uint32_t* words, uint32_t num_blocks,
+                                    const uint64_t* hashes, uint64_t n, uint32_t* d_out,
+                                    void* scratch, cudaStream_t s) {
+  if (n == 0) return SBBF_OK;
+  const uint32_t n_slices = slices_of(num_blocks);
+  if (n_slices == 0 || n_slices > kMaxSlices) return SBBF_EINVAL;
+  for (uint64_t off = 0; off < n; off += kMaxIndexedKeys) {
+    const uint64_t m = n - off < kMaxIndexedKeys ? n - off : kMaxIndexedKeys;
+    const PartScratch ps = carve(scratch, n_slices, m);
+    sbbf_status st = partition(hashes + off, m, num_blocks, n_slices, ps, true, s);
+    if (st != SBBF_OK) return st;
+    uint32_t* out = d_out + off / 32;
+    SBBF_CUDA(cudaMemsetAsync(out, 0, 4 * ((m + 31) / 32), s));
+    SBBF_CUDA(cudaMemsetAsync(ps.tiles, 0, 8, s));
+    static int occ_find = occupancy(sliced_find_kernel, 256);
+    sliced_find_kernel<<<grid_for((m + 63) / 64, 8, occ_find), 256, 0, s>>>(
+        words, num_blocks, ps.sorted, ps.idx, m, ps.offsets, n_slices, ps.tiles, out);
+    st = launch_status();
+    if (st != SBBF_OK) return st;
+  }
+  return SBBF_OK;
 }
 
 }  // namespace sbbf

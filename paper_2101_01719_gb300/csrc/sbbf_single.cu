@@ -74,9 +74,12 @@ sbbf_status launch_clear(uint32_t* dst, uint64_t n_words, cudaStream_t s) {
 
 static bool on_device(const sbbf_t* f) { return f->device == current_device(); }
 
-uint64_t partition_scratch_bytes(uint32_t num_blocks, uint64_t n);
+uint64_t partition_scratch_bytes(uint32_t num_blocks, uint64_t n, bool with_index);
 sbbf_status launch_insert_partitioned(uint32_t* words, uint32_t num_blocks, const uint64_t* hashes,
                                       uint64_t n, void* scratch, cudaStream_t s);
+sbbf_status launch_find_partitioned(const uint32_t* words, uint32_t num_blocks,
+                                    const uint64_t* hashes, uint64_t n, uint32_t* d_out,
+                                    void* scratch, cudaStream_t s);
 
 // Batches at least this large go through the partitioned insert when the
 // filter is at least kPartitionMinBytes (automatic mode).  Measured on GB300:
@@ -87,10 +90,17 @@ sbbf_status launch_insert_partitioned(uint32_t* words, uint32_t num_blocks, cons
 constexpr uint64_t kPartitionMinKeys = 4ull << 20;
 constexpr uint64_t kPartitionMinBytes = 256ull << 20;
 
-static bool want_partition(const sbbf_t* f, uint64_t n) {
+// Automatic mode also wants enough keys per block: a partitioned pass reads
+// every block of the filter once (the slice prefetch), so it pays only when
+// the batch touches each block about once (inserts: >= 1 key per block; a
+// 3e9-key batch into 2^30 blocks runs 2.3x faster) or more (lookups: >= 2;
+// 1e9 lookups into 128.9M blocks run 1.8x faster, into 2^30 blocks 9% slower).
+static bool want_partition(const sbbf_t* f, uint64_t n, uint64_t min_keys_per_block) {
   if (f->partition_mode == SBBF_PARTITION_OFF) return false;
   if (f->partition_mode == SBBF_PARTITION_ON) return true;
-  return n >= kPartitionMinKeys && static_cast<uint64_t>(f->num_blocks) * 32 >= kPartitionMinBytes;
+  return n >= kPartitionMinKeys &&
+         static_cast<uint64_t>(f->num_blocks) * 32 >= kPartitionMinBytes &&
+         n >= min_keys_per_block * f->num_blocks;
 }
 
 // Grows the filter's scratch (cudaMalloc, synchronous) to hold `bytes`.
@@ -207,8 +217,8 @@ sbbf_status sbbf_insert_hashes(sbbf_t* f, const uint64_t* d_hashes, size_t n,
   if (!f || !on_device(f)) return SBBF_EINVAL;
   if (n == 0) return SBBF_OK;
   if (!d_hashes || (reinterpret_cast<uintptr_t>(d_hashes) & 7)) return SBBF_EINVAL;
-  if (want_partition(f, n)) {
-    const sbbf_status st = ensure_scratch(f, partition_scratch_bytes(f->num_blocks, n));
+  if (want_partition(f, n, 1)) {
+    const sbbf_status st = ensure_scratch(f, partition_scratch_bytes(f->num_blocks, n, false));
     if (st == SBBF_OK)
       return launch_insert_partitioned(f->words, f->num_blocks, d_hashes, n, f->scratch, stream);
     if (st != SBBF_ENOMEM || f->partition_mode == SBBF_PARTITION_ON) return st;
@@ -232,6 +242,15 @@ sbbf_status sbbf_find_hashes(const sbbf_t* f, const uint64_t* d_hashes, size_t n
   if (!d_hashes || !d_out_bits || (reinterpret_cast<uintptr_t>(d_hashes) & 7) ||
       (reinterpret_cast<uintptr_t>(d_out_bits) & 3))
     return SBBF_EINVAL;
+  if (want_partition(f, n, 2)) {
+    const uint64_t piece = n < (1ull << 31) ? n : (1ull << 31);
+    const sbbf_status st =
+        ensure_scratch(const_cast<sbbf_t*>(f), partition_scratch_bytes(f->num_blocks, piece, true));
+    if (st == SBBF_OK)
+      return launch_find_partitioned(f->words, f->num_blocks, d_hashes, n, d_out_bits, f->scratch,
+                                     stream);
+    if (st != SBBF_ENOMEM || f->partition_mode == SBBF_PARTITION_ON) return st;
+  }
   return launch_find(f->words, f->num_blocks, d_hashes, n, d_out_bits, stream);
 }
 

@@ -331,3 +331,23 @@ def test_partitioned_insert_unaligned_and_repeated():
     assert np.array_equal(f.to_numpy(), ref)
     with pytest.raises(sb.SbbfError):
         f.set_partitioning(7)
+
+
+@pytest.mark.parametrize("B,n", [(2**20, 1), (2**20 + 5, 16_385), (3 * 2**20 - 1, 1_000_003),
+                                 (5 * 2**20 + 77, 2_500_033)])
+def test_partitioned_find_equals_oracle(B, n):
+    """Slice-partitioned lookups (forced on) answer exactly as the oracle,
+    every bit at its original position, tail bits zero."""
+    keys = inp.stream(140 + B % 13, 0, max(1, n // 3))
+    q = np.concatenate([inp.stream(140 + B % 13, 1, n - n // 4), keys[: n // 4]])[:n]
+    f = sb.Filter(B)
+    f.insert(to_dev(keys))
+    ref = _oracle_filter(B, keys)
+    f.set_partitioning(sb.PARTITION_ON)
+    out = torch.full((sb.out_words(n) + 1,), -1, dtype=torch.int32, device=dev())
+    f.find(to_dev(q), out=out)
+    got = bits_np(out)
+    assert np.array_equal(got[: sb.out_words(n)], oracle.find(ref, B, q))
+    assert got[-1] == 0xFFFFFFFF  # nothing written past the answers
+    f.set_partitioning(sb.PARTITION_OFF)
+    assert np.array_equal(bits_np(f.find(to_dev(q))), oracle.find(ref, B, q))
