@@ -188,11 +188,13 @@ sbbf_status sbbf_find_hashes_host(const sbbf_t *f, sbbf_host_pipe_t *p,
  * under a device-memory budget (not in the paper).
  *
  * A scheduler thread owned by the server forms launch windows from the
- * requests that have arrived (in arrival order, bounded by requests and
- * hashes per window), admits each request only when its filter is resident
- * within the budget (evicting the least recently used idle filter to pinned
- * host memory when needed), and runs all requests of a window in one launch
- * while the next window is being formed.  Results equal serial replay in
+ * requests that have arrived (filters in the order of their oldest queued
+ * request, each filter's requests in arrival order, bounded by requests and
+ * hashes per window), admits a filter's requests only when the filter is
+ * resident within the budget (evicting the least recently used filter with
+ * no queued requests, else the least recently used, to pinned host memory),
+ * and runs all requests of a window in one launch while the next window is
+ * being formed.  Results equal serial replay in
  * arrival order: a lookup sees exactly the inserts on its filter that arrived
  * before it (per filter, runs of inserts and runs of lookups execute as
  * ordered phases).

@@ -1,14 +1,18 @@
 // Serving: many resident filters, requests arriving over time, continuous
 // batching under a device-memory budget.
 //
-// A request is one insert or lookup of n hashes on one filter.  A scheduler
-// thread owns the GPU stream.  Whenever fewer than `max_inflight_windows`
-// windows are on the GPU it forms the next window from the requests that
-// have arrived: in arrival order, up to `max_window_requests` requests and
-// `max_window_keys` hashes, skipping (and keeping in order) requests whose
-// filter cannot be made resident within the budget.  Requests that arrive
-// while earlier windows run are admitted into the next window as slots and
-// memory free up, and all requests of a window run in one kernel launch.
+// A request is one insert or lookup of n hashes on one filter.  Requests
+// queue per filter in arrival order.  A scheduler thread owns the GPU stream;
+// whenever fewer than `max_inflight_windows` windows are on the GPU it forms
+// the next window: it visits the filters in the order of their oldest queued
+// request and, for each filter it can make resident within the budget, takes
+// that filter's queued requests in order (at most four runs of one
+// operation, so a window has at most four phases), up to
+// `max_window_requests` requests and `max_window_keys` hashes per window.  One admission thus
+// serves a filter's whole backlog, and a filter that cannot be admitted yet
+// holds back only its own requests.  Requests that arrive while earlier
+// windows run are admitted into the next window as slots and memory free up,
+// and all requests of a window run in one kernel launch.
 //
 // Result semantics are those of serial replay in arrival order: a lookup sees
 // exactly the inserts on its filter that arrived before it.  Within a window
@@ -34,7 +38,9 @@
 #include <cstring>
 #include <deque>
 #include <mutex>
+#include <set>
 #include <thread>
+#include <utility>
 #include <vector>
 
 #include "sbbf.h"
@@ -145,10 +151,23 @@ bool device_resident(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Runs of one operation a filter may contribute to one window; each run is
+// a phase (a launch), so this bounds the launches of a window.
+constexpr int kMaxRunsPerFilter = 4;
+// Windows after an eviction or a refused admission during which filters
+// drain their whole backlog instead of kMaxRunsPerFilter runs.
+constexpr int kPressureWindows = 16;
+
+// A non-resident filter whose oldest request has waited this long is
+// admitted in the same pass as the resident filters and may evict a filter
+// that still has queued requests.
+constexpr uint64_t kAdmitAgeNs = 50000000;
+
 struct Pending {
   sbbf_request_t req;
   uint64_t ticket;
   uint64_t dev_bytes;  // device-resident payload + result bytes (budgeted)
+  uint64_t t_submit;   // steady-clock ns at submission
 };
 
 struct FilterState {
@@ -157,7 +176,6 @@ struct FilterState {
   uint32_t* h_words = nullptr;  // pinned host copy after an eviction
   bool written = false;         // ever inserted into
   bool host_valid = false;      // h_words equals the current contents
-  uint64_t pending = 0;         // queued requests not yet in a window
   uint64_t last_use = 0;        // window sequence number of its last use
   uint64_t bytes() const { return static_cast<uint64_t>(num_blocks) * 32; }
 };
@@ -189,7 +207,12 @@ struct sbbf_server {
   cudaStream_t stream = nullptr;
   std::mutex mu;
   std::condition_variable cv;
-  std::deque<Pending> pending;
+  // Queued requests per filter in arrival order, and the filters ordered by
+  // the ticket of their oldest queued request.
+  std::vector<std::deque<Pending>> queues;
+  std::set<std::pair<uint64_t, uint32_t>> heads;
+  uint64_t n_pending = 0;
+  int pressure = 0;  // windows left in "memory pressure" mode (see launch_window)
   std::vector<FilterState> filters;
   std::vector<uint64_t> done_ns;   // per ticket: completion time, 0 while pending
   std::vector<int> status;         // per ticket: SBBF_OK or an error
@@ -254,7 +277,7 @@ sbbf_status admit(sbbf_server_t* s, uint32_t f) {
 // `in_window`.  `extra` is the budgeted bytes the caller adds besides.
 // Returns SBBF_EBUSY when the budget cannot be met now.
 sbbf_status make_resident(sbbf_server_t* s, uint32_t f, uint64_t extra,
-                          const std::vector<char>& in_window) {
+                          const std::vector<char>& in_window, bool evict_queued = true) {
   FilterState& st = s->filters[f];
   const uint64_t need = (st.d_words ? 0 : st.bytes()) + extra;
   while (s->resident_bytes + s->inflight_bytes + need > s->cfg.budget_bytes) {
@@ -265,12 +288,13 @@ sbbf_status make_resident(sbbf_server_t* s, uint32_t f, uint64_t extra,
     for (size_t i = 0; i < s->filters.size(); ++i) {
       const FilterState& c = s->filters[i];
       if (!c.d_words || in_window[i] || i == f) continue;
+      if (!evict_queued && !s->queues[i].empty()) continue;
       if (victim < 0) {
         victim = static_cast<int>(i);
         continue;
       }
       const FilterState& v = s->filters[victim];
-      const bool c_idle = c.pending == 0, v_idle = v.pending == 0;
+      const bool c_idle = s->queues[i].empty(), v_idle = s->queues[victim].empty();
       if ((c_idle && !v_idle) || (c_idle == v_idle && c.last_use < v.last_use))
         victim = static_cast<int>(i);
     }
@@ -296,40 +320,76 @@ sbbf_status launch_window(sbbf_server_t* s, bool* launched) {
     }
   if (slot < 0) return SBBF_OK;
   WindowSlot& ws = s->slots[slot];
-  std::vector<char> in_window(s->filters.size(), 0), blocked(s->filters.size(), 0);
+  std::vector<char> in_window(s->filters.size(), 0);
   std::vector<Pending> taken;
   uint64_t keys = 0, bytes = 0;
-  // Scan a bounded prefix of the queue so that a long backlog behind blocked
-  // filters costs no more than a window's worth of work per launch.
+  // Filters in the order of their oldest queued request; each admitted filter
+  // brings as many of its queued requests (in order) as the window holds, so
+  // one admission serves a filter's whole backlog.  A filter that cannot be
+  // made resident now keeps its requests queued; other filters proceed.
+  // Pass 0 takes resident filters (and non-resident ones that waited longer
+  // than kAdmitAgeNs); pass 1 admits the others, evicting only then.
+  std::vector<std::pair<uint64_t, uint32_t>> done_heads, new_heads;
+  const uint64_t now = now_ns();
+  bool full = false;
+  for (int pass = 0; pass < 2 && !full; ++pass) {
   size_t scanned = 0;
-  const size_t scan_limit = static_cast<size_t>(s->cfg.max_window_requests) + 4096;
-  for (auto it = s->pending.begin();
-       it != s->pending.end() && taken.size() < s->cfg.max_window_requests &&
-       scanned < scan_limit;
-       ++scanned) {
-    const Pending& p = *it;
-    const uint32_t f = p.req.filter;
-    if (blocked[f]) {
-      ++it;
-      continue;
+  const size_t scan_limit = static_cast<size_t>(s->cfg.max_window_requests) + 64;
+  for (auto it = s->heads.begin(); it != s->heads.end() &&
+                                   taken.size() < s->cfg.max_window_requests &&
+                                   scanned < scan_limit;
+       ++it, ++scanned) {
+    const uint32_t f = it->second;
+    if (in_window[f]) continue;  // taken in pass 0
+    std::deque<Pending>& q = s->queues[f];
+    const bool resident = s->filters[f].d_words != nullptr;
+    const bool aged = now - q.front().t_submit >= kAdmitAgeNs;
+    if (pass == 0 && !resident && !aged) continue;
+    if (!taken.empty() && keys + q.front().req.n > s->cfg.max_window_keys) {
+      full = true;
+      break;
     }
-    if (!taken.empty() && keys + p.req.n > s->cfg.max_window_keys) break;
-    sbbf_status rc = make_resident(s, f, bytes + p.dev_bytes, in_window);
+    // Only a request that waited kAdmitAgeNs may push out a filter that
+    // still has queued requests; otherwise backlogged filters drain first.
+    const uint64_t evictions_before = s->stats.evictions;
+    sbbf_status rc = make_resident(s, f, bytes + q.front().dev_bytes, in_window, aged);
+    if (s->stats.evictions != evictions_before) s->pressure = kPressureWindows;
     if (rc == SBBF_EBUSY) {
-      blocked[f] = 1;  // later requests on f wait behind this one
       ++s->stats.admission_waits;
-      ++it;
+      s->pressure = kPressureWindows;
       continue;
     }
     if (rc != SBBF_OK) return rc;
     in_window[f] = 1;
-    keys += p.req.n;
-    bytes += p.dev_bytes;
-    --s->filters[f].pending;
-    taken.push_back(p);
-    it = s->pending.erase(it);
+    int runs = 0;
+    uint32_t last_op = ~0u;
+    // Under memory pressure a resident filter drains its whole backlog, so
+    // each admission serves as many requests as possible.
+    const int max_runs = s->pressure > 0 ? 1 << 30 : kMaxRunsPerFilter;
+    while (!q.empty() && taken.size() < s->cfg.max_window_requests) {
+      const Pending& p = q.front();
+      if (!taken.empty() && keys + p.req.n > s->cfg.max_window_keys) break;
+      if (p.req.op != last_op) {  // a new run of this filter: one more phase
+        if (runs == max_runs) break;
+        ++runs;
+        last_op = p.req.op;
+      }
+      if (s->resident_bytes + s->inflight_bytes + bytes + p.dev_bytes > s->cfg.budget_bytes) break;
+      keys += p.req.n;
+      bytes += p.dev_bytes;
+      taken.push_back(p);
+      q.pop_front();
+      --s->n_pending;
+    }
+    done_heads.push_back(*it);
+    if (!q.empty()) new_heads.push_back({q.front().ticket, f});
   }
+  if (taken.size() >= s->cfg.max_window_requests) full = true;
+  }
+  for (const auto& h : done_heads) s->heads.erase(h);
+  for (const auto& h : new_heads) s->heads.insert(h);
   if (taken.empty()) return SBBF_OK;
+  if (s->pressure > 0) --s->pressure;
   const uint64_t seq = ++s->window_seq;
   // Phases: per filter, a new phase at every change of operation.
   std::vector<int> last_op(s->filters.size(), -1), phase_of(s->filters.size(), 0);
@@ -423,9 +483,9 @@ void worker_loop(sbbf_server_t* s) {
   std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
     collect(s);
-    if (s->stop && s->pending.empty() && s->inflight.empty()) break;
+    if (s->stop && s->n_pending == 0 && s->inflight.empty()) break;
     bool launched = false;
-    if (!s->paused && !s->pending.empty() &&
+    if (!s->paused && s->n_pending > 0 &&
         s->inflight.size() < s->cfg.max_inflight_windows && s->error == SBBF_OK) {
       const sbbf_status rc = launch_window(s, &launched);
       if (rc != SBBF_OK) s->error = rc;
@@ -530,6 +590,7 @@ sbbf_status sbbf_server_add_filter(sbbf_server_t* s, uint32_t num_blocks, uint32
   FilterState f;
   f.num_blocks = num_blocks;
   s->filters.push_back(f);
+  s->queues.emplace_back();
   *id = static_cast<uint32_t>(s->filters.size() - 1);
   return SBBF_OK;
 }
@@ -543,20 +604,23 @@ sbbf_status sbbf_server_submit(sbbf_server_t* s, const sbbf_request_t* r, uint64
   Pending p;
   p.req = *r;
   p.dev_bytes = 0;
+  p.t_submit = now_ns();
   if (r->n && device_resident(r->d_hashes)) p.dev_bytes += 8 * r->n;
   if (r->n && r->op == SBBF_OP_FIND && device_resident(r->d_out_bits)) p.dev_bytes += 4 * ((r->n + 31) / 32);
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if (r->filter >= s->filters.size()) return SBBF_EINVAL;
     if (s->error != SBBF_OK) return s->error;
-    if (s->pending.size() >= s->cfg.max_pending_requests) return SBBF_EBUSY;
+    if (s->n_pending >= s->cfg.max_pending_requests) return SBBF_EBUSY;
     if (s->filters[r->filter].bytes() + p.dev_bytes > s->cfg.budget_bytes) return SBBF_EBUSY;
     p.ticket = s->done_ns.size();
     s->done_ns.push_back(r->n == 0 ? now_ns() : 0);
     s->status.push_back(SBBF_OK);
     if (r->n > 0) {
-      s->pending.push_back(p);
-      ++s->filters[r->filter].pending;
+      std::deque<Pending>& q = s->queues[r->filter];
+      if (q.empty()) s->heads.insert({p.ticket, r->filter});
+      q.push_back(p);
+      ++s->n_pending;
     }
     *ticket = p.ticket;
   }
@@ -583,7 +647,7 @@ sbbf_status sbbf_server_drain(sbbf_server_t* s, uint64_t timeout_ns) {
   if (!s) return SBBF_EINVAL;
   const uint64_t deadline = timeout_ns ? now_ns() + timeout_ns : 0;
   std::unique_lock<std::mutex> lk(s->mu);
-  while (!s->pending.empty() || !s->inflight.empty()) {
+  while (s->n_pending > 0 || !s->inflight.empty()) {
     if (s->error != SBBF_OK) return s->error;
     if (deadline && now_ns() >= deadline) return SBBF_ETIMEOUT;
     s->cv.wait_for(lk, std::chrono::microseconds(200));
