@@ -75,6 +75,14 @@ def lib():
                 "oracle_find_mt": (i32, [P32, u32, P64, sz, P32, i32]),
                 "oracle_insert_mt": (i32, [P32, u32, P64, sz, i32]),
                 "oracle_num_cores": (i32, []),
+                "oracle_seed_k": (u32, [i32]),
+                "oracle_insert_k": (i32, [P32, u32, i32, P64, sz]),
+                "oracle_find_k": (i32, [P32, u32, i32, P64, sz, P32]),
+                "oracle_fpr_poisson_k": (ctypes.c_double, [ctypes.c_double, i32]),
+                "oracle_xxh64": (u64, [ctypes.c_void_p, sz, u64]),
+                "oracle_xxh64_fixed": (None, [ctypes.c_void_p, sz, sz, u64, P64]),
+                "oracle_xxh64_var": (None, [ctypes.c_void_p, P64, sz, u64, P64]),
+                "oracle_swap_lane_pairs": (None, [P32, sz, P32]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(L, name)
@@ -211,3 +219,67 @@ def insert_mt(words, num_blocks, hashes, n_threads) -> int:
 
 def num_cores() -> int:
     return int(lib().oracle_num_cores())
+
+
+# ---- lane-count variants, key hashing, Parquet layout ----------------------
+
+def seed_k(i: int) -> int:
+    return int(lib().oracle_seed_k(i))
+
+
+def insert_k(words: np.ndarray, num_blocks: int, k: int, hashes) -> np.ndarray:
+    h = _c_u64(hashes)
+    assert words.dtype == np.uint32 and words.flags.c_contiguous
+    assert words.size == k * num_blocks
+    if lib().oracle_insert_k(_u32p(words), num_blocks, k, _u64p(h), h.size) != 0:
+        raise ValueError("lanes must be 4, 8 or 16")
+    return words
+
+
+def find_k(words: np.ndarray, num_blocks: int, k: int, hashes) -> np.ndarray:
+    h = _c_u64(hashes)
+    assert words.size == k * num_blocks
+    out = np.zeros((h.size + 31) // 32, np.uint32)
+    if lib().oracle_find_k(_u32p(words), num_blocks, k, _u64p(h), h.size, _u32p(out)) != 0:
+        raise ValueError("lanes must be 4, 8 or 16")
+    return out
+
+
+def fpr_poisson_k(a: float, k: int) -> float:
+    return float(lib().oracle_fpr_poisson_k(a, k))
+
+
+def xxh64(data: bytes, seed: int = 0) -> int:
+    buf = ctypes.create_string_buffer(bytes(data), max(len(data), 1))
+    return int(lib().oracle_xxh64(buf, len(data), seed))
+
+
+def xxh64_fixed(keys: np.ndarray, seed: int = 0) -> np.ndarray:
+    """XXH64 of each element's little-endian bytes (keys: a 1-D integer array)."""
+    a = np.ascontiguousarray(keys)
+    a = a.astype(a.dtype.newbyteorder("<"), copy=False)
+    out = np.empty(a.size, np.uint64)
+    lib().oracle_xxh64_fixed(a.ctypes.data_as(ctypes.c_void_p), a.dtype.itemsize, a.size,
+                             seed, _u64p(out))
+    return out
+
+
+def xxh64_var(data: np.ndarray, offsets: np.ndarray, seed: int = 0) -> np.ndarray:
+    """XXH64 of data[offsets[k]:offsets[k+1]] for each k."""
+    d = np.ascontiguousarray(data, dtype=np.uint8)
+    o = _c_u64(offsets)
+    n = o.size - 1
+    out = np.empty(max(n, 0), np.uint64)
+    if d.size == 0:
+        d = np.zeros(1, np.uint8)
+    lib().oracle_xxh64_var(d.ctypes.data_as(ctypes.c_void_p), _u64p(o), n, seed, _u64p(out))
+    return out
+
+
+def swap_lane_pairs(words: np.ndarray) -> np.ndarray:
+    """Appendix lane order <-> Parquet's salt order (word w <-> word w ^ 1)."""
+    w = _c_u32(words)
+    assert w.size % 2 == 0
+    out = np.empty_like(w)
+    lib().oracle_swap_lane_pairs(_u32p(w), w.size, _u32p(out))
+    return out

@@ -214,6 +214,162 @@ void oracle_splitmix64_fill(uint64_t seed, uint64_t start, size_t n,
   for (size_t k = 0; k < n; ++k) out[k] = oracle_splitmix64_at(seed, start + k);
 }
 
+/* ---- lane-count variants ----------------------------------------------
+ * The design list says four or sixteen lanes would work as well as eight.  A
+ * k-lane block is k consecutive 32-bit words; block selection is the
+ * appendix block_index over the filter's k-lane blocks, and lane i sets bit
+ * (s_i * x mod 2^32) >> 27 of word i, x the low 32 bits of the hash.
+ * Readings (the paper names no seeds beyond eight): k = 4 uses lanes 0..3 of
+ * the eight appendix seeds; k = 16 uses the eight appendix seeds followed by
+ * s_{8+j} = (splitmix64 output j of seed 0 >> 32) | 1, j = 0..7 (odd, as
+ * multiply-shift hashing requires). */
+uint32_t oracle_seed_k(int i) {
+  if (i < 8) return kSeed[i];
+  return (uint32_t)(oracle_splitmix64_at(0, (uint64_t)(i - 8)) >> 32) | 1u;
+}
+
+static int lanes_ok(int k) { return k == 4 || k == 8 || k == 16; }
+
+int oracle_insert_k(uint32_t *words, uint32_t num_blocks, int k,
+                    const uint64_t *hashes, size_t n) {
+  if (!lanes_ok(k)) return -1;
+  for (size_t j = 0; j < n; ++j) {
+    uint64_t b = oracle_block_index(hashes[j], num_blocks);
+    uint32_t x = (uint32_t)hashes[j];
+    for (int i = 0; i < k; ++i) {
+      uint32_t bit = (uint32_t)(oracle_seed_k(i) * x) >> 27;
+      words[(uint64_t)k * b + (uint64_t)i] |= (uint32_t)1u << bit;
+    }
+  }
+  return 0;
+}
+
+int oracle_find_k(const uint32_t *words, uint32_t num_blocks, int k,
+                  const uint64_t *hashes, size_t n, uint32_t *out_bits) {
+  if (!lanes_ok(k)) return -1;
+  for (size_t w = 0; w < (n + 31) / 32; ++w) out_bits[w] = 0;
+  for (size_t j = 0; j < n; ++j) {
+    uint64_t b = oracle_block_index(hashes[j], num_blocks);
+    uint32_t x = (uint32_t)hashes[j];
+    int hit = 1;
+    for (int i = 0; i < k; ++i) {
+      uint32_t bit = (uint32_t)(oracle_seed_k(i) * x) >> 27;
+      if ((words[(uint64_t)k * b + (uint64_t)i] & ((uint32_t)1u << bit)) == 0) hit = 0;
+    }
+    if (hit) out_bits[j / 32] |= (uint32_t)1u << (j % 32);
+  }
+  return 0;
+}
+
+/* FPR analysis with k lanes: sum_i Pois_a(i) * (1 - (1 - 1/32)^i)^k. */
+double oracle_fpr_poisson_k(double a, int k) {
+  if (!(a > 0.0)) return 0.0;
+  const double q = 1.0 - 1.0 / 32.0;
+  size_t i_max = (size_t)(a + 40.0 * sqrt(a + 1.0) + 200.0);
+  double sum = 0.0;
+  for (size_t i = 0; i <= i_max; ++i) {
+    double log_p = (double)i * log(a) - a - lgamma((double)i + 1.0);
+    sum += exp(log_p) * pow(1.0 - pow(q, (double)i), (double)k);
+  }
+  return sum;
+}
+
+/* ---- key hashing --------------------------------------------------------
+ * The paper hashes each key once to 64 bits and fixes no hash function.
+ * Parquet, one of the adopters the paper lists, uses XXH64 with seed 0; this
+ * is XXH64 as its published specification defines it (Y. Collet, "xxHash
+ * fast digest algorithm", XXH64): four accumulators over 32-byte stripes for
+ * inputs of 32 bytes or more, then the length, then 8-, 4- and 1-byte tail
+ * steps, then the final avalanche.  Input bytes are read little-endian. */
+#define XP1 UINT64_C(0x9E3779B185EBCA87)
+#define XP2 UINT64_C(0xC2B2AE3D27D4EB4F)
+#define XP3 UINT64_C(0x165667B19E3779F9)
+#define XP4 UINT64_C(0x85EBCA77C2B2AE63)
+#define XP5 UINT64_C(0x27D4EB2F165667C5)
+
+static uint64_t xrotl(uint64_t x, int r) { return (x << r) | (x >> (64 - r)); }
+
+static uint64_t read_le(const uint8_t *p, int bytes) {
+  uint64_t v = 0;
+  for (int i = bytes - 1; i >= 0; --i) v = (v << 8) | p[i];
+  return v;
+}
+
+static uint64_t xround(uint64_t acc, uint64_t lane) {
+  acc += lane * XP2;
+  acc = xrotl(acc, 31);
+  return acc * XP1;
+}
+
+static uint64_t xmerge(uint64_t acc, uint64_t v) {
+  acc ^= xround(0, v);
+  return acc * XP1 + XP4;
+}
+
+uint64_t oracle_xxh64(const void *data, size_t len, uint64_t seed) {
+  const uint8_t *p = (const uint8_t *)data;
+  size_t i = 0;
+  uint64_t acc;
+  if (len >= 32) {
+    uint64_t v1 = seed + XP1 + XP2, v2 = seed + XP2, v3 = seed, v4 = seed - XP1;
+    for (; i + 32 <= len; i += 32) {
+      v1 = xround(v1, read_le(p + i, 8));
+      v2 = xround(v2, read_le(p + i + 8, 8));
+      v3 = xround(v3, read_le(p + i + 16, 8));
+      v4 = xround(v4, read_le(p + i + 24, 8));
+    }
+    acc = xrotl(v1, 1) + xrotl(v2, 7) + xrotl(v3, 12) + xrotl(v4, 18);
+    acc = xmerge(acc, v1);
+    acc = xmerge(acc, v2);
+    acc = xmerge(acc, v3);
+    acc = xmerge(acc, v4);
+  } else {
+    acc = seed + XP5;
+  }
+  acc += (uint64_t)len;
+  for (; i + 8 <= len; i += 8) {
+    acc ^= xround(0, read_le(p + i, 8));
+    acc = xrotl(acc, 27) * XP1 + XP4;
+  }
+  if (i + 4 <= len) {
+    acc ^= read_le(p + i, 4) * XP1;
+    acc = xrotl(acc, 23) * XP2 + XP3;
+    i += 4;
+  }
+  for (; i < len; ++i) {
+    acc ^= (uint64_t)p[i] * XP5;
+    acc = xrotl(acc, 11) * XP1;
+  }
+  acc ^= acc >> 33;
+  acc *= XP2;
+  acc ^= acc >> 29;
+  acc *= XP3;
+  acc ^= acc >> 32;
+  return acc;
+}
+
+void oracle_xxh64_fixed(const void *keys, size_t key_bytes, size_t n,
+                        uint64_t seed, uint64_t *out) {
+  const uint8_t *p = (const uint8_t *)keys;
+  for (size_t k = 0; k < n; ++k) out[k] = oracle_xxh64(p + k * key_bytes, key_bytes, seed);
+}
+
+void oracle_xxh64_var(const uint8_t *data, const uint64_t *offsets, size_t n,
+                      uint64_t seed, uint64_t *out) {
+  for (size_t k = 0; k < n; ++k)
+    out[k] = oracle_xxh64(data + offsets[k], (size_t)(offsets[k + 1] - offsets[k]), seed);
+}
+
+/* Parquet's block layout.  Parquet lists its eight salts in the order the
+ * paper's text prints the appendix constants, which swaps each pair of the
+ * appendix's little-endian lane order: Parquet lane i uses the multiplier of
+ * appendix lane i ^ 1.  The same keys therefore give the same blocks with
+ * words 2j and 2j+1 exchanged; this maps one layout to the other (the map is
+ * its own inverse). */
+void oracle_swap_lane_pairs(const uint32_t *in, size_t n_words, uint32_t *out) {
+  for (size_t w = 0; w < n_words; ++w) out[w] = in[w ^ 1];
+}
+
 int oracle_num_cores(void) {
   long c = sysconf(_SC_NPROCESSORS_ONLN);
   return c > 0 ? (int)c : 1;

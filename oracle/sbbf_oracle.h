@@ -100,6 +100,34 @@ int oracle_find_mt(const uint32_t *words, uint32_t num_blocks,
 int oracle_insert_mt(uint32_t *words, uint32_t num_blocks,
                      const uint64_t *hashes, size_t n, int n_threads);
 
+/* Lane-count variants (k = 4, 8 or 16 lanes per block; the design list says
+ * four or sixteen work as well).  A k-lane block is k words; lane i uses
+ * seed oracle_seed_k(i): the appendix seeds for i < 8, and for k = 16
+ * lanes 8..15 use (splitmix64(seed 0) output i-8 >> 32) | 1.  Return -1 for
+ * any other k. */
+uint32_t oracle_seed_k(int i);
+int oracle_insert_k(uint32_t *words, uint32_t num_blocks, int k,
+                    const uint64_t *hashes, size_t n);
+int oracle_find_k(const uint32_t *words, uint32_t num_blocks, int k,
+                  const uint64_t *hashes, size_t n, uint32_t *out_bits);
+double oracle_fpr_poisson_k(double a, int k);
+
+/* XXH64 of len bytes (published xxHash specification).  The paper hashes
+ * each key once and fixes no hash; Parquet's split block filters use XXH64,
+ * seed 0. */
+uint64_t oracle_xxh64(const void *data, size_t len, uint64_t seed);
+/* XXH64 of n fixed-width keys of key_bytes bytes each, stored back to back. */
+void oracle_xxh64_fixed(const void *keys, size_t key_bytes, size_t n,
+                        uint64_t seed, uint64_t *out);
+/* XXH64 of n variable-length keys: key k is data[offsets[k], offsets[k+1]). */
+void oracle_xxh64_var(const uint8_t *data, const uint64_t *offsets, size_t n,
+                      uint64_t seed, uint64_t *out);
+
+/* Parquet block layout: out word w = in word (w ^ 1) (Parquet lists the
+ * salts in the paper text's order, pairwise swapped against the appendix's
+ * little-endian lane order). */
+void oracle_swap_lane_pairs(const uint32_t *in, size_t n_words, uint32_t *out);
+
 /* Number of online host cores. */
 int oracle_num_cores(void);
 
