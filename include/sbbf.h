@@ -91,6 +91,28 @@ sbbf_status sbbf_create(uint32_t num_blocks, sbbf_t **out);
  * handle.  Errors: SBBF_EINVAL (NULL, zero blocks, misaligned). */
 sbbf_status sbbf_wrap(uint32_t *d_words, uint32_t num_blocks, sbbf_t **out);
 
+/* Lane-count variants.  The paper uses eight 32-bit lanes per block to fill a
+ * 256-bit SIMD register and notes that four or sixteen lanes would work too
+ * (design list, footnote).  A filter of `lanes` = 4, 8 or 16 has blocks of
+ * `lanes` consecutive 32-bit words (16, 32 or 64 bytes); block selection is
+ * the appendix block_index over its num_blocks blocks, and lane i of the
+ * block sets bit (s_i * x mod 2^32) >> 27 of word i (x the hash's low 32
+ * bits).  Lanes 0..7 use the appendix seeds; lanes 8..15 (lanes = 16) use
+ * the odd constants 0xe220a839, 0x6e789e6b, 0x06c45d19, 0xf88bb8a9,
+ * 0x1b39896b, 0x53cb9f0d, 0x2c829abf, 0xc584133b ((splitmix64 output j of
+ * seed 0 >> 32) | 1; the paper names only eight seeds).  Filters of 4 or 16
+ * lanes support the single-filter calls (insert, find, keys, union, clear,
+ * copy, host pipe, serialization); they never take the partitioned path,
+ * and Parquet export wants 8 lanes.  Memory: num_blocks * lanes * 4 bytes.
+ * Errors: SBBF_EINVAL (lanes not 4, 8 or 16, else as sbbf_create /
+ * sbbf_wrap). */
+sbbf_status sbbf_create_lanes(uint32_t num_blocks, uint32_t lanes, sbbf_t **out);
+sbbf_status sbbf_wrap_lanes(uint32_t *d_words, uint32_t num_blocks,
+                            uint32_t lanes, sbbf_t **out);
+
+/* 32-bit lanes per block of f (0 for NULL). */
+uint32_t sbbf_lanes(const sbbf_t *f);
+
 /* Copy h_words (num_blocks * 8 uint32 in the layout above) into a new
  * library-owned filter (synchronous).  Errors as sbbf_create. */
 sbbf_status sbbf_create_from_host(const uint32_t *h_words, uint32_t num_blocks,
@@ -103,7 +125,8 @@ sbbf_status sbbf_destroy(sbbf_t *f);
 /* Number of blocks (0 for NULL). */
 uint32_t sbbf_num_blocks(const sbbf_t *f);
 
-/* Device address and size in bytes of the filter words. */
+/* Device address and size in bytes of the filter words (num_blocks * lanes *
+ * 4 bytes). */
 sbbf_status sbbf_device_words(const sbbf_t *f, uint32_t **d_words,
                               size_t *bytes);
 
@@ -147,15 +170,93 @@ sbbf_status sbbf_find_hashes(const sbbf_t *f, const uint64_t *d_hashes,
                              sbbf_stream_t stream);
 
 /* dst |= src word by word: afterwards dst answers true for every hash either
- * filter held.  Not in the paper; meaningful only for equal num_blocks (the
- * seeds are fixed).  Errors: SBBF_EINVAL (NULL or num_blocks differ). */
+ * filter held.  Not in the paper; meaningful only for equal num_blocks and
+ * lanes (the seeds are fixed).  Errors: SBBF_EINVAL (NULL, num_blocks or
+ * lanes differ). */
 sbbf_status sbbf_union(sbbf_t *dst, const sbbf_t *src, sbbf_stream_t stream);
 
 /* Copy the filter words to host memory h_words of at least
- * num_blocks * 32 bytes; synchronises the stream before returning.
+ * num_blocks * lanes * 4 bytes; synchronises the stream before returning.
  * Errors: SBBF_EINVAL (NULL or bytes too small), SBBF_ECUDA. */
 sbbf_status sbbf_copy_to_host(const sbbf_t *f, uint32_t *h_words, size_t bytes,
                               sbbf_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Serialization (not in the paper; the systems it lists as adopters store
+ * filters).  Both formats are synchronous and go through host memory.
+ *
+ * Native checkpoint format: a 64-byte little-endian header, then the filter
+ * words in the layout above.
+ *   bytes  0..3   'S' 'B' 'B' 'F'
+ *   bytes  4..7   u32 format version, 1
+ *   bytes  8..11  u32 lanes (4, 8 or 16)
+ *   bytes 12..15  u32 num_blocks
+ *   bytes 16..23  u64 layout digest: XXH64 (seed 0) of the lanes' seeds as
+ *                 little-endian uint32, lane 0 first (detects a filter built
+ *                 with other seeds or another lane order)
+ *   bytes 24..31  u64 payload bytes, num_blocks * lanes * 4
+ *   bytes 32..39  u64 XXH64 (seed 0) of the payload
+ *   bytes 40..63  zero
+ * ---------------------------------------------------------------------- */
+
+/* Bytes sbbf_serialize writes for f (0 for NULL). */
+size_t sbbf_serialized_size(const sbbf_t *f);
+
+/* Write f into h_buf (host memory, at least sbbf_serialized_size(f) bytes)
+ * after the work already on `stream`.  Errors: SBBF_EINVAL (NULL, buffer too
+ * small), SBBF_ECUDA. */
+sbbf_status sbbf_serialize(const sbbf_t *f, void *h_buf, size_t bytes,
+                           sbbf_stream_t stream);
+
+/* Create a library-owned filter on the current device from a native buffer.
+ * Errors: SBBF_EINVAL (bad magic, version, lanes, digest, sizes, nonzero
+ * reserved bytes, truncated buffer or checksum mismatch), SBBF_ENOMEM,
+ * SBBF_ECUDA. */
+sbbf_status sbbf_deserialize(const void *h_buf, size_t bytes, sbbf_t **out);
+
+/* Parquet's Bloom-filter format: a Thrift compact-protocol BloomFilterHeader
+ * {1: i32 numBytes; 2: algorithm = BLOCK; 3: hash = XXHASH; 4: compression =
+ * UNCOMPRESSED} followed by numBytes of bitset.  Parquet's blocks are eight
+ * little-endian uint32 words, but it lists the eight seeds in the order the
+ * paper's text prints the appendix constants, which exchanges words 2j and
+ * 2j+1 of every block relative to this library's lane order (the appendix's
+ * little-endian order); export and import make that exchange.  Parquet hashes
+ * values with XXH64 seed 0 (sbbf_insert_keys / sbbf_insert_bytes with seed
+ * 0 insert the same hashes).  numBytes must be a positive multiple of 32 below
+ * 2^31 (Parquet writers use powers of two up to 128 MiB; readers may require
+ * a power of two). */
+
+/* The header for a bitset of num_bytes bytes: its length in *header_len and,
+ * if h_out is not NULL, its bytes in h_out (cap bytes).  Host only.
+ * Errors: SBBF_EINVAL (num_bytes not a positive multiple of 32 below 2^31,
+ * cap too small). */
+sbbf_status sbbf_parquet_header(uint64_t num_bytes, uint8_t *h_out, size_t cap,
+                                size_t *header_len);
+
+/* Parse a header at h_buf (bytes available): the bitset size and the header
+ * length.  Unknown fields are skipped.  Host only.  Errors: SBBF_EINVAL
+ * (malformed or truncated header, an algorithm, hash or compression other
+ * than BLOCK / XXHASH / UNCOMPRESSED, numBytes not a positive multiple of
+ * 32). */
+sbbf_status sbbf_parquet_parse_header(const uint8_t *h_buf, size_t bytes,
+                                      uint64_t *num_bytes, size_t *header_len);
+
+/* Bytes sbbf_export_parquet writes for f (0 for NULL, lanes != 8 or a filter
+ * of 2 GiB or more). */
+size_t sbbf_parquet_size(const sbbf_t *f);
+
+/* Write header and bitset of f to h_buf; *written (may be NULL) receives the
+ * byte count.  Errors: SBBF_EINVAL (NULL, lanes != 8, buffer too small,
+ * filter too large), SBBF_ECUDA. */
+sbbf_status sbbf_export_parquet(const sbbf_t *f, uint8_t *h_buf, size_t bytes,
+                                size_t *written, sbbf_stream_t stream);
+
+/* Create a library-owned 8-lane filter of numBytes / 32 blocks from a
+ * Parquet Bloom filter at h_buf; *consumed (may be NULL) receives header +
+ * bitset bytes.  Errors: as sbbf_parquet_parse_header, SBBF_EINVAL if the
+ * bitset is truncated, SBBF_ENOMEM, SBBF_ECUDA. */
+sbbf_status sbbf_import_parquet(const uint8_t *h_buf, size_t bytes,
+                                sbbf_t **out, size_t *consumed);
 
 /* ------------------------------------------------------------------------
  * Host-buffer path: copies, kernels and result copies pipelined in chunks.
@@ -182,6 +283,51 @@ sbbf_status sbbf_insert_hashes_host(sbbf_t *f, sbbf_host_pipe_t *p,
 sbbf_status sbbf_find_hashes_host(const sbbf_t *f, sbbf_host_pipe_t *p,
                                   const uint64_t *h_hashes, size_t n,
                                   uint32_t *h_out_bits, sbbf_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Keys hashed on the device (the step before the method: the paper hashes a
+ * key once to 64 bits before block selection, intro, and fixes no hash
+ * function).  The hash is XXH64 of the key's bytes with the caller's seed
+ * (Y. Collet's published xxHash specification).  Parquet's split block
+ * filters hash with XXH64, seed 0, so with seed 0 these calls insert the
+ * hashes a Parquet writer inserts.
+ *
+ * Fixed-width keys: d_keys holds n keys of key_bytes = 4 or 8 bytes each
+ * (a uint32 or uint64 array, aligned to key_bytes); key k is hashed as its
+ * key_bytes little-endian bytes.  Variable-length keys (byte strings): key k
+ * is d_data[d_offsets[k] .. d_offsets[k+1]), d_offsets n + 1 non-decreasing
+ * uint64 (8-byte aligned; not checked against the size of d_data), d_data
+ * any alignment.
+ * Errors: SBBF_EINVAL (key_bytes not 4 or 8, NULL with n > 0, misaligned),
+ * SBBF_ECUDA.
+ * ---------------------------------------------------------------------- */
+
+/* d_hashes[k] = XXH64(key k, seed) for k in [0, n) (d_hashes 8-byte
+ * aligned). */
+sbbf_status sbbf_hash_keys(const void *d_keys, uint32_t key_bytes, size_t n,
+                           uint64_t seed, uint64_t *d_hashes,
+                           sbbf_stream_t stream);
+sbbf_status sbbf_hash_bytes(const uint8_t *d_data, const uint64_t *d_offsets,
+                            size_t n, uint64_t seed, uint64_t *d_hashes,
+                            sbbf_stream_t stream);
+
+/* Insert / look up keys with the hash computed inside the insert and lookup
+ * kernels (no hash array in memory).  The filter and the result bits equal
+ * those of sbbf_hash_keys (or sbbf_hash_bytes) followed by
+ * sbbf_insert_hashes / sbbf_find_hashes.  A batch that takes the partitioned
+ * path (sbbf_set_partitioning) is hashed into the filter's scratch first,
+ * which then grows by 8 bytes per key. */
+sbbf_status sbbf_insert_keys(sbbf_t *f, const void *d_keys, uint32_t key_bytes,
+                             size_t n, uint64_t seed, sbbf_stream_t stream);
+sbbf_status sbbf_find_keys(const sbbf_t *f, const void *d_keys,
+                           uint32_t key_bytes, size_t n, uint64_t seed,
+                           uint32_t *d_out_bits, sbbf_stream_t stream);
+sbbf_status sbbf_insert_bytes(sbbf_t *f, const uint8_t *d_data,
+                              const uint64_t *d_offsets, size_t n,
+                              uint64_t seed, sbbf_stream_t stream);
+sbbf_status sbbf_find_bytes(const sbbf_t *f, const uint8_t *d_data,
+                            const uint64_t *d_offsets, size_t n, uint64_t seed,
+                            uint32_t *d_out_bits, sbbf_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Serving: resident filters, requests arriving over time, continuous batching

@@ -56,11 +56,42 @@ inline unsigned grid_for(uint64_t work_items, uint64_t per_cta, int resident) {
 
 // The single-filter handle (opaque to callers).
 struct sbbf_filter {
-  uint32_t *words;      // device, num_blocks * 8 uint32
+  uint32_t *words;      // device, num_blocks * lanes uint32
   uint32_t num_blocks;
+  uint32_t lanes;       // 32-bit words per block: 8 (the paper's), 4 or 16
   int device;
   int owns;             // 1: allocated by the library
   int partition_mode;   // SBBF_PARTITION_*
   void *scratch;        // partitioned-insert scratch (library-owned), or NULL
   size_t scratch_bytes;
 };
+
+namespace sbbf {
+
+// Partitioned path for filters larger than L2 (sbbf_partition.cu) and the
+// single-filter policy that selects it (sbbf_single.cu).
+uint64_t partition_scratch_bytes(uint32_t num_blocks, uint64_t n, bool with_index);
+sbbf_status launch_insert_partitioned(uint32_t* words, uint32_t num_blocks, const uint64_t* hashes,
+                                      uint64_t n, void* scratch, cudaStream_t s);
+sbbf_status launch_find_partitioned(const uint32_t* words, uint32_t num_blocks,
+                                    const uint64_t* hashes, uint64_t n, uint32_t* d_out,
+                                    void* scratch, cudaStream_t s);
+// True when a batch of n keys should take the partitioned path (the filter's
+// mode, its size, and at least min_keys_per_block keys per block).
+bool want_partition(const sbbf_filter* f, uint64_t n, uint64_t min_keys_per_block);
+// Grows the filter's scratch (cudaMalloc, synchronous) to at least `bytes`.
+sbbf_status ensure_scratch(sbbf_filter* f, size_t bytes);
+
+// Words and bytes of a filter's bit array.
+inline uint64_t filter_words(const sbbf_filter* f) {
+  return static_cast<uint64_t>(f->num_blocks) * f->lanes;
+}
+inline uint64_t filter_bytes(const sbbf_filter* f) { return filter_words(f) * 4; }
+
+// Unpartitioned insert / lookup of device hashes for any lane count.
+sbbf_status launch_insert_filter(const sbbf_filter* f, const uint64_t* d_hashes, uint64_t n,
+                                 cudaStream_t s);
+sbbf_status launch_find_filter(const sbbf_filter* f, const uint64_t* d_hashes, uint64_t n,
+                               uint32_t* d_out, cudaStream_t s);
+
+}  // namespace sbbf

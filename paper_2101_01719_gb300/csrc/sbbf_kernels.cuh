@@ -11,6 +11,9 @@
 // blocks whose block 0 is arena block dir[t].base, so every filter keeps the
 // paper's block selection and mask.
 //
+// A key source S (sbbf_keys.cuh) yields each key's 64-bit hash: the caller's
+// hashes (the paper's input) or raw keys hashed in the same pass.
+//
 // Warp work unit: 64 consecutive keys, two per lane (one 16-byte load when
 // the hash array is 16-byte aligned).
 //
@@ -28,6 +31,7 @@
 #include <cstdint>
 
 #include "sbbf_device.cuh"
+#include "sbbf_keys.cuh"
 
 namespace sbbf {
 
@@ -129,18 +133,6 @@ struct Tagged {
   }
 };
 
-// Two consecutive hashes k, k+1 (zero past n).
-__device__ __forceinline__ void load_pair(const uint64_t* __restrict__ hashes, uint64_t k,
-                                          uint64_t n, bool vec, uint64_t pol, uint64_t& h0,
-                                          uint64_t& h1) {
-  if (vec && k + 1 < n) {
-    load_keys2(hashes + k, pol, h0, h1);
-  } else {
-    h0 = k < n ? load_key1(hashes + k, pol) : 0;
-    h1 = k + 1 < n ? load_key1(hashes + k + 1, pol) : 0;
-  }
-}
-
 __device__ __forceinline__ void warp_span(uint64_t& warp, uint64_t& n_warps) {
   warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   n_warps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
@@ -212,17 +204,16 @@ struct UnitIter {
 // Inserts the 64-hash group g with eight lanes per key: in 16 rounds each
 // group of eight lanes takes one key and lane j ORs lane j's mask bit into
 // word j of the key's block.
-template <class R>
-__device__ __forceinline__ void insert_group8(uint32_t* __restrict__ words, R& res,
-                                              const uint64_t* __restrict__ hashes, uint64_t n,
-                                              bool vec, uint64_t pol, uint64_t g) {
+template <class R, class S>
+__device__ __forceinline__ void insert_group8(uint32_t* __restrict__ words, R& res, const S& src,
+                                              uint64_t n, uint64_t pol, uint64_t g) {
   const unsigned lane = lane_id();
   const uint32_t seed = lane_seed(lane & 7);
   uint32_t* const word_j = words + (lane & 7);
   const int group_base = static_cast<int>(lane & ~7u);
   const uint64_t k = g * 64 + 2 * lane;
   uint64_t h0, h1;
-  load_pair(hashes, k, n, vec, pol, h0, h1);
+  src.pair(k, n, pol, h0, h1);
   res.begin_chunk(g * 64);
   const uint64_t b0 = k < n ? res.block(k, h0) : kNoBlock64;
   const uint64_t b1 = k + 1 < n ? res.block(k + 1, h1) : kNoBlock64;
@@ -237,14 +228,13 @@ __device__ __forceinline__ void insert_group8(uint32_t* __restrict__ words, R& r
 }
 
 // The same group with one lane per key: four red.or.b64 per key.
-template <class R>
-__device__ __forceinline__ void insert_group1(uint32_t* __restrict__ words, R& res,
-                                              const uint64_t* __restrict__ hashes, uint64_t n,
-                                              bool vec, uint64_t pol, uint64_t g) {
+template <class R, class S>
+__device__ __forceinline__ void insert_group1(uint32_t* __restrict__ words, R& res, const S& src,
+                                              uint64_t n, uint64_t pol, uint64_t g) {
   const unsigned lane = lane_id();
   const uint64_t k = g * 64 + 2 * lane;
   uint64_t h0, h1;
-  load_pair(hashes, k, n, vec, pol, h0, h1);
+  src.pair(k, n, pol, h0, h1);
   res.begin_chunk(g * 64);
   const uint64_t b0 = k < n ? res.block(k, h0) : kNoBlock64;
   const uint64_t b1 = k + 1 < n ? res.block(k + 1, h1) : kNoBlock64;
@@ -261,17 +251,16 @@ __device__ __forceinline__ void insert_group1(uint32_t* __restrict__ words, R& r
   }
 }
 
-template <class R, bool kLanes8>
+template <class R, bool kLanes8, class S = HashInput>
 __global__ void __launch_bounds__(kMaxThreads)
-    insert_kernel(uint32_t* __restrict__ words, R res, const uint64_t* __restrict__ hashes,
-                  uint64_t n, unsigned long long* __restrict__ tiles) {
+    insert_kernel(uint32_t* __restrict__ words, R res, S src, uint64_t n,
+                  unsigned long long* __restrict__ tiles) {
   const uint64_t n_groups = (n + 63) >> 6;
   const uint64_t pol = policy_evict_first();
-  const bool vec = (reinterpret_cast<uintptr_t>(hashes) & 15) == 0;
   UnitIter it(n_groups, tiles);
   for (uint64_t g; it.next(g);) {
-    if (kLanes8) insert_group8(words, res, hashes, n, vec, pol, g);
-    else insert_group1(words, res, hashes, n, vec, pol, g);
+    if (kLanes8) insert_group8(words, res, src, n, pol, g);
+    else insert_group1(words, res, src, n, pol, g);
   }
   res.finish();
 }
@@ -282,22 +271,21 @@ __global__ void __launch_bounds__(kMaxThreads)
 // are held to R::kMinBlocks 512-thread CTAs per SM (<= 42 registers at 3,
 // <= 64 at 2), which keeps occupancy high without spilling; the others may
 // use up to 128 registers so that their loads in flight do not spill.
-template <class R>
+template <class R, class S>
 constexpr int find_min_blocks(bool lanes8, int unroll) {
-  return (lanes8 || unroll >= 4) ? 1 : R::kMinBlocks;
+  return (lanes8 || unroll >= 4 || S::kHeavy) ? 1 : R::kMinBlocks;
 }
 
-template <class R, bool kLanes8, int U, bool kL1Bypass>
-__global__ void __launch_bounds__(kMaxThreads, find_min_blocks<R>(kLanes8, U))
-    find_kernel(const uint32_t* __restrict__ words, R res, const uint64_t* __restrict__ hashes,
-                uint64_t n, uint32_t* __restrict__ out, unsigned long long* __restrict__ tiles) {
+template <class R, bool kLanes8, int U, bool kL1Bypass, class S = HashInput>
+__global__ void __launch_bounds__(kMaxThreads, find_min_blocks<R, S>(kLanes8, U))
+    find_kernel(const uint32_t* __restrict__ words, R res, S src, uint64_t n,
+                uint32_t* __restrict__ out, unsigned long long* __restrict__ tiles) {
   constexpr bool l1_bypass = kL1Bypass;  // block loads skip L1 allocation
   const unsigned lane = lane_id();
   const uint64_t n_groups = (n + 63) >> 6;
   const uint64_t n_out = (n + 31) >> 5;
   const uint64_t pk = policy_evict_first();
   const uint64_t pf = policy_evict_last();
-  const bool vec = (reinterpret_cast<uintptr_t>(hashes) & 15) == 0;
 
   if (!kLanes8) {
     // a unit is U consecutive groups, all loads issued before any test
@@ -308,7 +296,7 @@ __global__ void __launch_bounds__(kMaxThreads, find_min_blocks<R>(kLanes8, U))
       uint64_t h[U][2], b[U][2];
 #pragma unroll
       for (int u = 0; u < U; ++u)
-        load_pair(hashes, (g0 + u) * 64 + 2 * lane, n, vec, pk, h[u][0], h[u][1]);
+        src.pair((g0 + u) * 64 + 2 * lane, n, pk, h[u][0], h[u][1]);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         res.begin_chunk((g0 + u) * 64 < n ? (g0 + u) * 64 : 0);
@@ -352,7 +340,7 @@ __global__ void __launch_bounds__(kMaxThreads, find_min_blocks<R>(kLanes8, U))
     for (uint64_t g; it.next(g);) {
       const uint64_t k = g * 64 + 2 * lane;
       uint64_t h0, h1;
-      load_pair(hashes, k, n, vec, pk, h0, h1);
+      src.pair(k, n, pk, h0, h1);
       res.begin_chunk(g * 64);
       const uint64_t b0 = k < n ? res.block(k, h0) : kNoBlock64;
       const uint64_t b1 = k + 1 < n ? res.block(k + 1, h1) : kNoBlock64;

@@ -52,37 +52,49 @@ inline int cached_occupancy(const void* func, int threads) {
 
 // With `tiles` (a device counter), the launch uses the dynamic in-order
 // schedule: the counter is zeroed on the stream first.
-template <class R>
-sbbf_status launch_insert_t(const Tuning& t, uint32_t* words, R res, const uint64_t* hashes,
-                            uint64_t n, cudaStream_t s, unsigned long long* tiles = nullptr) {
+template <class R, class S>
+sbbf_status launch_insert_src(const Tuning& t, uint32_t* words, R res, S src, uint64_t n,
+                              cudaStream_t s, unsigned long long* tiles = nullptr) {
   if (n == 0) return SBBF_OK;
-  void (*k)(uint32_t*, R, const uint64_t*, uint64_t, unsigned long long*) =
-      t.lanes == 8 ? insert_kernel<R, true> : insert_kernel<R, false>;
+  void (*k)(uint32_t*, R, S, uint64_t, unsigned long long*) =
+      t.lanes == 8 ? insert_kernel<R, true, S> : insert_kernel<R, false, S>;
   const uint64_t groups = (n + 63) / 64;
   const unsigned grid =
       grid_for(groups, t.threads / 32, cached_occupancy(reinterpret_cast<const void*>(k), t.threads));
   if (tiles) SBBF_CUDA(cudaMemsetAsync(tiles, 0, sizeof(unsigned long long), s));
-  k<<<grid, t.threads, 0, s>>>(words, res, hashes, n, tiles);
+  k<<<grid, t.threads, 0, s>>>(words, res, src, n, tiles);
   return launch_status();
 }
 
-template <class R, bool kB>
+template <class R>
+sbbf_status launch_insert_t(const Tuning& t, uint32_t* words, R res, const uint64_t* hashes,
+                            uint64_t n, cudaStream_t s, unsigned long long* tiles = nullptr) {
+  return launch_insert_src(t, words, res, HashInput(hashes), n, s, tiles);
+}
+
+template <class R, bool kB, class S>
 auto find_kernel_pick(const Tuning& t) {
-  void (*k)(const uint32_t*, R, const uint64_t*, uint64_t, uint32_t*, unsigned long long*) =
-      nullptr;
+  void (*k)(const uint32_t*, R, S, uint64_t, uint32_t*, unsigned long long*) = nullptr;
   if (t.lanes == 8) {
-    k = t.unroll == 1 ? find_kernel<R, true, 1, kB>
-        : t.unroll == 2 ? find_kernel<R, true, 2, kB> : find_kernel<R, true, 4, kB>;
+    k = t.unroll == 1 ? find_kernel<R, true, 1, kB, S>
+        : t.unroll == 2 ? find_kernel<R, true, 2, kB, S> : find_kernel<R, true, 4, kB, S>;
   } else {
-    k = t.unroll == 1 ? find_kernel<R, false, 1, kB>
-        : t.unroll == 2 ? find_kernel<R, false, 2, kB> : find_kernel<R, false, 4, kB>;
+    k = t.unroll == 1 ? find_kernel<R, false, 1, kB, S>
+        : t.unroll == 2 ? find_kernel<R, false, 2, kB, S> : find_kernel<R, false, 4, kB, S>;
   }
   return k;
 }
 
-template <class R>
+template <class R, class S = HashInput>
 auto find_kernel_for(const Tuning& t) {
-  return t.l1_bypass ? find_kernel_pick<R, true>(t) : find_kernel_pick<R, false>(t);
+  return t.l1_bypass ? find_kernel_pick<R, true, S>(t) : find_kernel_pick<R, false, S>(t);
+}
+
+// The one shape a fused key-hashing lookup is built in (one lane per key, two
+// groups in flight), with or without L1 allocation of block loads.
+template <class R, class S>
+auto find_kernel_fused(bool l1_bypass) {
+  return l1_bypass ? find_kernel<R, false, 2, true, S> : find_kernel<R, false, 2, false, S>;
 }
 
 // CTAs for a lookup launch of n keys with shape t.
@@ -100,7 +112,19 @@ sbbf_status launch_find_t(const Tuning& t, const uint32_t* words, R res, const u
   auto k = find_kernel_for<R>(t);
   const unsigned grid = find_grid(t, n, reinterpret_cast<const void*>(k));
   if (tiles) SBBF_CUDA(cudaMemsetAsync(tiles, 0, sizeof(unsigned long long), s));
-  k<<<grid, t.threads, 0, s>>>(words, res, hashes, n, out, tiles);
+  k<<<grid, t.threads, 0, s>>>(words, res, HashInput(hashes), n, out, tiles);
+  return launch_status();
+}
+
+// Lookup with a key source other than plain hashes, in the fused shape.
+template <class R, class S>
+sbbf_status launch_find_src(bool l1_bypass, const uint32_t* words, R res, S src, uint64_t n,
+                            uint32_t* out, cudaStream_t s) {
+  if (n == 0) return SBBF_OK;
+  const Tuning t = {256, 1, 2, l1_bypass ? 1 : 0};
+  auto k = find_kernel_fused<R, S>(l1_bypass);
+  const unsigned grid = find_grid(t, n, reinterpret_cast<const void*>(k));
+  k<<<grid, t.threads, 0, s>>>(words, res, src, n, out, nullptr);
   return launch_status();
 }
 

@@ -545,7 +545,7 @@ sbbf_status sbbf_multi_graph_create(sbbf_multi_t* m, sbbf_multi_graph_t** out) {
   // Placeholder arguments; every launch sets the real ones.
   Segments r = seg_resolver(m, nullptr);
   uint32_t* words = m->words;
-  const uint64_t* h = nullptr;
+  HashInput h(nullptr);
   uint64_t n = 0;
   uint32_t* o = nullptr;
   unsigned long long* ti = m->d_tiles;
@@ -596,8 +596,7 @@ sbbf_status sbbf_multi_graph_launch(sbbf_multi_graph_t* g, const uint64_t* d_ins
   sbbf_multi_t* m = g->m;
   Segments ri = seg_resolver(m, d_ins_offsets), rf = seg_resolver(m, d_q_offsets);
   uint32_t* words = m->words;
-  const uint64_t* hi = d_ins;
-  const uint64_t* hq = d_q;
+  HashInput hi(d_ins), hq(d_q);
   uint64_t ni = n_ins, nq = n_q;
   uint32_t* o = d_out_bits;
   unsigned long long* ti = m->d_tiles;

@@ -320,7 +320,6 @@ __global__ void __launch_bounds__(256)
   const uint64_t groups_per_tile = static_cast<uint64_t>(wpc) * kTileRounds;
   const uint64_t keys_per_tile = groups_per_tile * 64;
   const uint64_t pol = policy_evict_first();
-  const bool vec = (reinterpret_cast<uintptr_t>(keys) & 15) == 0;
   OneFilter res{nb};
   if (wic == 0) {
     uint64_t lo, hi, a, b;
@@ -353,7 +352,7 @@ __global__ void __launch_bounds__(256)
     }
     for (int r = 0; r < kTileRounds; ++r) {
       const uint64_t g = g0 + static_cast<uint64_t>(r) * wpc + wic;
-      if (g < n_groups) insert_group8(words, res, keys, n, vec, pol, g);
+      if (g < n_groups) insert_group8(words, res, HashInput(keys), n, pol, g);
     }
   }
 }
@@ -375,7 +374,6 @@ __global__ void __launch_bounds__(256)
   const uint64_t keys_per_tile = groups_per_tile * 64;
   const uint64_t pk = policy_evict_first();
   const uint64_t pf = policy_evict_last();
-  const bool vec = (reinterpret_cast<uintptr_t>(keys) & 15) == 0;
   if (wic == 0) {
     uint64_t lo, hi, a, b;
     slice_bytes(nb, 0, lo, hi);
@@ -410,7 +408,7 @@ __global__ void __launch_bounds__(256)
       if (g >= n_groups) continue;
       const uint64_t k = g * 64 + 2 * lane;
       uint64_t h0, h1;
-      load_pair(keys, k, n, vec, pk, h0, h1);
+      HashInput(keys).pair(k, n, pk, h0, h1);
       uint32_t w0[8], w1[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) w0[i] = w1[i] = 0;

@@ -9,12 +9,6 @@
 #include "sbbf.h"
 #include "sbbf_host.cuh"
 
-namespace sbbf {
-sbbf_status launch_insert(uint32_t*, uint32_t, const uint64_t*, uint64_t, cudaStream_t);
-sbbf_status launch_find(const uint32_t*, uint32_t, const uint64_t*, uint64_t, uint32_t*,
-                        cudaStream_t);
-}  // namespace sbbf
-
 struct sbbf_host_pipe {
   size_t chunk;
   uint64_t* d_keys[2];
@@ -103,7 +97,7 @@ sbbf_status sbbf_insert_hashes_host(sbbf_t* f, sbbf_host_pipe_t* p, const uint64
   return run_chunks(p, n, stream, [&](size_t off, size_t cnt, int i) -> sbbf_status {
     SBBF_CUDA(cudaMemcpyAsync(p->d_keys[i], h_hashes + off, cnt * sizeof(uint64_t),
                               cudaMemcpyHostToDevice, p->s[i]));
-    return launch_insert(f->words, f->num_blocks, p->d_keys[i], cnt, p->s[i]);
+    return launch_insert_filter(f, p->d_keys[i], cnt, p->s[i]);
   });
 }
 
@@ -115,7 +109,7 @@ sbbf_status sbbf_find_hashes_host(const sbbf_t* f, sbbf_host_pipe_t* p, const ui
   return run_chunks(p, n, stream, [&](size_t off, size_t cnt, int i) -> sbbf_status {
     SBBF_CUDA(cudaMemcpyAsync(p->d_keys[i], h_hashes + off, cnt * sizeof(uint64_t),
                               cudaMemcpyHostToDevice, p->s[i]));
-    sbbf_status st = launch_find(f->words, f->num_blocks, p->d_keys[i], cnt, p->d_bits[i], p->s[i]);
+    sbbf_status st = launch_find_filter(f, p->d_keys[i], cnt, p->d_bits[i], p->s[i]);
     if (st != SBBF_OK) return st;
     // off is a multiple of the chunk (a multiple of 64), so word-aligned.
     SBBF_CUDA(cudaMemcpyAsync(h_out_bits + off / 32, p->d_bits[i], ((cnt + 31) / 32) * 4,

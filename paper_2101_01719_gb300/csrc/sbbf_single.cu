@@ -14,6 +14,7 @@
 #include "sbbf.h"
 #include "sbbf_device.cuh"
 #include "sbbf_host.cuh"
+#include "sbbf_lanes.cuh"
 #include "sbbf_launch.cuh"
 
 namespace sbbf {
@@ -57,7 +58,7 @@ sbbf_status launch_find(const uint32_t* words, uint32_t num_blocks, const uint64
 }
 
 sbbf_status launch_union(uint32_t* dst, const uint32_t* src, uint64_t n_words, cudaStream_t s) {
-  const uint64_t n16 = n_words / 4;  // n_words is a multiple of 8
+  const uint64_t n16 = n_words / 4;  // n_words is a multiple of 4
   static int occ = occupancy(union_kernel, kThreads);
   union_kernel<<<grid_for(n16, kThreads, occ), kThreads, 0, s>>>(
       reinterpret_cast<uint4*>(dst), reinterpret_cast<const uint4*>(src), n16);
@@ -74,12 +75,21 @@ sbbf_status launch_clear(uint32_t* dst, uint64_t n_words, cudaStream_t s) {
 
 static bool on_device(const sbbf_t* f) { return f->device == current_device(); }
 
-uint64_t partition_scratch_bytes(uint32_t num_blocks, uint64_t n, bool with_index);
-sbbf_status launch_insert_partitioned(uint32_t* words, uint32_t num_blocks, const uint64_t* hashes,
-                                      uint64_t n, void* scratch, cudaStream_t s);
-sbbf_status launch_find_partitioned(const uint32_t* words, uint32_t num_blocks,
-                                    const uint64_t* hashes, uint64_t n, uint32_t* d_out,
-                                    void* scratch, cudaStream_t s);
+sbbf_status launch_insert_filter(const sbbf_t* f, const uint64_t* d_hashes, uint64_t n,
+                                 cudaStream_t s) {
+  if (f->lanes != 8)
+    return launch_insert_lanes(static_cast<int>(f->lanes), f->words, f->num_blocks,
+                               HashInput(d_hashes), n, s);
+  return launch_insert(f->words, f->num_blocks, d_hashes, n, s);
+}
+
+sbbf_status launch_find_filter(const sbbf_t* f, const uint64_t* d_hashes, uint64_t n,
+                               uint32_t* d_out, cudaStream_t s) {
+  if (f->lanes != 8)
+    return launch_find_lanes(static_cast<int>(f->lanes), f->words, f->num_blocks,
+                             HashInput(d_hashes), n, d_out, s);
+  return launch_find(f->words, f->num_blocks, d_hashes, n, d_out, s);
+}
 
 // Batches at least this large go through the partitioned insert when the
 // filter is at least kPartitionMinBytes (automatic mode).  Measured on GB300:
@@ -95,8 +105,8 @@ constexpr uint64_t kPartitionMinBytes = 256ull << 20;
 // the batch touches each block about once (inserts: >= 1 key per block; a
 // 3e9-key batch into 2^30 blocks runs 2.3x faster) or more (lookups: >= 2;
 // 1e9 lookups into 128.9M blocks run 1.8x faster, into 2^30 blocks 9% slower).
-static bool want_partition(const sbbf_t* f, uint64_t n, uint64_t min_keys_per_block) {
-  if (f->partition_mode == SBBF_PARTITION_OFF) return false;
+bool want_partition(const sbbf_t* f, uint64_t n, uint64_t min_keys_per_block) {
+  if (f->lanes != 8 || f->partition_mode == SBBF_PARTITION_OFF) return false;
   if (f->partition_mode == SBBF_PARTITION_ON) return true;
   return n >= kPartitionMinKeys &&
          static_cast<uint64_t>(f->num_blocks) * 32 >= kPartitionMinBytes &&
@@ -104,7 +114,7 @@ static bool want_partition(const sbbf_t* f, uint64_t n, uint64_t min_keys_per_bl
 }
 
 // Grows the filter's scratch (cudaMalloc, synchronous) to hold `bytes`.
-static sbbf_status ensure_scratch(sbbf_t* f, size_t bytes) {
+sbbf_status ensure_scratch(sbbf_t* f, size_t bytes) {
   if (f->scratch_bytes >= bytes) return SBBF_OK;
   if (f->scratch) {
     cudaError_t e = cudaFree(f->scratch);
@@ -127,21 +137,21 @@ using namespace sbbf;
 
 extern "C" {
 
-sbbf_status sbbf_create(uint32_t num_blocks, sbbf_t** out) {
-  if (!out || num_blocks == 0) return SBBF_EINVAL;
+sbbf_status sbbf_create_lanes(uint32_t num_blocks, uint32_t lanes, sbbf_t** out) {
+  if (!out || num_blocks == 0 || (lanes != 4 && lanes != 8 && lanes != 16)) return SBBF_EINVAL;
   *out = nullptr;
   sbbf_t* f = static_cast<sbbf_t*>(std::calloc(1, sizeof(sbbf_t)));
   if (!f) return SBBF_ENOMEM;
-  const size_t bytes = static_cast<size_t>(num_blocks) * 32;
-  cudaError_t e = cudaMalloc(&f->words, bytes);
+  f->num_blocks = num_blocks;
+  f->lanes = lanes;
+  cudaError_t e = cudaMalloc(&f->words, filter_bytes(f));
   if (e != cudaSuccess) {
     std::free(f);
     return record_cuda(e);
   }
-  f->num_blocks = num_blocks;
   f->device = current_device();
   f->owns = 1;
-  sbbf_status st = launch_clear(f->words, static_cast<uint64_t>(num_blocks) * 8, nullptr);
+  sbbf_status st = launch_clear(f->words, filter_words(f), nullptr);
   if (st == SBBF_OK) {
     e = cudaStreamSynchronize(nullptr);
     if (e != cudaSuccess) st = record_cuda(e);
@@ -155,18 +165,29 @@ sbbf_status sbbf_create(uint32_t num_blocks, sbbf_t** out) {
   return SBBF_OK;
 }
 
-sbbf_status sbbf_wrap(uint32_t* d_words, uint32_t num_blocks, sbbf_t** out) {
+sbbf_status sbbf_create(uint32_t num_blocks, sbbf_t** out) {
+  return sbbf_create_lanes(num_blocks, 8, out);
+}
+
+sbbf_status sbbf_wrap_lanes(uint32_t* d_words, uint32_t num_blocks, uint32_t lanes,
+                            sbbf_t** out) {
   if (!out || !d_words || num_blocks == 0) return SBBF_EINVAL;
+  if (lanes != 4 && lanes != 8 && lanes != 16) return SBBF_EINVAL;
   if (reinterpret_cast<uintptr_t>(d_words) & 31) return SBBF_EINVAL;
   *out = nullptr;
   sbbf_t* f = static_cast<sbbf_t*>(std::calloc(1, sizeof(sbbf_t)));
   if (!f) return SBBF_ENOMEM;
   f->words = d_words;
   f->num_blocks = num_blocks;
+  f->lanes = lanes;
   f->device = current_device();
   f->owns = 0;
   *out = f;
   return SBBF_OK;
+}
+
+sbbf_status sbbf_wrap(uint32_t* d_words, uint32_t num_blocks, sbbf_t** out) {
+  return sbbf_wrap_lanes(d_words, num_blocks, 8, out);
 }
 
 sbbf_status sbbf_create_from_host(const uint32_t* h_words, uint32_t num_blocks, sbbf_t** out) {
@@ -200,16 +221,18 @@ sbbf_status sbbf_destroy(sbbf_t* f) {
 
 uint32_t sbbf_num_blocks(const sbbf_t* f) { return f ? f->num_blocks : 0; }
 
+uint32_t sbbf_lanes(const sbbf_t* f) { return f ? f->lanes : 0; }
+
 sbbf_status sbbf_device_words(const sbbf_t* f, uint32_t** d_words, size_t* bytes) {
   if (!f) return SBBF_EINVAL;
   if (d_words) *d_words = f->words;
-  if (bytes) *bytes = static_cast<size_t>(f->num_blocks) * 32;
+  if (bytes) *bytes = filter_bytes(f);
   return SBBF_OK;
 }
 
 sbbf_status sbbf_clear(sbbf_t* f, sbbf_stream_t stream) {
   if (!f || !on_device(f)) return SBBF_EINVAL;
-  return launch_clear(f->words, static_cast<uint64_t>(f->num_blocks) * 8, stream);
+  return launch_clear(f->words, filter_words(f), stream);
 }
 
 sbbf_status sbbf_insert_hashes(sbbf_t* f, const uint64_t* d_hashes, size_t n,
@@ -224,7 +247,7 @@ sbbf_status sbbf_insert_hashes(sbbf_t* f, const uint64_t* d_hashes, size_t n,
     if (st != SBBF_ENOMEM || f->partition_mode == SBBF_PARTITION_ON) return st;
     // automatic mode without room for the scratch: insert unpartitioned
   }
-  return launch_insert(f->words, f->num_blocks, d_hashes, n, stream);
+  return launch_insert_filter(f, d_hashes, n, stream);
 }
 
 sbbf_status sbbf_set_partitioning(sbbf_t* f, int mode) {
@@ -251,21 +274,21 @@ sbbf_status sbbf_find_hashes(const sbbf_t* f, const uint64_t* d_hashes, size_t n
                                      stream);
     if (st != SBBF_ENOMEM || f->partition_mode == SBBF_PARTITION_ON) return st;
   }
-  return launch_find(f->words, f->num_blocks, d_hashes, n, d_out_bits, stream);
+  return launch_find_filter(f, d_hashes, n, d_out_bits, stream);
 }
 
 sbbf_status sbbf_union(sbbf_t* dst, const sbbf_t* src, sbbf_stream_t stream) {
-  if (!dst || !src || dst->num_blocks != src->num_blocks) return SBBF_EINVAL;
+  if (!dst || !src || dst->num_blocks != src->num_blocks || dst->lanes != src->lanes)
+    return SBBF_EINVAL;
   if (!on_device(dst) || !on_device(src)) return SBBF_EINVAL;
   if (dst->words == src->words) return SBBF_OK;  // x | x == x
-  return launch_union(dst->words, src->words, static_cast<uint64_t>(dst->num_blocks) * 8,
-                      stream);
+  return launch_union(dst->words, src->words, filter_words(dst), stream);
 }
 
 sbbf_status sbbf_copy_to_host(const sbbf_t* f, uint32_t* h_words, size_t bytes,
                               sbbf_stream_t stream) {
   if (!f || !h_words) return SBBF_EINVAL;
-  const size_t need = static_cast<size_t>(f->num_blocks) * 32;
+  const size_t need = filter_bytes(f);
   if (bytes < need) return SBBF_EINVAL;
   SBBF_CUDA(cudaMemcpyAsync(h_words, f->words, need, cudaMemcpyDeviceToHost, stream));
   SBBF_CUDA(cudaStreamSynchronize(stream));

@@ -37,6 +37,17 @@ SIGNATURES = {
     "sbbf_version": (_u32, []),
     "sbbf_create": (_int, [_u32, _c.POINTER(_P)]),
     "sbbf_wrap": (_int, [_P, _u32, _c.POINTER(_P)]),
+    "sbbf_create_lanes": (_int, [_u32, _u32, _c.POINTER(_P)]),
+    "sbbf_wrap_lanes": (_int, [_P, _u32, _u32, _c.POINTER(_P)]),
+    "sbbf_lanes": (_u32, [_P]),
+    "sbbf_serialized_size": (_sz, [_P]),
+    "sbbf_serialize": (_int, [_P, _P, _sz, _P]),
+    "sbbf_deserialize": (_int, [_P, _sz, _c.POINTER(_P)]),
+    "sbbf_parquet_header": (_int, [_u64, _P, _sz, _c.POINTER(_sz)]),
+    "sbbf_parquet_parse_header": (_int, [_P, _sz, _c.POINTER(_u64), _c.POINTER(_sz)]),
+    "sbbf_parquet_size": (_sz, [_P]),
+    "sbbf_export_parquet": (_int, [_P, _P, _sz, _c.POINTER(_sz), _P]),
+    "sbbf_import_parquet": (_int, [_P, _sz, _c.POINTER(_P), _c.POINTER(_sz)]),
     "sbbf_create_from_host": (_int, [_P, _u32, _c.POINTER(_P)]),
     "sbbf_destroy": (_int, [_P]),
     "sbbf_num_blocks": (_u32, [_P]),
@@ -51,6 +62,12 @@ SIGNATURES = {
     "sbbf_host_pipe_destroy": (_int, [_P]),
     "sbbf_insert_hashes_host": (_int, [_P, _P, _P, _sz, _P]),
     "sbbf_find_hashes_host": (_int, [_P, _P, _P, _sz, _P, _P]),
+    "sbbf_hash_keys": (_int, [_P, _u32, _sz, _u64, _P, _P]),
+    "sbbf_hash_bytes": (_int, [_P, _P, _sz, _u64, _P, _P]),
+    "sbbf_insert_keys": (_int, [_P, _P, _u32, _sz, _u64, _P]),
+    "sbbf_find_keys": (_int, [_P, _P, _u32, _sz, _u64, _P, _P]),
+    "sbbf_insert_bytes": (_int, [_P, _P, _P, _sz, _u64, _P]),
+    "sbbf_find_bytes": (_int, [_P, _P, _P, _sz, _u64, _P, _P]),
     "sbbf_fill_splitmix64": (_int, [_P, _sz, _u64, _u64, _P]),
     "sbbf_fill_queries": (_int, [_P, _sz, _u64, _u64, _u64, _u64, _u64, _u64, _u64, _P]),
     "sbbf_count_bits": (_int, [_P, _sz, _P, _P]),
@@ -147,31 +164,181 @@ def _hashes_ptr(t: torch.Tensor, device) -> int:
     return t.data_ptr()
 
 
+_KEY_DTYPES = (torch.int32, torch.int64) + tuple(
+    getattr(torch, n) for n in ("uint32", "uint64") if hasattr(torch, n))
+
+
+def _keys_arg(t: torch.Tensor, device):
+    """(pointer, key_bytes) of a fixed-width key tensor (4- or 8-byte ints)."""
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("keys must be a CUDA tensor")
+    if t.dtype not in _KEY_DTYPES:
+        raise TypeError("keys must be 32- or 64-bit integers")
+    if not t.is_contiguous():
+        raise ValueError("keys must be contiguous")
+    if device is not None and t.device != device:
+        raise ValueError("keys are on %s, filter on %s" % (t.device, device))
+    return t.data_ptr(), t.element_size()
+
+
+def _bytes_args(data: torch.Tensor, offsets: torch.Tensor, device):
+    """(data pointer, offsets pointer, n) of byte-string keys: key k is
+    data[offsets[k]:offsets[k+1]] (data uint8, offsets int64 of n + 1)."""
+    for name, t in (("data", data), ("offsets", offsets)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+            raise TypeError("%s must be a contiguous CUDA tensor" % name)
+        if device is not None and t.device != device:
+            raise ValueError("%s is on %s, filter on %s" % (name, t.device, device))
+    if data.dtype != torch.uint8:
+        raise TypeError("data must be uint8")
+    if offsets.dtype != torch.int64 or offsets.dim() != 1 or offsets.numel() < 1:
+        raise TypeError("offsets must be a 1-D int64 tensor of n + 1 entries")
+    if data.numel() == 0:  # all keys empty: any readable address will do
+        data = torch.zeros(8, dtype=torch.uint8, device=offsets.device)
+    return data.data_ptr(), offsets.data_ptr(), offsets.numel() - 1, data
+
+
+def hash_keys(keys: torch.Tensor, seed: int = 0, out: torch.Tensor | None = None, stream=None):
+    """XXH64 of each fixed-width key (its little-endian bytes) on the device."""
+    ptr, kb = _keys_arg(keys, None)
+    n = keys.numel()
+    if out is None:
+        out = torch.empty(n, dtype=torch.int64, device=keys.device)
+    with torch.cuda.device(keys.device):
+        check(lib().sbbf_hash_keys(ptr, kb, n, seed, out.data_ptr(), stream_handle(stream)),
+              "sbbf_hash_keys")
+    return out
+
+
+def hash_bytes(data: torch.Tensor, offsets: torch.Tensor, seed: int = 0,
+               out: torch.Tensor | None = None, stream=None):
+    """XXH64 of each byte string data[offsets[k]:offsets[k+1]] on the device."""
+    dp, op, n, _keep = _bytes_args(data, offsets, None)
+    if out is None:
+        out = torch.empty(n, dtype=torch.int64, device=offsets.device)
+    with torch.cuda.device(offsets.device):
+        check(lib().sbbf_hash_bytes(dp, op, n, seed, out.data_ptr(), stream_handle(stream)),
+              "sbbf_hash_bytes")
+    return out
+
+
 def out_words(n: int) -> int:
     """Words of packed lookup output for n hashes."""
     return (n + 31) // 32
 
 
-class Filter:
-    """A split block Bloom filter of ``num_blocks`` 256-bit blocks whose words
-    live in a torch tensor (``self.words``, int32, ``num_blocks * 8``)."""
+def _host_bytes(buf):
+    import numpy as np
+    a = np.frombuffer(buf, dtype=np.uint8) if isinstance(buf, (bytes, bytearray, memoryview)) \
+        else np.ascontiguousarray(buf, dtype=np.uint8)
+    return a
 
-    def __init__(self, num_blocks: int, device=None, words: torch.Tensor | None = None):
+
+def parquet_header(num_bytes: int) -> bytes:
+    """Thrift BloomFilterHeader of a Parquet bitset of num_bytes bytes (host)."""
+    n = _sz()
+    check(lib().sbbf_parquet_header(num_bytes, None, 0, _c.byref(n)), "sbbf_parquet_header")
+    out = (_c.c_uint8 * n.value)()
+    check(lib().sbbf_parquet_header(num_bytes, out, n.value, _c.byref(n)), "sbbf_parquet_header")
+    return bytes(out)
+
+
+def parse_parquet_header(buf):
+    """(bitset bytes, header length) of a Parquet Bloom filter (host)."""
+    a = _host_bytes(buf)
+    nb, hl = _u64(), _sz()
+    check(lib().sbbf_parquet_parse_header(a.ctypes.data, a.size, _c.byref(nb), _c.byref(hl)),
+          "sbbf_parquet_parse_header")
+    return int(nb.value), int(hl.value)
+
+
+class _DeviceWords:
+    """__cuda_array_interface__ over a library-owned filter's words."""
+
+    def __init__(self, ptr, n_words):
+        self.__cuda_array_interface__ = {"shape": (n_words,), "typestr": "<i4",
+                                         "data": (ptr, False), "version": 3}
+
+
+class Filter:
+    """A split block Bloom filter of ``num_blocks`` blocks of ``lanes`` 32-bit
+    words (8, the paper's; 4 or 16) whose words live in a torch tensor
+    (``self.words``, int32, ``num_blocks * lanes``)."""
+
+    def __init__(self, num_blocks: int, device=None, words: torch.Tensor | None = None,
+                 lanes: int = 8):
         if num_blocks <= 0 or num_blocks >= 2**32:
             raise ValueError("num_blocks must be in [1, 2^32)")
+        if lanes not in (4, 8, 16):
+            raise ValueError("lanes must be 4, 8 or 16")
         if words is None:
             dev = (torch.device("cuda", torch.cuda.current_device()) if device is None
                    else torch.device(device))
-            words = torch.zeros(num_blocks * 8, dtype=torch.int32, device=dev)
-        if words.numel() != num_blocks * 8 or not words.is_cuda or not words.is_contiguous():
-            raise ValueError("words must be a contiguous CUDA tensor of num_blocks*8 int32")
+            words = torch.zeros(num_blocks * lanes, dtype=torch.int32, device=dev)
+        if words.numel() != num_blocks * lanes or not words.is_cuda or not words.is_contiguous():
+            raise ValueError("words must be a contiguous CUDA tensor of num_blocks*lanes int32")
         self.words = words
         self.num_blocks = int(num_blocks)
+        self.lanes = int(lanes)
         self.device = words.device
         h = _P()
         with torch.cuda.device(self.device):
-            check(lib().sbbf_wrap(words.data_ptr(), num_blocks, _c.byref(h)), "sbbf_wrap")
+            check(lib().sbbf_wrap_lanes(words.data_ptr(), num_blocks, lanes, _c.byref(h)),
+                  "sbbf_wrap_lanes")
         self._h = h
+
+    @classmethod
+    def _adopt(cls, h):
+        """A torch-backed copy of a library-owned filter handle (destroyed)."""
+        try:
+            lanes, nb = lib().sbbf_lanes(h), lib().sbbf_num_blocks(h)
+            ptr, nbytes = _P(), _sz()
+            check(lib().sbbf_device_words(h, _c.byref(ptr), _c.byref(nbytes)), "sbbf_device_words")
+            dev = torch.device("cuda", torch.cuda.current_device())
+            words = torch.as_tensor(_DeviceWords(ptr.value, nbytes.value // 4), device=dev).clone()
+            torch.cuda.synchronize(dev)
+        finally:
+            lib().sbbf_destroy(h)
+        return cls(nb, words=words, lanes=lanes)
+
+    def serialize(self, stream=None):
+        """The filter in the native checkpoint format (numpy uint8)."""
+        import numpy as np
+        n = lib().sbbf_serialized_size(self._h)
+        out = np.empty(n, np.uint8)
+        with torch.cuda.device(self.device):
+            check(lib().sbbf_serialize(self._h, out.ctypes.data, n, stream_handle(stream)),
+                  "sbbf_serialize")
+        return out
+
+    @classmethod
+    def deserialize(cls, buf) -> "Filter":
+        a = _host_bytes(buf)
+        h = _P()
+        check(lib().sbbf_deserialize(a.ctypes.data, a.size, _c.byref(h)), "sbbf_deserialize")
+        return cls._adopt(h)
+
+    def export_parquet(self, stream=None):
+        """Header and bitset in Parquet's Bloom-filter format (numpy uint8)."""
+        import numpy as np
+        n = lib().sbbf_parquet_size(self._h)
+        if n == 0:
+            raise ValueError("Parquet filters have 8 lanes and fewer than 2^31 bytes")
+        out = np.empty(n, np.uint8)
+        w = _sz()
+        with torch.cuda.device(self.device):
+            check(lib().sbbf_export_parquet(self._h, out.ctypes.data, n, _c.byref(w),
+                                            stream_handle(stream)), "sbbf_export_parquet")
+        return out[:w.value]
+
+    @classmethod
+    def import_parquet(cls, buf):
+        """(Filter, bytes consumed) from a Parquet Bloom filter."""
+        a = _host_bytes(buf)
+        h, used = _P(), _sz()
+        check(lib().sbbf_import_parquet(a.ctypes.data, a.size, _c.byref(h), _c.byref(used)),
+              "sbbf_import_parquet")
+        return cls._adopt(h), int(used.value)
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -210,6 +377,49 @@ class Filter:
         with torch.cuda.device(self.device):
             check(lib().sbbf_find_hashes(self._h, ptr, n, out.data_ptr(), stream_handle(stream)),
                   "sbbf_find_hashes")
+        return out
+
+    def _out(self, n, out):
+        if out is None:
+            return torch.empty(out_words(n), dtype=torch.int32, device=self.device)
+        if out.numel() < out_words(n) or not out.is_cuda or out.element_size() != 4:
+            raise ValueError("out must be a CUDA int32 tensor of (n+31)//32 words")
+        return out
+
+    def insert_keys(self, keys: torch.Tensor, seed: int = 0, stream=None):
+        """Insert fixed-width keys, hashed with XXH64 inside the insert kernel."""
+        ptr, kb = _keys_arg(keys, self.device)
+        with torch.cuda.device(self.device):
+            check(lib().sbbf_insert_keys(self._h, ptr, kb, keys.numel(), seed,
+                                         stream_handle(stream)), "sbbf_insert_keys")
+        return self
+
+    def find_keys(self, keys: torch.Tensor, seed: int = 0, out: torch.Tensor | None = None,
+                  stream=None):
+        ptr, kb = _keys_arg(keys, self.device)
+        n = keys.numel()
+        out = self._out(n, out)
+        with torch.cuda.device(self.device):
+            check(lib().sbbf_find_keys(self._h, ptr, kb, n, seed, out.data_ptr(),
+                                       stream_handle(stream)), "sbbf_find_keys")
+        return out
+
+    def insert_bytes(self, data: torch.Tensor, offsets: torch.Tensor, seed: int = 0,
+                     stream=None):
+        """Insert byte-string keys data[offsets[k]:offsets[k+1]] (XXH64 in-kernel)."""
+        dp, op, n, _keep = _bytes_args(data, offsets, self.device)
+        with torch.cuda.device(self.device):
+            check(lib().sbbf_insert_bytes(self._h, dp, op, n, seed, stream_handle(stream)),
+                  "sbbf_insert_bytes")
+        return self
+
+    def find_bytes(self, data: torch.Tensor, offsets: torch.Tensor, seed: int = 0,
+                   out: torch.Tensor | None = None, stream=None):
+        dp, op, n, _keep = _bytes_args(data, offsets, self.device)
+        out = self._out(n, out)
+        with torch.cuda.device(self.device):
+            check(lib().sbbf_find_bytes(self._h, dp, op, n, seed, out.data_ptr(),
+                                        stream_handle(stream)), "sbbf_find_bytes")
         return out
 
     def union_(self, other: "Filter", stream=None):
