@@ -54,6 +54,11 @@ def parse_args(argv=None):
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="approximate CPU work for the oracle baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--keys", choices=["hashes", "u64", "u32"], default="hashes",
+                   help="measurement variant: insert/look up raw 8- or 4-byte keys hashed "
+                        "with XXH64 inside the kernels instead of precomputed hashes")
+    p.add_argument("--lanes", type=int, choices=[4, 8, 16], default=8,
+                   help="measurement variant: 4- or 16-lane blocks (same filter bytes)")
     p.add_argument("--eager", action="store_true",
                    help="launch each kernel from Python instead of replaying CUDA graphs")
     p.add_argument("--requests", type=int, default=0,
@@ -173,15 +178,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# Sources the single-filter lookup kernel (the dominant kernel) is compiled
+# from: its template, device helpers, key sources, launch shapes and the
+# translation unit that instantiates it.
+DOMINANT_SOURCES = ("sbbf_device.cuh", "sbbf_kernels.cuh", "sbbf_keys.cuh", "sbbf_launch.cuh",
+                    "sbbf_single.cu")
+
+
 def kernel_sources_digest() -> str:
-    """Digest of the CUDA sources; a stored ncu figure applies only while the
-    kernels are unchanged."""
+    """Digest of the dominant kernel's sources; a stored ncu figure applies
+    only while that kernel is unchanged."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2101_01719_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, name), "rb") as fh:
-                h.update(name.encode() + fh.read())
+    for name in DOMINANT_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
@@ -224,18 +235,26 @@ def run_ours(args):
     # the lookup stream (units sharded by rank, no data-path collective).
     ins = wl.gen_inserts(w, 0, w.n_insert, device=dev)
     qry = wl.gen_queries(w, lookup_slice_start(rank, w.n_lookup), w.n_lookup, device=dev)
+    if args.keys == "u32":  # 4-byte keys: the high half of each generated value
+        ins = (ins >> 32).to(torch.int32)
+        qry = (qry >> 32).to(torch.int32)
     out = torch.empty(sb.out_words(w.n_lookup), dtype=torch.int32, device=dev)
-    f = sb.Filter(w.num_blocks, device=dev)
+    num_blocks = w.num_blocks * 8 // args.lanes  # the same filter bytes at any lane count
+    f = sb.Filter(num_blocks, device=dev, lanes=args.lanes)
     torch.cuda.synchronize()
+    variant = args.keys != "hashes" or args.lanes != 8
+    do_insert = f.insert if args.keys == "hashes" else f.insert_keys
+    do_find = ((lambda q, out: f.find(q, out=out)) if args.keys == "hashes"
+               else (lambda q, out: f.find_keys(q, out=out)))
 
     def insert_all():
         for s0, cnt in batches:
-            f.insert(ins[s0:s0 + cnt])
+            do_insert(ins[s0:s0 + cnt])
 
     def step():
         f.clear()
         insert_all()
-        f.find(qry, out=out)
+        do_find(qry, out)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -246,7 +265,7 @@ def run_ours(args):
     graphs = {}
     if not args.eager:
         for name, fn in (("step", step), ("insert", insert_all),
-                         ("find", lambda: f.find(qry, out=out))):
+                         ("find", lambda: do_find(qry, out))):
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g):
                 fn()
@@ -296,7 +315,7 @@ def run_ours(args):
         find_ms = per_call_ms(graphs["find"].replay, reps)
     else:
         insert_ms = per_call_ms(insert_all, reps)
-        find_ms = per_call_ms(lambda: f.find(qry, out=out), reps)
+        find_ms = per_call_ms(lambda: do_find(qry, out), reps)
     keys_per_step = w.n_insert + w.n_lookup
     value = aggregate([keys_per_step * args.steps] * world, slowest_ms / 1e3) / 1e9
 
@@ -305,7 +324,7 @@ def run_ours(args):
 
     # end to end through the host-buffer C-ABI calls (pinned host memory)
     e2e = None
-    if args.e2e_steps > 0:
+    if args.e2e_steps > 0 and not variant:
         h_ins = ins.cpu().pin_memory()
         h_q = qry.cpu().pin_memory()
         h_out = torch.empty(sb.out_words(w.n_lookup), dtype=torch.int32).pin_memory()
@@ -332,10 +351,13 @@ def run_ours(args):
     l2_bytes = props.L2_cache_size if hasattr(props, "L2_cache_size") else 126 * 2**20
     l2_resident = w.filter_bytes < l2_bytes / 2
     per_key = LOOKUP_HBM_BYTES_L2_RESIDENT if l2_resident else LOOKUP_HBM_BYTES_HBM_RESIDENT
+    key_bytes_less = 4 if args.keys == "u32" else 0  # 4-byte keys instead of 8-byte hashes
+    per_key -= key_bytes_less
     achieved = per_key * w.n_lookup / (find_ms / 1e3) / 1e9
     ins_per_key = INSERT_HBM_BYTES_L2_RESIDENT if l2_resident else INSERT_HBM_BYTES_HBM_RESIDENT
+    ins_per_key -= key_bytes_less
     ins_achieved = ins_per_key * w.n_insert / (insert_ms / 1e3) / 1e9
-    traffic = profiled_traffic(w.name)
+    traffic = None if variant else profiled_traffic(w.name)
     clocks = sampler.summary()
 
     if rank != 0:
@@ -346,7 +368,9 @@ def run_ours(args):
         "ms_per_step": round(slowest_ms / args.steps, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (seeded splitmix64 hashes generated on the device)",
-        "config": {"workload": w.name, "num_blocks": w.num_blocks,
+        "config": {"workload": w.name, "num_blocks": num_blocks, "lanes": args.lanes,
+                   "keys": ("64-bit hashes" if args.keys == "hashes"
+                            else "%s keys, XXH64 in the kernels" % args.keys),
                    "filter_bytes": w.filter_bytes, "n_insert": w.n_insert,
                    "launch": "eager" if args.eager else "CUDA graph of the step",
                    "n_lookup": w.n_lookup, "member_frac": w.member_frac,
@@ -369,7 +393,10 @@ def run_ours(args):
         "gpu_launches": (2 + len(batches)) * args.steps,
         "clocks": clocks,
     }
-    if not args.no_cpu_baseline:
+    if variant:
+        line["roofline"]["note"] = ("variant: e2e, traffic and cpu_baseline are reported "
+                                    "for the hash path only")
+    if not args.no_cpu_baseline and not variant:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
     return line
 
@@ -645,7 +672,9 @@ def run_reference(args):
             "ms_per_step": round(1e3 * elapsed / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic (seeded splitmix64 hashes)",
-            "config": {"workload": w.name, "num_blocks": w.num_blocks,
+            "config": {"workload": w.name, "num_blocks": num_blocks, "lanes": args.lanes,
+                   "keys": ("64-bit hashes" if args.keys == "hashes"
+                            else "%s keys, XXH64 in the kernels" % args.keys),
                        "n_insert": w.n_insert, "n_lookup": w.n_lookup,
                        "member_frac": w.member_frac},
             "cpu_baseline": {"value": cb["value"], "unit": UNIT, "cores": cb["cores"],
