@@ -272,6 +272,21 @@ typedef struct sbbf_host_pipe sbbf_host_pipe_t;
 sbbf_status sbbf_host_pipe_create(size_t chunk_hashes, sbbf_host_pipe_t **out);
 sbbf_status sbbf_host_pipe_destroy(sbbf_host_pipe_t *p);
 
+/* How a pipe moves the data of a call.
+ *   SBBF_PIPE_AUTO (default): direct when every host buffer of the call is
+ *     page-locked memory mapped into the device's address space (e.g.
+ *     cudaHostAlloc / cudaHostRegister memory, torch pin_memory), else staged;
+ *   SBBF_PIPE_COPY: always staged: chunked cudaMemcpyAsync to the pipe's
+ *     device buffers, overlapped with the kernels on two streams;
+ *   SBBF_PIPE_DIRECT: the kernels read the hashes from, and write the result
+ *     bits to, the host buffers in place through the device mapping (on a
+ *     Grace-Blackwell node over NVLink-C2C); calls whose buffers are not
+ *     mapped return SBBF_EINVAL.
+ * Results are identical in every mode.  Errors: SBBF_EINVAL (NULL, unknown
+ * mode). */
+enum { SBBF_PIPE_AUTO = 0, SBBF_PIPE_COPY = 1, SBBF_PIPE_DIRECT = 2 };
+sbbf_status sbbf_host_pipe_set_mode(sbbf_host_pipe_t *p, int mode);
+
 /* Insert / look up hashes held in HOST memory (pinned memory overlaps copies
  * with kernels; pageable memory works but serialises).  The call returns when
  * every result is in h_out_bits ((n + 31) / 32 words, host memory), i.e. it

@@ -13,6 +13,9 @@ from .sbbf import (  # noqa: F401
     PARTITION_AUTO,
     PARTITION_OFF,
     PARTITION_ON,
+    PIPE_AUTO,
+    PIPE_COPY,
+    PIPE_DIRECT,
     Filter,
     HostPipe,
     MultiFilter,

@@ -1,21 +1,28 @@
-// Block-range partitioned inserts for filters larger than L2.
+// Block-range partitioned inserts and lookups for filters larger than L2.
 //
 // A random 32-byte block of a filter far larger than L2 costs a DRAM access
 // of at least 64 bytes, and DRAM serves only ~40 G random accesses per
 // second, whereas the same block in L2 costs one L1/L2 request.  So for a
 // large batch the keys are first grouped by filter slice -- 2^20 consecutive
-// blocks (32 MiB) -- and then inserted slice by slice, in order:
-//   1. count the keys of every slice (per-CTA shared-memory histogram,
-//      warp-aggregated with __match_any_sync, then one global add per slice);
-//   2. exclusive scan of the counts (one CTA);
-//   3. scatter the keys into slice order (per 16384-key tile: count, reserve
-//      each slice's run with one global add, place with shared-memory ranks);
-//   4. insert the slice-ordered keys with the in-order dynamic tile schedule;
-//      the CTA that starts a slice prefetches the next slice into L2 with
-//      bulk prefetches, so its blocks are read from DRAM sequentially and hit
-//      in L2 when their keys arrive.
+// blocks (32 MiB) -- and then processed slice by slice, in order:
+//   1. count: the keys are split into one contiguous range per CTA; each CTA
+//      histograms its range by slice in shared memory and stores its row;
+//   2. scan (one CTA): slice totals, slice start offsets, and for every
+//      (CTA, slice) the output position where that CTA's keys of the slice
+//      begin -- so the scatter needs no global atomics and its output order
+//      is the same on every run;
+//   3. scatter: each CTA streams its range in tiles through shared memory
+//      (double-buffered bulk copies, cp.async.bulk with an mbarrier, the next
+//      tile arriving while the current one is processed), counting-sorts the
+//      tile by slice there and writes each slice's run at its own cursor, so
+//      consecutive threads write consecutive addresses;
+//   4. insert or look up the slice-ordered keys with the in-order dynamic
+//      tile schedule; the tiles of slice q bulk-prefetch slice q + 1 into L2,
+//      so the filter is read from DRAM sequentially and hit in L2 when the
+//      keys arrive.
 // Inserts commute (OR), so the order within a slice does not matter and the
-// filter equals the unpartitioned insert bit for bit.
+// filter equals the unpartitioned insert bit for bit; lookups carry each
+// key's original position and set that bit of the result.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -33,7 +40,7 @@ namespace {
 constexpr int kSliceShift = 20;          // 2^20 blocks (32 MiB) per slice
 constexpr uint32_t kMaxSlices = 4096;    // num_blocks < 2^32
 constexpr uint32_t kFewSlices = 32;      // ballot counting up to this many slices
-constexpr int kPartThreads = 512;
+constexpr int kPartThreads = 1024;
 
 __device__ __forceinline__ uint32_t slice_of(uint64_t h, uint32_t nb) {
   return block_of(h, nb) >> kSliceShift;
@@ -45,10 +52,10 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
-// Keys per thread per pass and keys per tile of the scatter (kept in
-// registers between the passes).
+// Keys per thread per load round of the count pass (16-byte loads of two
+// consecutive keys, so every round of a CTA reads a contiguous span).
 constexpr int kKeysPerThread = 16;
-constexpr uint32_t kTileKeys = kPartThreads * kKeysPerThread;  // 8192
+constexpr int kCountThreads = 1024;
 
 // Adds 1 to bins[p] for every valid lane's p.  With few bins (kFew) a warp
 // counts each bin with one ballot; with many, lanes rarely collide and add
@@ -86,55 +93,57 @@ __device__ __forceinline__ unsigned rank_warp(unsigned* ranks, uint32_t n_slices
   return v ? atomicAdd(&ranks[p], 1u) : 0u;
 }
 
-// Loads the kKeysPerThread keys of this thread in tile [t0, t1): key i of
-// thread x is t0 + 2 * (i / 2) * blockDim + 2 * x + (i % 2), so each load
-// instruction reads 16 consecutive bytes per lane.
-__device__ __forceinline__ void load_tile_keys(const uint64_t* __restrict__ hashes, uint64_t t0,
-                                               uint64_t t1, bool vec, uint64_t pol,
-                                               uint64_t h[kKeysPerThread], bool ok[kKeysPerThread]) {
-#pragma unroll
-  for (int i = 0; i < kKeysPerThread; i += 2) {
-    const uint64_t k = t0 + static_cast<uint64_t>(i / 2) * 2 * blockDim.x + 2 * threadIdx.x;
-    ok[i] = k < t1;
-    ok[i + 1] = k + 1 < t1;
-    if (vec && ok[i + 1]) {
-      load_keys2(hashes + k, pol, h[i], h[i + 1]);
-    } else {
-      h[i] = ok[i] ? load_key1(hashes + k, pol) : 0;
-      h[i + 1] = ok[i + 1] ? load_key1(hashes + k + 1, pol) : 0;
-    }
-  }
+// Keys [c * R, min(n, (c + 1) * R)) belong to CTA c of the count and scatter
+// passes (R even, so a range starts 16-byte aligned whenever the array does).
+__host__ __device__ __forceinline__ uint64_t range_keys(uint64_t n, uint32_t ctas) {
+  const uint64_t r = (n + ctas - 1) / ctas;
+  return (r + 1) & ~1ull;
 }
 
-// counts[p] += number of keys in slice p.
+// hist[c * n_slices + p] = keys of CTA c's range that fall in slice p.
 template <bool kFew>
-__global__ void __launch_bounds__(kPartThreads)
+__global__ void __launch_bounds__(kCountThreads)
     count_kernel(const uint64_t* __restrict__ hashes, uint64_t n, uint32_t nb, uint32_t n_slices,
-                 unsigned long long* __restrict__ counts) {
+                 uint64_t range, unsigned* __restrict__ hist) {
   extern __shared__ unsigned s_cnt[];
   for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x) s_cnt[i] = 0;
   __syncthreads();
   const uint64_t pol = policy_evict_first();
   const bool vec = (reinterpret_cast<uintptr_t>(hashes) & 15) == 0;
-  const uint64_t n_tiles = (n + kTileKeys - 1) / kTileKeys;
-  for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const uint64_t t0 = tile * kTileKeys, t1 = t0 + kTileKeys < n ? t0 + kTileKeys : n;
+  const uint64_t a = static_cast<uint64_t>(blockIdx.x) * range;
+  const uint64_t b = a + range < n ? a + range : n;
+  const uint64_t per_round = static_cast<uint64_t>(kKeysPerThread) * blockDim.x;
+  for (uint64_t t0 = a; t0 < b; t0 += per_round) {
     uint64_t h[kKeysPerThread];
     bool ok[kKeysPerThread];
-    load_tile_keys(hashes, t0, t1, vec, pol, h, ok);
+#pragma unroll
+    for (int i = 0; i < kKeysPerThread; i += 2) {
+      const uint64_t k = t0 + static_cast<uint64_t>(i / 2) * 2 * blockDim.x + 2 * threadIdx.x;
+      ok[i] = k < b;
+      ok[i + 1] = k + 1 < b;
+      if (vec && ok[i + 1]) {
+        load_keys2(hashes + k, pol, h[i], h[i + 1]);
+      } else {
+        h[i] = ok[i] ? load_key1(hashes + k, pol) : 0;
+        h[i + 1] = ok[i + 1] ? load_key1(hashes + k + 1, pol) : 0;
+      }
+    }
 #pragma unroll
     for (int i = 0; i < kKeysPerThread; ++i)
       count_warp<kFew>(s_cnt, n_slices, ok[i], ok[i] ? slice_of(h[i], nb) : 0u);
   }
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x)
-    if (s_cnt[i]) atomicAdd(&counts[i], static_cast<unsigned long long>(s_cnt[i]));
+    hist[static_cast<uint64_t>(blockIdx.x) * n_slices + i] = s_cnt[i];
 }
 
-// offsets[0..n_slices] = exclusive scan of counts; cursors = offsets.
+// From the per-CTA histograms of `ctas` CTAs: offsets[0..n_slices] (slice
+// starts in the sorted array, exclusive scan of the slice totals) and
+// base[c * n_slices + p] = offsets[p] + keys of slice p in the ranges of CTAs
+// before c.  One CTA.
 __global__ void __launch_bounds__(1024)
-    scan_kernel(const unsigned long long* __restrict__ counts, uint32_t n_slices,
-                unsigned long long* __restrict__ offsets, unsigned long long* __restrict__ cursors) {
+    scan_kernel(const unsigned* __restrict__ hist, uint32_t ctas, uint32_t n_slices,
+                unsigned long long* __restrict__ offsets, unsigned long long* __restrict__ base) {
   __shared__ unsigned long long warp_total[32];
   __shared__ unsigned long long carry;
   const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -142,7 +151,9 @@ __global__ void __launch_bounds__(1024)
   __syncthreads();
   for (uint32_t start = 0; start < n_slices; start += blockDim.x) {
     const uint32_t t = start + threadIdx.x;
-    const unsigned long long v = t < n_slices ? counts[t] : 0ull;
+    unsigned long long v = 0;
+    if (t < n_slices)
+      for (uint32_t c = 0; c < ctas; ++c) v += hist[static_cast<uint64_t>(c) * n_slices + t];
     unsigned long long x = v;
     for (int o = 1; o < 32; o <<= 1) {
       const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
@@ -162,7 +173,11 @@ __global__ void __launch_bounds__(1024)
     const unsigned long long before = carry + (warp > 0 ? warp_total[warp - 1] : 0ull) + x - v;
     if (t < n_slices) {
       offsets[t] = before;
-      cursors[t] = before;
+      unsigned long long run = before;
+      for (uint32_t c = 0; c < ctas; ++c) {
+        base[static_cast<uint64_t>(c) * n_slices + t] = run;
+        run += hist[static_cast<uint64_t>(c) * n_slices + t];
+      }
     }
     __syncthreads();
     if (threadIdx.x == blockDim.x - 1) carry += warp_total[31];
@@ -173,7 +188,8 @@ __global__ void __launch_bounds__(1024)
 
 // Exclusive scan of vals[0..n) in place over the CTA (n <= 8 * blockDim);
 // each thread scans up to 8 consecutive entries, then the per-thread sums
-// are scanned with warp shuffles.
+// are scanned with warp shuffles.  Callers synchronise before the call; it
+// ends with a barrier.
 __device__ __forceinline__ void cta_exclusive_scan(unsigned* vals, uint32_t n, unsigned* warp_sums) {
   const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
   const uint32_t a = threadIdx.x * per, b = a + per < n ? a + per : n;
@@ -206,68 +222,164 @@ __device__ __forceinline__ void cta_exclusive_scan(unsigned* vals, uint32_t n, u
   __syncthreads();
 }
 
-// Keys into slice order, one tile of kTileKeys at a time: the tile is
-// counted per slice, counting-sorted into shared memory, each slice's run is
-// reserved in the output with one global add, and the sorted tile is written
-// out in order, so consecutive threads write consecutive output positions.
-template <bool kFew, bool kIndex>
-__global__ void __launch_bounds__(kPartThreads)
+// ---- bulk copies into shared memory ------------------------------------------
+
+constexpr uint64_t kWaitNs = 2000ull * 1000 * 1000;  // a tile copy is microseconds
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Polls the mbarrier phase with the given parity; false after kWaitNs.
+__device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; "
+        "selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+}
+
+// One thread: copy `bytes` (a multiple of 16, 16-byte aligned ends) from
+// global src to shared dst, completing on mbarrier bar (armed here; a
+// zero-byte copy just arrives).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (bytes == 0) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+    return;
+  }
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// Shared memory of the scatter: two input tiles, the sorted tile, the
+// per-slice cursors (u64), counts and run starts (u32), and the tile
+// positions of the sorted keys (u16, lookups only).
+__host__ __device__ constexpr size_t scatter_smem_bytes(uint32_t tile, uint32_t n_slices,
+                                                        bool with_index) {
+  return 3ull * 8 * tile + 16ull * n_slices + (with_index ? 2ull * tile : 0);
+}
+
+// Keys into slice order.  CTA c streams its range in tiles of kT keys: the
+// tile is counted per slice, counting-sorted into shared memory, and each
+// slice's run is written at the CTA's cursor for that slice (from the scan),
+// which then advances.  Tile t+1 is bulk-copied into the other buffer while
+// tile t is processed.  The copies need a 16-byte aligned key array; with
+// any other alignment, or if a copy ever failed to complete in time, the
+// CTA reads the keys straight from global memory instead.
+template <bool kFew, bool kIndex, uint32_t kT>
+__global__ void __launch_bounds__(kPartThreads, 1)
     scatter_kernel(const uint64_t* __restrict__ hashes, uint64_t n, uint32_t nb, uint32_t n_slices,
-                   unsigned long long* __restrict__ cursors, uint64_t* __restrict__ out,
-                   uint32_t* __restrict__ out_idx) {
-  extern __shared__ unsigned long long smem[];
-  uint64_t* s_keys = reinterpret_cast<uint64_t*>(smem);                      // kTileKeys
-  unsigned long long* s_gbase = smem + kTileKeys;                             // n_slices
-  unsigned* s_cnt = reinterpret_cast<unsigned*>(s_gbase + n_slices);          // n_slices
-  unsigned* s_off = s_cnt + n_slices;                                         // n_slices
-  unsigned* s_idx = s_off + n_slices;  // kTileKeys original positions (kIndex)
+                   uint64_t range, const unsigned long long* __restrict__ base,
+                   uint64_t* __restrict__ out, uint32_t* __restrict__ out_idx) {
+  extern __shared__ __align__(16) unsigned long long smem[];
+  uint64_t* s_buf0 = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* s_buf1 = s_buf0 + kT;
+  uint64_t* s_sorted = s_buf1 + kT;
+  unsigned long long* s_cursor = reinterpret_cast<unsigned long long*>(s_sorted + kT);
+  unsigned* s_cnt = reinterpret_cast<unsigned*>(s_cursor + n_slices);
+  unsigned* s_off = s_cnt + n_slices;
+  uint16_t* s_pos = reinterpret_cast<uint16_t*>(s_off + n_slices);  // kIndex
   __shared__ unsigned warp_sums[32];
+  __shared__ __align__(8) unsigned long long s_bar[2];
+
+  const uint64_t a = static_cast<uint64_t>(blockIdx.x) * range;
+  if (a >= n) return;  // the whole CTA: nothing of the key array is ours
+  const uint64_t b = a + range < n ? a + range : n;
+  const uint64_t n_tiles = (b - a + kT - 1) / kT;
+  for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x)
+    s_cursor[i] = base[static_cast<uint64_t>(blockIdx.x) * n_slices + i];
+  bool bulk = (reinterpret_cast<uintptr_t>(hashes) & 15) == 0;  // uniform over the CTA
+  const uint32_t bar0 = smem_u32(&s_bar[0]), bar1 = smem_u32(&s_bar[1]);
+  if (threadIdx.x == 0 && bulk) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // thread 0 starts the copy of tile t (its even-length head; an odd last
+  // key is loaded after the wait)
+  auto issue = [&](uint64_t t) {
+    const uint64_t t0 = a + t * kT;
+    const uint64_t m = b - t0 < kT ? b - t0 : kT;
+    bulk_load((t & 1) ? s_buf1 : s_buf0, hashes + t0, static_cast<uint32_t>((m & ~1ull) * 8),
+              (t & 1) ? bar1 : bar0);
+  };
+  if (threadIdx.x == 0 && bulk) issue(0);
+  uint32_t parity = 0;  // bit i: phase parity expected next on buffer i
   const uint64_t pol = policy_evict_first();
-  const bool vec = (reinterpret_cast<uintptr_t>(hashes) & 15) == 0;
-  const uint64_t n_tiles = (n + kTileKeys - 1) / kTileKeys;
-  for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const uint64_t t0 = tile * kTileKeys, t1 = t0 + kTileKeys < n ? t0 + kTileKeys : n;
-    const uint32_t m = static_cast<uint32_t>(t1 - t0);
+
+  for (uint64_t t = 0; t < n_tiles; ++t) {
+    const uint64_t t0 = a + t * kT;
+    const uint32_t m = static_cast<uint32_t>(b - t0 < kT ? b - t0 : kT);
+    const int cur = static_cast<int>(t & 1);
+    uint64_t* s_in = cur ? s_buf1 : s_buf0;
+    if (bulk) {
+      // the other buffer's last reader finished at the previous tile's end
+      if (threadIdx.x == 0 && t + 1 < n_tiles) issue(t + 1);
+      const bool ok = wait_phase(cur ? bar1 : bar0, (parity >> cur) & 1);
+      parity ^= 1u << cur;
+      bulk = __syncthreads_and(ok);  // all threads agree; on failure never use the buffers again
+      if (bulk && (m & 1) && threadIdx.x == 0) s_in[m - 1] = load_key1(hashes + t0 + m - 1, pol);
+    }
+    const bool from_smem = bulk;
+    auto key_at = [&](uint32_t j) -> uint64_t {
+      return from_smem ? s_in[j] : load_key1(hashes + t0 + j, pol);
+    };
     for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x) s_cnt[i] = 0;
     __syncthreads();
-    uint64_t h[kKeysPerThread];
-    bool ok[kKeysPerThread];
-    uint32_t p[kKeysPerThread];
-    load_tile_keys(hashes, t0, t1, vec, pol, h, ok);
-#pragma unroll
-    for (int i = 0; i < kKeysPerThread; ++i) {
-      p[i] = ok[i] ? slice_of(h[i], nb) : 0u;
-      count_warp<kFew>(s_cnt, n_slices, ok[i], p[i]);
+    for (uint32_t j0 = 0; j0 < m; j0 += blockDim.x) {
+      const uint32_t j = j0 + threadIdx.x;
+      const bool v = j < m;
+      count_warp<kFew>(s_cnt, n_slices, v, v ? slice_of(key_at(j), nb) : 0u);
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x) {
-      const unsigned c = s_cnt[i];
-      s_off[i] = c;
-      if (c) s_gbase[i] = atomicAdd(&cursors[i], static_cast<unsigned long long>(c));
-    }
+    for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x) s_off[i] = s_cnt[i];
     __syncthreads();
-    cta_exclusive_scan(s_off, n_slices, warp_sums);  // local run starts (ends with a barrier)
+    cta_exclusive_scan(s_off, n_slices, warp_sums);  // local run starts
     for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x) s_cnt[i] = 0;
     __syncthreads();
-#pragma unroll
-    for (int i = 0; i < kKeysPerThread; ++i) {
-      const unsigned r = rank_warp<kFew>(s_cnt, n_slices, ok[i], p[i]);
-      if (ok[i]) {
-        s_keys[s_off[p[i]] + r] = h[i];
-        if (kIndex)  // tile position of key i of this thread (see load_tile_keys)
-          s_idx[s_off[p[i]] + r] = (i / 2) * 2 * blockDim.x + 2 * threadIdx.x + (i % 2);
+    for (uint32_t j0 = 0; j0 < m; j0 += blockDim.x) {
+      const uint32_t j = j0 + threadIdx.x;
+      const bool v = j < m;
+      const uint64_t key = v ? key_at(j) : 0;
+      const uint32_t q = v ? slice_of(key, nb) : 0u;
+      const unsigned r = rank_warp<kFew>(s_cnt, n_slices, v, q);
+      if (v) {
+        s_sorted[s_off[q] + r] = key;
+        if (kIndex) s_pos[s_off[q] + r] = static_cast<uint16_t>(j);
       }
     }
     __syncthreads();
     for (uint32_t j = threadIdx.x; j < m; j += blockDim.x) {
-      const uint64_t key = s_keys[j];
+      const uint64_t key = s_sorted[j];
       const uint32_t q = slice_of(key, nb);
-      const unsigned long long pos = s_gbase[q] + (j - s_off[q]);
+      const unsigned long long pos = s_cursor[q] + (j - s_off[q]);
       if (pos < n) {  // in range unless the input changed between the passes
         out[pos] = key;
-        if (kIndex) out_idx[pos] = static_cast<uint32_t>(t0 + s_idx[j]);
+        if (kIndex) out_idx[pos] = static_cast<uint32_t>(t0 + s_pos[j]);
       }
     }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x) s_cursor[i] += s_cnt[i];
     __syncthreads();
   }
 }
@@ -286,46 +398,96 @@ __device__ __forceinline__ void prefetch_bytes(const uint32_t* words, uint64_t l
   }
 }
 
-// Byte range [lo, hi) of slice s, or an empty range past the filter.
-__device__ __forceinline__ void slice_bytes(uint32_t nb, uint32_t s, uint64_t& lo, uint64_t& hi) {
-  const uint64_t first = static_cast<uint64_t>(s) << kSliceShift;
-  const uint64_t end = first + (1ull << kSliceShift) < nb ? first + (1ull << kSliceShift) : nb;
-  lo = first < nb ? first * 32 : 0;
-  hi = first < nb ? end * 32 : 0;
+// Streaming prefetch by key position.  Slice q holds sorted positions
+// [offsets[q], offsets[q+1]) and filter blocks [q << kSliceShift, ...); the
+// position p of slice q is mapped to byte
+//   slice_lo + floor((p - first) * slice_bytes / keys / 32) * 32
+// so consecutive position ranges map to consecutive, disjoint byte ranges and
+// every byte of every slice that holds keys is covered exactly once.  A warp
+// prefetches the bytes of positions [p0, p1) (any number of slices).
+__device__ __forceinline__ uint64_t position_byte(uint32_t nb, uint32_t q, uint64_t first,
+                                                  uint64_t keys, uint64_t p) {
+  const uint64_t b0 = static_cast<uint64_t>(q) << kSliceShift;
+  const uint64_t b1 = b0 + (1ull << kSliceShift) < nb ? b0 + (1ull << kSliceShift) : nb;
+  const uint64_t blocks = b1 - b0;
+  // (p - first) * blocks / keys without overflow: both factors < 2^32 here
+  // unless keys is large, so split the quotient
+  const uint64_t d = p - first;
+  const uint64_t blk = (d / keys) * blocks + ((d % keys) * blocks) / keys;
+  return 32 * (b0 + blk);
 }
 
-// Part `part` of `parts` equal parts (32-byte aligned) of [lo, hi).
-__device__ __forceinline__ void share(uint64_t lo, uint64_t hi, uint64_t part, uint64_t parts,
-                                      uint64_t& a, uint64_t& b) {
-  const uint64_t blocks = (hi - lo) / 32;
-  const uint64_t per = (blocks + parts - 1) / parts;
-  a = lo + 32 * (part * per < blocks ? part * per : blocks);
-  b = lo + 32 * ((part + 1) * per < blocks ? (part + 1) * per : blocks);
+__device__ __forceinline__ void prefetch_positions(const uint32_t* words, uint32_t nb,
+                                                   const unsigned long long* __restrict__ offsets,
+                                                   uint32_t n_slices, uint64_t p0, uint64_t p1) {
+  const uint64_t n = offsets[n_slices];
+  if (p0 >= n) return;
+  if (p1 > n) p1 = n;
+  uint32_t lo = 0, hi = n_slices;  // last q with offsets[q] <= p0
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (offsets[mid] <= p0) lo = mid; else hi = mid;
+  }
+  for (uint32_t q = lo; q < n_slices && offsets[q] < p1; ++q) {
+    const uint64_t first = offsets[q], last = offsets[q + 1];
+    if (last == first) continue;
+    const uint64_t a = p0 > first ? p0 : first, b = p1 < last ? p1 : last;
+    if (a >= b) continue;
+    prefetch_bytes(words, position_byte(nb, q, first, last - first, a),
+                   position_byte(nb, q, first, last - first, b));
+  }
 }
 
-// Slice-ordered insert with the in-order dynamic tile schedule (tiles of
-// kTileRounds x warps-per-CTA 64-key groups).  The L2 prefetch of the next
-// slice is spread over the current slice's tiles: tile i of the T tiles
-// covering slice q prefetches part i of T of slice q + 1, so every SM's bulk
-// prefetch unit takes a share and the next slice is in L2 when its keys
-// start.  At launch every CTA prefetches its share of slice 0.
+// Distance, in sorted positions, that the streaming prefetch runs ahead of
+// the newest claimed tile: one whole slice of keys (the largest), so a
+// slice's blocks are all in L2 before its first key is processed, plus half
+// the window of keys in flight, for the prefetches to land.  The L2
+// footprint is then about one slice plus 1.5 windows of filter bytes.  One
+// warp computes it (all lanes return the same value).
+__device__ __forceinline__ uint64_t prefetch_ahead(const unsigned long long* __restrict__ offsets,
+                                                   uint32_t n_slices, uint64_t window) {
+  unsigned long long k_max = 0;
+  for (uint32_t q = lane_id(); q < n_slices; q += 32) {
+    const unsigned long long k = offsets[q + 1] - offsets[q];
+    k_max = k > k_max ? k : k_max;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xFFFFFFFFu, k_max, o);
+    k_max = v > k_max ? v : k_max;
+  }
+  return k_max + window / 2;
+}
+
+// Rounds of 64-key groups per warp per tile (a launch argument, 1..8; even
+// for lookups).  The host picks it from the filter bytes per key: the window
+// of keys in flight (CTAs x tile) times that is held near 24 MiB, so window
+// and prefetch fit in L2 with a slice; dense batches get long tiles (fewer
+// claims of the shared tile counter), sparse ones short tiles.
+constexpr int kMaxSlicedRounds = 8;
+
+// Slice-ordered insert with the in-order dynamic tile schedule.  Every tile
+// at position a0 prefetches the filter bytes of positions [a0 + ahead,
+// a0 + ahead + tile) (see prefetch_ahead), so each block is read from DRAM
+// once, sequentially, before its keys arrive.  At launch the CTAs split the
+// prefetch of positions [0, ahead).
 __global__ void __launch_bounds__(256)
     sliced_insert_kernel(uint32_t* __restrict__ words, uint32_t nb,
                          const uint64_t* __restrict__ keys, uint64_t n,
                          const unsigned long long* __restrict__ offsets, uint32_t n_slices,
-                         unsigned long long* __restrict__ tiles) {
+                         unsigned long long* __restrict__ tiles, int rounds) {
   __shared__ unsigned long long s_tile;
   const unsigned wpc = blockDim.x >> 5, wic = threadIdx.x >> 5;
   const uint64_t n_groups = (n + 63) >> 6;
-  const uint64_t groups_per_tile = static_cast<uint64_t>(wpc) * kTileRounds;
+  const uint64_t groups_per_tile = static_cast<uint64_t>(wpc) * rounds;
   const uint64_t keys_per_tile = groups_per_tile * 64;
   const uint64_t pol = policy_evict_first();
   OneFilter res{nb};
+  uint64_t ahead = 0;
   if (wic == 0) {
-    uint64_t lo, hi, a, b;
-    slice_bytes(nb, 0, lo, hi);
-    share(lo, hi, blockIdx.x, gridDim.x, a, b);
-    prefetch_bytes(words, a, b);
+    ahead = prefetch_ahead(offsets, n_slices, keys_per_tile * gridDim.x);
+    const uint64_t share = (ahead + gridDim.x - 1) / gridDim.x;
+    prefetch_positions(words, nb, offsets, n_slices, blockIdx.x * share,
+                       (blockIdx.x + 1) * share);
   }
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(tiles, 1ull);
@@ -333,24 +495,10 @@ __global__ void __launch_bounds__(256)
     const uint64_t g0 = s_tile * groups_per_tile;
     __syncthreads();
     if (g0 >= n_groups) break;
-    if (wic == 0) {
-      const uint64_t a0 = g0 * 64;
-      uint32_t lo = 0, hi = n_slices;  // last q with offsets[q] <= a0
-      while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (offsets[mid] <= a0) lo = mid; else hi = mid;
-      }
-      const uint64_t q_first = offsets[lo], q_end = offsets[lo + 1];
-      const uint64_t n_tiles_q = (q_end - q_first + keys_per_tile - 1) / keys_per_tile;
-      if (n_tiles_q > 0 && lo + 1 < n_slices) {
-        uint64_t s_lo, s_hi, a, b;
-        slice_bytes(nb, lo + 1, s_lo, s_hi);
-        const uint64_t i = (a0 - q_first) / keys_per_tile;
-        share(s_lo, s_hi, i < n_tiles_q ? i : n_tiles_q - 1, n_tiles_q, a, b);
-        prefetch_bytes(words, a, b);
-      }
-    }
-    for (int r = 0; r < kTileRounds; ++r) {
+    if (wic == 0)
+      prefetch_positions(words, nb, offsets, n_slices, g0 * 64 + ahead,
+                         g0 * 64 + ahead + keys_per_tile);
+    for (int r = 0; r < rounds; ++r) {
       const uint64_t g = g0 + static_cast<uint64_t>(r) * wpc + wic;
       if (g < n_groups) insert_group8(words, res, HashInput(keys), n, pol, g);
     }
@@ -358,27 +506,30 @@ __global__ void __launch_bounds__(256)
 }
 
 // Slice-ordered lookups of keys[0..n) (original positions idx[]), with the
-// same tile schedule and distributed prefetch as the sliced insert.  A key
-// found in the filter sets bit idx of `out` (zeroed beforehand) with one
-// atomicOr; misses write nothing.
+// same schedule and streaming prefetch as the sliced insert.  A key found in
+// the filter sets bit idx of `out` (zeroed beforehand) with one atomicOr;
+// misses write nothing.
 __global__ void __launch_bounds__(256)
     sliced_find_kernel(const uint32_t* __restrict__ words, uint32_t nb,
                        const uint64_t* __restrict__ keys, const uint32_t* __restrict__ idx,
                        uint64_t n, const unsigned long long* __restrict__ offsets,
                        uint32_t n_slices, unsigned long long* __restrict__ tiles,
-                       uint32_t* __restrict__ out) {
+                       uint32_t* __restrict__ out, int rounds) {
   __shared__ unsigned long long s_tile;
   const unsigned wpc = blockDim.x >> 5, wic = threadIdx.x >> 5, lane = lane_id();
   const uint64_t n_groups = (n + 63) >> 6;
-  const uint64_t groups_per_tile = static_cast<uint64_t>(wpc) * kTileRounds;
+  const uint64_t groups_per_tile = static_cast<uint64_t>(wpc) * rounds;
   const uint64_t keys_per_tile = groups_per_tile * 64;
   const uint64_t pk = policy_evict_first();
-  const uint64_t pf = policy_evict_last();
+  // blocks at normal priority: a slice is dropped from L2 once its keys are
+  // done, making room for the slices being prefetched
+  const uint64_t pf = policy_evict_normal();
+  uint64_t ahead = 0;
   if (wic == 0) {
-    uint64_t lo, hi, a, b;
-    slice_bytes(nb, 0, lo, hi);
-    share(lo, hi, blockIdx.x, gridDim.x, a, b);
-    prefetch_bytes(words, a, b);
+    ahead = prefetch_ahead(offsets, n_slices, keys_per_tile * gridDim.x);
+    const uint64_t share = (ahead + gridDim.x - 1) / gridDim.x;
+    prefetch_positions(words, nb, offsets, n_slices, blockIdx.x * share,
+                       (blockIdx.x + 1) * share);
   }
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(tiles, 1ull);
@@ -386,41 +537,40 @@ __global__ void __launch_bounds__(256)
     const uint64_t g0 = s_tile * groups_per_tile;
     __syncthreads();
     if (g0 >= n_groups) break;
-    if (wic == 0) {
-      const uint64_t a0 = g0 * 64;
-      uint32_t lo = 0, hi = n_slices;  // last q with offsets[q] <= a0
-      while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (offsets[mid] <= a0) lo = mid; else hi = mid;
-      }
-      const uint64_t q_first = offsets[lo], q_end = offsets[lo + 1];
-      const uint64_t n_tiles_q = (q_end - q_first + keys_per_tile - 1) / keys_per_tile;
-      if (n_tiles_q > 0 && lo + 1 < n_slices) {
-        uint64_t s_lo, s_hi, a, b;
-        slice_bytes(nb, lo + 1, s_lo, s_hi);
-        const uint64_t i = (a0 - q_first) / keys_per_tile;
-        share(s_lo, s_hi, i < n_tiles_q ? i : n_tiles_q - 1, n_tiles_q, a, b);
-        prefetch_bytes(words, a, b);
-      }
-    }
-    for (int r = 0; r < kTileRounds; ++r) {
-      const uint64_t g = g0 + static_cast<uint64_t>(r) * wpc + wic;
-      if (g >= n_groups) continue;
-      const uint64_t k = g * 64 + 2 * lane;
-      uint64_t h0, h1;
-      HashInput(keys).pair(k, n, pk, h0, h1);
-      uint32_t w0[8], w1[8];
+    if (wic == 0)
+      prefetch_positions(words, nb, offsets, n_slices, g0 * 64 + ahead,
+                         g0 * 64 + ahead + keys_per_tile);
+    // two rounds per step: four block loads per lane in flight before any test
+    for (int r = 0; r < rounds; r += 2) {
+      uint64_t k[2], h[2][2];
+      uint32_t w[2][2][8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) w0[i] = w1[i] = 0;
-      if (k < n) load_block_na(words + 8ull * block_of(h0, nb), pf, w0);
-      if (k + 1 < n) load_block_na(words + 8ull * block_of(h1, nb), pf, w1);
-      if (k < n && block_has(w0, static_cast<uint32_t>(h0))) {
-        const uint32_t j = idx[k];
-        atomicOr(out + (j >> 5), 1u << (j & 31));
+      for (int u = 0; u < 2; ++u) {
+        const uint64_t g = g0 + static_cast<uint64_t>(r + u) * wpc + wic;
+        k[u] = g * 64 + 2 * lane;  // >= n past the last group
+        HashInput(keys).pair(k[u], n, pk, h[u][0], h[u][1]);
       }
-      if (k + 1 < n && block_has(w1, static_cast<uint32_t>(h1))) {
-        const uint32_t j = idx[k + 1];
-        atomicOr(out + (j >> 5), 1u << (j & 31));
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          if (k[u] + e < n) {
+            load_block_na(words + 8ull * block_of(h[u][e], nb), pf, w[u][e]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) w[u][e][i] = 0;
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          if (k[u] + e < n && block_has(w[u][e], static_cast<uint32_t>(h[u][e]))) {
+            const uint32_t j = idx[k[u] + e];
+            atomicOr(out + (j >> 5), 1u << (j & 31));
+          }
+        }
       }
     }
   }
@@ -428,13 +578,41 @@ __global__ void __launch_bounds__(256)
 
 inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
 
+// Tile rounds for a sliced launch of `grid` CTAs of 8 warps over n keys into
+// a filter of `filter_bytes`: the largest power of two (at least `min_rounds`,
+// at most kMaxSlicedRounds) whose window of keys times filter bytes per key
+// stays within 24 MiB.
+int sliced_rounds(unsigned grid, uint64_t n, uint64_t filter_bytes, int min_rounds) {
+  const double bytes_per_key = static_cast<double>(filter_bytes) / static_cast<double>(n);
+  const double window_keys = 24.0 * 1024 * 1024 / bytes_per_key;
+  int r = min_rounds;
+  while (r < kMaxSlicedRounds && 2.0 * r * grid * 8 * 64 <= window_keys) r *= 2;
+  return r;
+}
+
+// Dynamic shared memory a CTA may use on this architecture (227 KB), less a
+// margin for the kernel's static shared memory.
+constexpr size_t kSmemBudget = 227 * 1024 - 512;
+
+// Scatter tile size: 8192 keys while three tiles, the index and the slice
+// tables fit, else 4096.
+uint32_t scatter_tile(uint32_t n_slices, bool with_index) {
+  return scatter_smem_bytes(8192, n_slices, with_index) <= kSmemBudget ? 8192u : 4096u;
+}
+
+// CTAs of the count and scatter passes (one per SM; both use the same key
+// ranges).
+uint32_t partition_ctas() { return static_cast<uint32_t>(sm_count()); }
+
 }  // namespace
 
 // Scratch bytes for a partitioned insert (or, with_index, lookup) of n keys
 // into num_blocks blocks.
 uint64_t partition_scratch_bytes(uint32_t num_blocks, uint64_t n, bool with_index) {
   const uint64_t s = (static_cast<uint64_t>(num_blocks) + (1ull << kSliceShift) - 1) >> kSliceShift;
-  return 3 * align256(8 * (s + 1)) + 256 + align256(8 * n) + (with_index ? align256(4 * n) : 0);
+  const uint64_t g = partition_ctas();
+  return align256(4 * g * s) + align256(8 * g * s) + align256(8 * (s + 1)) + 256 +
+         align256(8 * n) + (with_index ? align256(4 * n) : 0);
 }
 
 // Largest batch a partitioned lookup handles in one pass (32-bit positions).
@@ -443,19 +621,23 @@ constexpr uint64_t kMaxIndexedKeys = 1ull << 31;
 namespace {
 
 struct PartScratch {
-  unsigned long long *counts, *offsets, *cursors, *tiles;
+  unsigned* hist;                  // [ctas][n_slices]
+  unsigned long long* base;        // [ctas][n_slices]
+  unsigned long long* offsets;     // [n_slices + 1]
+  unsigned long long* tiles;       // dynamic-schedule counter
   uint64_t* sorted;
   uint32_t* idx;
 };
 
-PartScratch carve(void* scratch, uint32_t n_slices, uint64_t n) {
+PartScratch carve(void* scratch, uint32_t ctas, uint32_t n_slices, uint64_t n) {
   PartScratch r;
   char* p = static_cast<char*>(scratch);
-  r.counts = reinterpret_cast<unsigned long long*>(p);
-  p += align256(8 * (n_slices + 1));
+  const uint64_t cells = static_cast<uint64_t>(ctas) * n_slices;
+  r.hist = reinterpret_cast<unsigned*>(p);
+  p += align256(4 * cells);
+  r.base = reinterpret_cast<unsigned long long*>(p);
+  p += align256(8 * cells);
   r.offsets = reinterpret_cast<unsigned long long*>(p);
-  p += align256(8 * (n_slices + 1));
-  r.cursors = reinterpret_cast<unsigned long long*>(p);
   p += align256(8 * (n_slices + 1));
   r.tiles = reinterpret_cast<unsigned long long*>(p);
   p += 256;
@@ -465,54 +647,52 @@ PartScratch carve(void* scratch, uint32_t n_slices, uint64_t n) {
   return r;
 }
 
-// Steps 1-3: counts, offsets and the slice-ordered keys (and positions).
+template <bool kFew, bool kIndex, uint32_t kT>
+sbbf_status launch_scatter(const uint64_t* hashes, uint64_t n, uint32_t nb, uint32_t n_slices,
+                           uint64_t range, uint32_t ctas, const PartScratch& ps, cudaStream_t s) {
+  const size_t smem = scatter_smem_bytes(kT, n_slices, kIndex);
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      scatter_kernel<kFew, kIndex, kT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      static_cast<int>(kSmemBudget));
+  if (attr != cudaSuccess) return record_cuda(attr);
+  scatter_kernel<kFew, kIndex, kT><<<ctas, kPartThreads, smem, s>>>(
+      hashes, n, nb, n_slices, range, ps.base, ps.sorted, kIndex ? ps.idx : nullptr);
+  return launch_status();
+}
+
+// Steps 1-3: per-CTA counts, offsets and bases, and the slice-ordered keys
+// (and positions).
 sbbf_status partition(const uint64_t* hashes, uint64_t n, uint32_t num_blocks, uint32_t n_slices,
                       const PartScratch& ps, bool with_index, cudaStream_t s) {
-  SBBF_CUDA(cudaMemsetAsync(ps.counts, 0, 8ull * n_slices, s));
   const bool few = n_slices <= kFewSlices;
-  const uint64_t tiles_n = (n + kTileKeys - 1) / kTileKeys;
+  const uint32_t ctas = partition_ctas();
+  const uint64_t range = range_keys(n, ctas);
   const size_t count_smem = 4ull * n_slices;
-  const size_t scatter_smem = 8ull * kTileKeys + 16ull * n_slices + (with_index ? 4ull * kTileKeys : 0);
-  const size_t max_smem = 12ull * kTileKeys + 16ull * kMaxSlices;
-  static const bool smem_set = [max_smem] {
-    cudaFuncSetAttribute(scatter_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(max_smem));
-    cudaFuncSetAttribute(scatter_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(max_smem));
-    cudaFuncSetAttribute(scatter_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(max_smem));
-    cudaFuncSetAttribute(scatter_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(max_smem));
-    return true;
-  }();
-  (void)smem_set;
-  static int occ_count_few = occupancy(count_kernel<true>, kPartThreads, 4 * kFewSlices);
-  static int occ_count_many = occupancy(count_kernel<false>, kPartThreads, 4 * kMaxSlices);
-  static int occ_scatter = occupancy(scatter_kernel<false, true>, kPartThreads, max_smem);
   if (few)
-    count_kernel<true><<<grid_for(tiles_n, 1, occ_count_few), kPartThreads, count_smem, s>>>(
-        hashes, n, num_blocks, n_slices, ps.counts);
+    count_kernel<true><<<ctas, kCountThreads, count_smem, s>>>(hashes, n, num_blocks, n_slices,
+                                                              range, ps.hist);
   else
-    count_kernel<false><<<grid_for(tiles_n, 1, occ_count_many), kPartThreads, count_smem, s>>>(
-        hashes, n, num_blocks, n_slices, ps.counts);
+    count_kernel<false><<<ctas, kCountThreads, count_smem, s>>>(hashes, n, num_blocks, n_slices,
+                                                               range, ps.hist);
   sbbf_status st = launch_status();
   if (st != SBBF_OK) return st;
-  scan_kernel<<<1, 1024, 0, s>>>(ps.counts, n_slices, ps.offsets, ps.cursors);
+  scan_kernel<<<1, 1024, 0, s>>>(ps.hist, ctas, n_slices, ps.offsets, ps.base);
   if ((st = launch_status()) != SBBF_OK) return st;
-  const unsigned grid = grid_for(tiles_n, 1, occ_scatter);
-  if (few && with_index)
-    scatter_kernel<true, true><<<grid, kPartThreads, scatter_smem, s>>>(
-        hashes, n, num_blocks, n_slices, ps.cursors, ps.sorted, ps.idx);
-  else if (few)
-    scatter_kernel<true, false><<<grid, kPartThreads, scatter_smem, s>>>(
-        hashes, n, num_blocks, n_slices, ps.cursors, ps.sorted, nullptr);
-  else if (with_index)
-    scatter_kernel<false, true><<<grid, kPartThreads, scatter_smem, s>>>(
-        hashes, n, num_blocks, n_slices, ps.cursors, ps.sorted, ps.idx);
-  else
-    scatter_kernel<false, false><<<grid, kPartThreads, scatter_smem, s>>>(
-        hashes, n, num_blocks, n_slices, ps.cursors, ps.sorted, nullptr);
-  return launch_status();
+  const bool big = scatter_tile(n_slices, with_index) == 8192;
+  if (few)
+    return with_index ? launch_scatter<true, true, 8192>(hashes, n, num_blocks, n_slices, range,
+                                                         ctas, ps, s)
+                      : launch_scatter<true, false, 8192>(hashes, n, num_blocks, n_slices, range,
+                                                          ctas, ps, s);
+  if (with_index)
+    return big ? launch_scatter<false, true, 8192>(hashes, n, num_blocks, n_slices, range, ctas,
+                                                   ps, s)
+               : launch_scatter<false, true, 4096>(hashes, n, num_blocks, n_slices, range, ctas,
+                                                   ps, s);
+  return big ? launch_scatter<false, false, 8192>(hashes, n, num_blocks, n_slices, range, ctas,
+                                                  ps, s)
+             : launch_scatter<false, false, 4096>(hashes, n, num_blocks, n_slices, range, ctas,
+                                                  ps, s);
 }
 
 uint32_t slices_of(uint32_t num_blocks) {
@@ -529,13 +709,15 @@ sbbf_status launch_insert_partitioned(uint32_t* words, uint32_t num_blocks, cons
   if (n == 0) return SBBF_OK;
   const uint32_t n_slices = slices_of(num_blocks);
   if (n_slices == 0 || n_slices > kMaxSlices) return SBBF_EINVAL;
-  const PartScratch ps = carve(scratch, n_slices, n);
+  const PartScratch ps = carve(scratch, partition_ctas(), n_slices, n);
   sbbf_status st = partition(hashes, n, num_blocks, n_slices, ps, false, s);
   if (st != SBBF_OK) return st;
   SBBF_CUDA(cudaMemsetAsync(ps.tiles, 0, 8, s));
   static int occ_ins = occupancy(sliced_insert_kernel, 256);
-  sliced_insert_kernel<<<grid_for((n + 63) / 64, 8, occ_ins), 256, 0, s>>>(
-      words, num_blocks, ps.sorted, n, ps.offsets, n_slices, ps.tiles);
+  const unsigned grid = grid_for((n + 63) / 64, 8, occ_ins);
+  const int rounds = sliced_rounds(grid, n, 32ull * num_blocks, 1);
+  sliced_insert_kernel<<<grid, 256, 0, s>>>(words, num_blocks, ps.sorted, n, ps.offsets, n_slices,
+                                            ps.tiles, rounds);
   return launch_status();
 }
 
@@ -551,15 +733,17 @@ sbbf_status launch_find_partitioned(const uint32_t* words, uint32_t num_blocks,
   if (n_slices == 0 || n_slices > kMaxSlices) return SBBF_EINVAL;
   for (uint64_t off = 0; off < n; off += kMaxIndexedKeys) {
     const uint64_t m = n - off < kMaxIndexedKeys ? n - off : kMaxIndexedKeys;
-    const PartScratch ps = carve(scratch, n_slices, m);
+    const PartScratch ps = carve(scratch, partition_ctas(), n_slices, m);
     sbbf_status st = partition(hashes + off, m, num_blocks, n_slices, ps, true, s);
     if (st != SBBF_OK) return st;
     uint32_t* out = d_out + off / 32;
     SBBF_CUDA(cudaMemsetAsync(out, 0, 4 * ((m + 31) / 32), s));
     SBBF_CUDA(cudaMemsetAsync(ps.tiles, 0, 8, s));
     static int occ_find = occupancy(sliced_find_kernel, 256);
-    sliced_find_kernel<<<grid_for((m + 63) / 64, 8, occ_find), 256, 0, s>>>(
-        words, num_blocks, ps.sorted, ps.idx, m, ps.offsets, n_slices, ps.tiles, out);
+    const unsigned grid = grid_for((m + 63) / 64, 8, occ_find);
+    const int rounds = sliced_rounds(grid, m, 32ull * num_blocks, 2);
+    sliced_find_kernel<<<grid, 256, 0, s>>>(words, num_blocks, ps.sorted, ps.idx, m, ps.offsets,
+                                            n_slices, ps.tiles, out, rounds);
     st = launch_status();
     if (st != SBBF_OK) return st;
   }

@@ -60,6 +60,7 @@ SIGNATURES = {
     "sbbf_copy_to_host": (_int, [_P, _P, _sz, _P]),
     "sbbf_host_pipe_create": (_int, [_sz, _c.POINTER(_P)]),
     "sbbf_host_pipe_destroy": (_int, [_P]),
+    "sbbf_host_pipe_set_mode": (_int, [_P, _int]),
     "sbbf_insert_hashes_host": (_int, [_P, _P, _P, _sz, _P]),
     "sbbf_find_hashes_host": (_int, [_P, _P, _P, _sz, _P, _P]),
     "sbbf_hash_keys": (_int, [_P, _u32, _sz, _u64, _P, _P]),
@@ -112,6 +113,7 @@ SIGNATURES = {
 OP_INSERT, OP_FIND = 0, 1
 FORM_SEGMENTS, FORM_TAGGED = 0, 1
 PARTITION_AUTO, PARTITION_OFF, PARTITION_ON = 0, 1, 2
+PIPE_AUTO, PIPE_COPY, PIPE_DIRECT = 0, 1, 2
 
 
 class SbbfError(RuntimeError):
@@ -435,11 +437,18 @@ class Filter:
 class HostPipe:
     """Staging buffers and streams for host-memory insert/lookup calls."""
 
-    def __init__(self, chunk_hashes: int = 1 << 24):
+    def __init__(self, chunk_hashes: int = 1 << 24, mode: int = PIPE_AUTO):
         h = _P()
         check(lib().sbbf_host_pipe_create(chunk_hashes, _c.byref(h)), "sbbf_host_pipe_create")
         self._h = h
         self.chunk = chunk_hashes
+        self.set_mode(mode)
+
+    def set_mode(self, mode: int):
+        """PIPE_AUTO / PIPE_COPY / PIPE_DIRECT (see sbbf.h)."""
+        check(lib().sbbf_host_pipe_set_mode(self._h, mode), "sbbf_host_pipe_set_mode")
+        self.mode = mode
+        return self
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -72,7 +72,14 @@ C2_11BPK = SingleFilterWorkload("sbbf_128906250blk_3G_ins_1G_lookup", 22,
 C2_PROFILE = SingleFilterWorkload("sbbf_4194304blk_100M_ins_64M_lookup", 2, 4_194_304,
                                   100_000_000, 16_000_000, 64 * 2**20, 0.1)
 
-WORKLOADS = {w.name: w for w in (C0, C1, C2, C2_BIG, C2_11BPK, C2_PROFILE)}
+# A 2 GiB filter (64 slices) with 128M inserts in one batch and 128M lookups:
+# both take the partitioned path in automatic mode (2 keys per block), with
+# about 5.5 GB on the device -- a profiling-sized case of the partition,
+# scatter and slice-ordered kernels the 32 GiB and 11 bits/key filters use.
+C2_PART_PROFILE = SingleFilterWorkload("sbbf_2^26blk_128M_ins_128M_lookup", 32, 2**26,
+                                       128 * 2**20, 128 * 2**20, 128 * 2**20, 0.1)
+
+WORKLOADS = {w.name: w for w in (C0, C1, C2, C2_BIG, C2_11BPK, C2_PROFILE, C2_PART_PROFILE)}
 
 
 def gen_inserts(w: SingleFilterWorkload, start: int, n: int, out: torch.Tensor | None = None,

@@ -16,7 +16,7 @@ import oracle
 import paper_2101_01719_gb300 as sb
 from paper_2101_01719_gb300 import workloads as wl
 import sbbf_inputs as inp
-from gpu_util import bit_at, bits_np, dev
+from gpu_util import bit_at, bits_np, dev, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -91,3 +91,29 @@ def test_three_billion_inserts_sampled_parity(w):
     lam = p * (w.n_lookup - members)
     assert hits >= members
     assert abs((hits - members) - lam) <= 6 * np.sqrt(lam) + 0.02 * lam + 10
+
+
+def test_partitioned_paths_over_1184_slices():
+    """A 1300-slice (40.6 GiB) filter takes the scatter's 4096-key tiles for
+    lookups (the index no longer fits beside 8192-key tiles).  A few million
+    keys are inserted and looked up partitioned; the touched blocks are
+    rebuilt by the oracle, every member hits, and every answer equals the
+    unpartitioned lookup of the same filter."""
+    B, n = 1300 * 2**20 + 17, 4_000_001
+    keys = inp.stream(160, 0, n)
+    f = sb.Filter(B).set_partitioning(sb.PARTITION_ON)
+    f.insert(to_dev(keys))
+    blocks = np.unique(np.array([oracle.block_index(int(h), B) for h in keys[::97]], np.uint64))
+    got = f.words.view(-1, 8)[torch.from_numpy(blocks.astype(np.int64)).to(dev())]
+    exp = oracle.insert_block_ranges(np.zeros(8 * blocks.size, np.uint32), B, keys, blocks,
+                                     blocks + np.uint64(1))
+    assert np.array_equal(got.cpu().numpy().view(np.uint32).ravel(), exp)
+    q = np.concatenate([inp.stream(160, 1, n), keys[: n // 4]])
+    dq = to_dev(q)
+    part = bits_np(f.find(dq))
+    f.set_partitioning(sb.PARTITION_OFF)
+    assert np.array_equal(part, bits_np(f.find(dq)))
+    tail = np.unpackbits(part.view(np.uint8), bitorder="little")[n: n + n // 4]
+    assert tail.all()
+    del f
+    torch.cuda.empty_cache()

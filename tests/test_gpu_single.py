@@ -221,6 +221,34 @@ def test_host_pipe_parity():
     assert np.array_equal(out2.numpy(), out.numpy())
 
 
+@pytest.mark.parametrize("mode", ["copy", "direct"])
+def test_host_pipe_modes(mode):
+    """Staged copies and in-place kernel access to pinned host memory give the
+    oracle's filter and bits; direct mode refuses unmapped (pageable) memory."""
+    B = 20_011
+    n = 5 * 4096 + 33
+    keys = inp.stream(129, 0, n)
+    q = np.concatenate([inp.stream(129, 1, 2 * n), keys[:1000]])
+    hk = torch.from_numpy(keys.view(np.int64)).pin_memory()
+    hq = torch.from_numpy(q.view(np.int64)).pin_memory()
+    out = torch.zeros(sb.out_words(q.size), dtype=torch.int32).pin_memory()
+    pipe = sb.HostPipe(4096, mode=sb.PIPE_COPY if mode == "copy" else sb.PIPE_DIRECT)
+    f = sb.Filter(B)
+    pipe.insert(f, hk)
+    pipe.find(f, hq, out)
+    ref = _oracle_filter(B, keys)
+    assert np.array_equal(f.to_numpy(), ref)
+    assert np.array_equal(out.numpy().view(np.uint32), oracle.find(ref, B, q))
+    if mode == "direct":
+        with pytest.raises(sb.SbbfError):
+            pipe.find(f, torch.from_numpy(q.view(np.int64)), out)  # pageable input
+        # an odd-length tail and a 16-lane filter through the same mapping
+        g = sb.Filter(777, lanes=16)
+        pipe.insert(g, hk[:101])
+        assert np.array_equal(g.to_numpy(), oracle.insert_k(np.zeros(777 * 16, np.uint32), 777,
+                                                            16, keys[:101]))
+
+
 def test_config_c0_full():
     """100k hashes in 4096 blocks; look up the 100k (all hit) then 1M fresh;
     bit-exact, and the measured FPR within the binomial interval."""
@@ -331,6 +359,28 @@ def test_partitioned_insert_unaligned_and_repeated():
     assert np.array_equal(f.to_numpy(), ref)
     with pytest.raises(sb.SbbfError):
         f.set_partitioning(7)
+
+
+def test_partitioned_many_slices():
+    """41 slices (more than the ballot-counted few): inserts and lookups,
+    with an odd batch length and an 8-byte-aligned (not 16) hash array, which
+    the scatter reads without bulk copies."""
+    B, n = 41 * 2**20 + 123, 2_000_001
+    keys = inp.stream(132, 0, n + 1)
+    dk = to_dev(keys)
+    ref = _oracle_filter(B, keys[:n])
+    for view in (dk[:n], dk[1:]):
+        f = sb.Filter(B).set_partitioning(sb.PARTITION_ON)
+        f.insert(view)
+        exp = ref if view.data_ptr() == dk.data_ptr() else _oracle_filter(B, keys[1:])
+        assert np.array_equal(f.to_numpy(), exp)
+    f = sb.Filter(B)
+    f.words.copy_(torch.from_numpy(ref.view(np.int32)).to(dev()))
+    q = np.concatenate([inp.stream(132, 1, n), keys[: n // 2]])
+    dq = to_dev(q)
+    f.set_partitioning(sb.PARTITION_ON)
+    for view, qq in ((dq, q), (dq[1:], q[1:])):
+        assert np.array_equal(bits_np(f.find(view)), oracle.find(ref, B, qq))
 
 
 @pytest.mark.parametrize("B,n", [(2**20, 1), (2**20 + 5, 16_385), (3 * 2**20 - 1, 1_000_003),
