@@ -3,8 +3,9 @@
 // A random 32-byte block of a filter far larger than L2 costs a DRAM access
 // of at least 64 bytes, and DRAM serves only ~40 G random accesses per
 // second, whereas the same block in L2 costs one L1/L2 request.  So for a
-// large batch the keys are first grouped by filter slice -- 2^20 consecutive
-// blocks (32 MiB) -- and then processed slice by slice, in order:
+// large batch the keys are first grouped by filter slice -- 2^shift
+// consecutive blocks, 4 to 32 MiB (see slice_shift) -- and then processed
+// slice by slice, in order:
 //   1. count: the keys are split into one contiguous range per CTA; each CTA
 //      histograms its range by slice in shared memory and stores its row;
 //   2. scan (one CTA): slice totals, slice start offsets, and for every
@@ -37,13 +38,15 @@ sbbf_status launch_clear(uint32_t* dst, uint64_t n_words, cudaStream_t s);
 
 namespace {
 
-constexpr int kSliceShift = 20;          // 2^20 blocks (32 MiB) per slice
-constexpr uint32_t kMaxSlices = 4096;    // num_blocks < 2^32
+constexpr int kMinSliceShift = 17;       // 2^17 blocks (4 MiB) per slice
+constexpr int kMaxSliceShift = 20;       // 2^20 blocks (32 MiB) per slice
+constexpr uint32_t kTargetSlices = 512;
+constexpr uint32_t kMaxSlices = 4096;    // num_blocks < 2^32 at the largest slice
 constexpr uint32_t kFewSlices = 32;      // ballot counting up to this many slices
 constexpr int kPartThreads = 1024;
 
-__device__ __forceinline__ uint32_t slice_of(uint64_t h, uint32_t nb) {
-  return block_of(h, nb) >> kSliceShift;
+__device__ __forceinline__ uint32_t slice_of(uint64_t h, uint32_t nb, int shift) {
+  return block_of(h, nb) >> shift;
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -103,8 +106,8 @@ __host__ __device__ __forceinline__ uint64_t range_keys(uint64_t n, uint32_t cta
 // hist[c * n_slices + p] = keys of CTA c's range that fall in slice p.
 template <bool kFew>
 __global__ void __launch_bounds__(kCountThreads)
-    count_kernel(const uint64_t* __restrict__ hashes, uint64_t n, uint32_t nb, uint32_t n_slices,
-                 uint64_t range, unsigned* __restrict__ hist) {
+    count_kernel(const uint64_t* __restrict__ hashes, uint64_t n, uint32_t nb, int shift,
+                 uint32_t n_slices, uint64_t range, unsigned* __restrict__ hist) {
   extern __shared__ unsigned s_cnt[];
   for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x) s_cnt[i] = 0;
   __syncthreads();
@@ -130,7 +133,7 @@ __global__ void __launch_bounds__(kCountThreads)
     }
 #pragma unroll
     for (int i = 0; i < kKeysPerThread; ++i)
-      count_warp<kFew>(s_cnt, n_slices, ok[i], ok[i] ? slice_of(h[i], nb) : 0u);
+      count_warp<kFew>(s_cnt, n_slices, ok[i], ok[i] ? slice_of(h[i], nb, shift) : 0u);
   }
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x)
@@ -287,8 +290,8 @@ __host__ __device__ constexpr size_t scatter_smem_bytes(uint32_t tile, uint32_t 
 // CTA reads the keys straight from global memory instead.
 template <bool kFew, bool kIndex, uint32_t kT>
 __global__ void __launch_bounds__(kPartThreads, 1)
-    scatter_kernel(const uint64_t* __restrict__ hashes, uint64_t n, uint32_t nb, uint32_t n_slices,
-                   uint64_t range, const unsigned long long* __restrict__ base,
+    scatter_kernel(const uint64_t* __restrict__ hashes, uint64_t n, uint32_t nb, int shift,
+                   uint32_t n_slices, uint64_t range, const unsigned long long* __restrict__ base,
                    uint64_t* __restrict__ out, uint32_t* __restrict__ out_idx) {
   extern __shared__ __align__(16) unsigned long long smem[];
   uint64_t* s_buf0 = reinterpret_cast<uint64_t*>(smem);
@@ -349,7 +352,7 @@ __global__ void __launch_bounds__(kPartThreads, 1)
     for (uint32_t j0 = 0; j0 < m; j0 += blockDim.x) {
       const uint32_t j = j0 + threadIdx.x;
       const bool v = j < m;
-      count_warp<kFew>(s_cnt, n_slices, v, v ? slice_of(key_at(j), nb) : 0u);
+      count_warp<kFew>(s_cnt, n_slices, v, v ? slice_of(key_at(j), nb, shift) : 0u);
     }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x) s_off[i] = s_cnt[i];
@@ -361,7 +364,7 @@ __global__ void __launch_bounds__(kPartThreads, 1)
       const uint32_t j = j0 + threadIdx.x;
       const bool v = j < m;
       const uint64_t key = v ? key_at(j) : 0;
-      const uint32_t q = v ? slice_of(key, nb) : 0u;
+      const uint32_t q = v ? slice_of(key, nb, shift) : 0u;
       const unsigned r = rank_warp<kFew>(s_cnt, n_slices, v, q);
       if (v) {
         s_sorted[s_off[q] + r] = key;
@@ -371,7 +374,7 @@ __global__ void __launch_bounds__(kPartThreads, 1)
     __syncthreads();
     for (uint32_t j = threadIdx.x; j < m; j += blockDim.x) {
       const uint64_t key = s_sorted[j];
-      const uint32_t q = slice_of(key, nb);
+      const uint32_t q = slice_of(key, nb, shift);
       const unsigned long long pos = s_cursor[q] + (j - s_off[q]);
       if (pos < n) {  // in range unless the input changed between the passes
         out[pos] = key;
@@ -399,16 +402,16 @@ __device__ __forceinline__ void prefetch_bytes(const uint32_t* words, uint64_t l
 }
 
 // Streaming prefetch by key position.  Slice q holds sorted positions
-// [offsets[q], offsets[q+1]) and filter blocks [q << kSliceShift, ...); the
+// [offsets[q], offsets[q+1]) and filter blocks [q << shift, ...); the
 // position p of slice q is mapped to byte
 //   slice_lo + floor((p - first) * slice_bytes / keys / 32) * 32
 // so consecutive position ranges map to consecutive, disjoint byte ranges and
 // every byte of every slice that holds keys is covered exactly once.  A warp
 // prefetches the bytes of positions [p0, p1) (any number of slices).
-__device__ __forceinline__ uint64_t position_byte(uint32_t nb, uint32_t q, uint64_t first,
-                                                  uint64_t keys, uint64_t p) {
-  const uint64_t b0 = static_cast<uint64_t>(q) << kSliceShift;
-  const uint64_t b1 = b0 + (1ull << kSliceShift) < nb ? b0 + (1ull << kSliceShift) : nb;
+__device__ __forceinline__ uint64_t position_byte(uint32_t nb, int shift, uint32_t q,
+                                                  uint64_t first, uint64_t keys, uint64_t p) {
+  const uint64_t b0 = static_cast<uint64_t>(q) << shift;
+  const uint64_t b1 = b0 + (1ull << shift) < nb ? b0 + (1ull << shift) : nb;
   const uint64_t blocks = b1 - b0;
   // (p - first) * blocks / keys without overflow: both factors < 2^32 here
   // unless keys is large, so split the quotient
@@ -417,7 +420,7 @@ __device__ __forceinline__ uint64_t position_byte(uint32_t nb, uint32_t q, uint6
   return 32 * (b0 + blk);
 }
 
-__device__ __forceinline__ void prefetch_positions(const uint32_t* words, uint32_t nb,
+__device__ __forceinline__ void prefetch_positions(const uint32_t* words, uint32_t nb, int shift,
                                                    const unsigned long long* __restrict__ offsets,
                                                    uint32_t n_slices, uint64_t p0, uint64_t p1) {
   const uint64_t n = offsets[n_slices];
@@ -433,8 +436,8 @@ __device__ __forceinline__ void prefetch_positions(const uint32_t* words, uint32
     if (last == first) continue;
     const uint64_t a = p0 > first ? p0 : first, b = p1 < last ? p1 : last;
     if (a >= b) continue;
-    prefetch_bytes(words, position_byte(nb, q, first, last - first, a),
-                   position_byte(nb, q, first, last - first, b));
+    prefetch_bytes(words, position_byte(nb, shift, q, first, last - first, a),
+                   position_byte(nb, shift, q, first, last - first, b));
   }
 }
 
@@ -471,7 +474,7 @@ constexpr int kMaxSlicedRounds = 8;
 // once, sequentially, before its keys arrive.  At launch the CTAs split the
 // prefetch of positions [0, ahead).
 __global__ void __launch_bounds__(256)
-    sliced_insert_kernel(uint32_t* __restrict__ words, uint32_t nb,
+    sliced_insert_kernel(uint32_t* __restrict__ words, uint32_t nb, int shift,
                          const uint64_t* __restrict__ keys, uint64_t n,
                          const unsigned long long* __restrict__ offsets, uint32_t n_slices,
                          unsigned long long* __restrict__ tiles, int rounds) {
@@ -486,7 +489,7 @@ __global__ void __launch_bounds__(256)
   if (wic == 0) {
     ahead = prefetch_ahead(offsets, n_slices, keys_per_tile * gridDim.x);
     const uint64_t share = (ahead + gridDim.x - 1) / gridDim.x;
-    prefetch_positions(words, nb, offsets, n_slices, blockIdx.x * share,
+    prefetch_positions(words, nb, shift, offsets, n_slices, blockIdx.x * share,
                        (blockIdx.x + 1) * share);
   }
   for (;;) {
@@ -496,7 +499,7 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     if (g0 >= n_groups) break;
     if (wic == 0)
-      prefetch_positions(words, nb, offsets, n_slices, g0 * 64 + ahead,
+      prefetch_positions(words, nb, shift, offsets, n_slices, g0 * 64 + ahead,
                          g0 * 64 + ahead + keys_per_tile);
     for (int r = 0; r < rounds; ++r) {
       const uint64_t g = g0 + static_cast<uint64_t>(r) * wpc + wic;
@@ -510,7 +513,7 @@ __global__ void __launch_bounds__(256)
 // the filter sets bit idx of `out` (zeroed beforehand) with one atomicOr;
 // misses write nothing.
 __global__ void __launch_bounds__(256)
-    sliced_find_kernel(const uint32_t* __restrict__ words, uint32_t nb,
+    sliced_find_kernel(const uint32_t* __restrict__ words, uint32_t nb, int shift,
                        const uint64_t* __restrict__ keys, const uint32_t* __restrict__ idx,
                        uint64_t n, const unsigned long long* __restrict__ offsets,
                        uint32_t n_slices, unsigned long long* __restrict__ tiles,
@@ -528,7 +531,7 @@ __global__ void __launch_bounds__(256)
   if (wic == 0) {
     ahead = prefetch_ahead(offsets, n_slices, keys_per_tile * gridDim.x);
     const uint64_t share = (ahead + gridDim.x - 1) / gridDim.x;
-    prefetch_positions(words, nb, offsets, n_slices, blockIdx.x * share,
+    prefetch_positions(words, nb, shift, offsets, n_slices, blockIdx.x * share,
                        (blockIdx.x + 1) * share);
   }
   for (;;) {
@@ -538,7 +541,7 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     if (g0 >= n_groups) break;
     if (wic == 0)
-      prefetch_positions(words, nb, offsets, n_slices, g0 * 64 + ahead,
+      prefetch_positions(words, nb, shift, offsets, n_slices, g0 * 64 + ahead,
                          g0 * 64 + ahead + keys_per_tile);
     // two rounds per step: four block loads per lane in flight before any test
     for (int r = 0; r < rounds; r += 2) {
@@ -604,12 +607,34 @@ uint32_t scatter_tile(uint32_t n_slices, bool with_index) {
 // ranges).
 uint32_t partition_ctas() { return static_cast<uint32_t>(sm_count()); }
 
+// Blocks per slice, 2^shift.  A slice's blocks stay in L2 from its prefetch
+// until its last key is processed, so about two slices plus the keys in
+// flight must fit there.  For inserts slices get smaller as long as the
+// partition's fan-out stays near kTargetSlices (the scatter's runs per tile
+// shrink with more slices), between 4 and 32 MiB: measured 67.6 against 60.3
+// G inserts/s on a 2 GiB filter.  Lookups keep 32 MiB slices: their scatter
+// also writes 4-byte positions, whose shorter runs cost more than the smaller
+// slices gain (59.1 against 62.2 G lookups/s on the same filter).
+int slice_shift(uint32_t num_blocks, bool lookup) {
+  if (lookup) return kMaxSliceShift;
+  int shift = kMinSliceShift;
+  while (shift < kMaxSliceShift &&
+         ((static_cast<uint64_t>(num_blocks) + (1ull << shift) - 1) >> shift) > kTargetSlices)
+    ++shift;
+  return shift;
+}
+
+uint32_t slices_of(uint32_t num_blocks, bool lookup) {
+  const int shift = slice_shift(num_blocks, lookup);
+  return static_cast<uint32_t>((static_cast<uint64_t>(num_blocks) + (1ull << shift) - 1) >> shift);
+}
+
 }  // namespace
 
 // Scratch bytes for a partitioned insert (or, with_index, lookup) of n keys
 // into num_blocks blocks.
 uint64_t partition_scratch_bytes(uint32_t num_blocks, uint64_t n, bool with_index) {
-  const uint64_t s = (static_cast<uint64_t>(num_blocks) + (1ull << kSliceShift) - 1) >> kSliceShift;
+  const uint64_t s = slices_of(num_blocks, with_index);
   const uint64_t g = partition_ctas();
   return align256(4 * g * s) + align256(8 * g * s) + align256(8 * (s + 1)) + 256 +
          align256(8 * n) + (with_index ? align256(4 * n) : 0);
@@ -648,15 +673,16 @@ PartScratch carve(void* scratch, uint32_t ctas, uint32_t n_slices, uint64_t n) {
 }
 
 template <bool kFew, bool kIndex, uint32_t kT>
-sbbf_status launch_scatter(const uint64_t* hashes, uint64_t n, uint32_t nb, uint32_t n_slices,
-                           uint64_t range, uint32_t ctas, const PartScratch& ps, cudaStream_t s) {
+sbbf_status launch_scatter(const uint64_t* hashes, uint64_t n, uint32_t nb, int shift,
+                           uint32_t n_slices, uint64_t range, uint32_t ctas, const PartScratch& ps,
+                           cudaStream_t s) {
   const size_t smem = scatter_smem_bytes(kT, n_slices, kIndex);
   static const cudaError_t attr = cudaFuncSetAttribute(
       scatter_kernel<kFew, kIndex, kT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
       static_cast<int>(kSmemBudget));
   if (attr != cudaSuccess) return record_cuda(attr);
   scatter_kernel<kFew, kIndex, kT><<<ctas, kPartThreads, smem, s>>>(
-      hashes, n, nb, n_slices, range, ps.base, ps.sorted, kIndex ? ps.idx : nullptr);
+      hashes, n, nb, shift, n_slices, range, ps.base, ps.sorted, kIndex ? ps.idx : nullptr);
   return launch_status();
 }
 
@@ -665,40 +691,38 @@ sbbf_status launch_scatter(const uint64_t* hashes, uint64_t n, uint32_t nb, uint
 sbbf_status partition(const uint64_t* hashes, uint64_t n, uint32_t num_blocks, uint32_t n_slices,
                       const PartScratch& ps, bool with_index, cudaStream_t s) {
   const bool few = n_slices <= kFewSlices;
+  const int shift = slice_shift(num_blocks, with_index);
   const uint32_t ctas = partition_ctas();
   const uint64_t range = range_keys(n, ctas);
   const size_t count_smem = 4ull * n_slices;
   if (few)
-    count_kernel<true><<<ctas, kCountThreads, count_smem, s>>>(hashes, n, num_blocks, n_slices,
-                                                              range, ps.hist);
+    count_kernel<true><<<ctas, kCountThreads, count_smem, s>>>(hashes, n, num_blocks, shift,
+                                                              n_slices, range, ps.hist);
   else
-    count_kernel<false><<<ctas, kCountThreads, count_smem, s>>>(hashes, n, num_blocks, n_slices,
-                                                               range, ps.hist);
+    count_kernel<false><<<ctas, kCountThreads, count_smem, s>>>(hashes, n, num_blocks, shift,
+                                                               n_slices, range, ps.hist);
   sbbf_status st = launch_status();
   if (st != SBBF_OK) return st;
   scan_kernel<<<1, 1024, 0, s>>>(ps.hist, ctas, n_slices, ps.offsets, ps.base);
   if ((st = launch_status()) != SBBF_OK) return st;
   const bool big = scatter_tile(n_slices, with_index) == 8192;
   if (few)
-    return with_index ? launch_scatter<true, true, 8192>(hashes, n, num_blocks, n_slices, range,
+    return with_index ? launch_scatter<true, true, 8192>(hashes, n, num_blocks, shift, n_slices, range,
                                                          ctas, ps, s)
-                      : launch_scatter<true, false, 8192>(hashes, n, num_blocks, n_slices, range,
+                      : launch_scatter<true, false, 8192>(hashes, n, num_blocks, shift, n_slices, range,
                                                           ctas, ps, s);
   if (with_index)
-    return big ? launch_scatter<false, true, 8192>(hashes, n, num_blocks, n_slices, range, ctas,
+    return big ? launch_scatter<false, true, 8192>(hashes, n, num_blocks, shift, n_slices, range, ctas,
                                                    ps, s)
-               : launch_scatter<false, true, 4096>(hashes, n, num_blocks, n_slices, range, ctas,
+               : launch_scatter<false, true, 4096>(hashes, n, num_blocks, shift, n_slices, range, ctas,
                                                    ps, s);
-  return big ? launch_scatter<false, false, 8192>(hashes, n, num_blocks, n_slices, range, ctas,
+  return big ? launch_scatter<false, false, 8192>(hashes, n, num_blocks, shift, n_slices, range, ctas,
                                                   ps, s)
-             : launch_scatter<false, false, 4096>(hashes, n, num_blocks, n_slices, range, ctas,
+             : launch_scatter<false, false, 4096>(hashes, n, num_blocks, shift, n_slices, range, ctas,
                                                   ps, s);
 }
 
-uint32_t slices_of(uint32_t num_blocks) {
-  return static_cast<uint32_t>((static_cast<uint64_t>(num_blocks) + (1ull << kSliceShift) - 1) >>
-                               kSliceShift);
-}
+
 
 }  // namespace
 
@@ -707,7 +731,7 @@ uint32_t slices_of(uint32_t num_blocks) {
 sbbf_status launch_insert_partitioned(uint32_t* words, uint32_t num_blocks, const uint64_t* hashes,
                                       uint64_t n, void* scratch, cudaStream_t s) {
   if (n == 0) return SBBF_OK;
-  const uint32_t n_slices = slices_of(num_blocks);
+  const uint32_t n_slices = slices_of(num_blocks, false);
   if (n_slices == 0 || n_slices > kMaxSlices) return SBBF_EINVAL;
   const PartScratch ps = carve(scratch, partition_ctas(), n_slices, n);
   sbbf_status st = partition(hashes, n, num_blocks, n_slices, ps, false, s);
@@ -716,8 +740,8 @@ sbbf_status launch_insert_partitioned(uint32_t* words, uint32_t num_blocks, cons
   static int occ_ins = occupancy(sliced_insert_kernel, 256);
   const unsigned grid = grid_for((n + 63) / 64, 8, occ_ins);
   const int rounds = sliced_rounds(grid, n, 32ull * num_blocks, 1);
-  sliced_insert_kernel<<<grid, 256, 0, s>>>(words, num_blocks, ps.sorted, n, ps.offsets, n_slices,
-                                            ps.tiles, rounds);
+  sliced_insert_kernel<<<grid, 256, 0, s>>>(words, num_blocks, slice_shift(num_blocks, false),
+                                            ps.sorted, n, ps.offsets, n_slices, ps.tiles, rounds);
   return launch_status();
 }
 
@@ -729,7 +753,7 @@ sbbf_status launch_find_partitioned(const uint32_t* words, uint32_t num_blocks,
                                     const uint64_t* hashes, uint64_t n, uint32_t* d_out,
                                     void* scratch, cudaStream_t s) {
   if (n == 0) return SBBF_OK;
-  const uint32_t n_slices = slices_of(num_blocks);
+  const uint32_t n_slices = slices_of(num_blocks, true);
   if (n_slices == 0 || n_slices > kMaxSlices) return SBBF_EINVAL;
   for (uint64_t off = 0; off < n; off += kMaxIndexedKeys) {
     const uint64_t m = n - off < kMaxIndexedKeys ? n - off : kMaxIndexedKeys;
@@ -742,8 +766,9 @@ sbbf_status launch_find_partitioned(const uint32_t* words, uint32_t num_blocks,
     static int occ_find = occupancy(sliced_find_kernel, 256);
     const unsigned grid = grid_for((m + 63) / 64, 8, occ_find);
     const int rounds = sliced_rounds(grid, m, 32ull * num_blocks, 2);
-    sliced_find_kernel<<<grid, 256, 0, s>>>(words, num_blocks, ps.sorted, ps.idx, m, ps.offsets,
-                                            n_slices, ps.tiles, out, rounds);
+    sliced_find_kernel<<<grid, 256, 0, s>>>(words, num_blocks, slice_shift(num_blocks, true),
+                                            ps.sorted, ps.idx, m, ps.offsets, n_slices, ps.tiles,
+                                            out, rounds);
     st = launch_status();
     if (st != SBBF_OK) return st;
   }

@@ -336,7 +336,7 @@ PARTITION_CASES = [(2**20, 0), (2**20, 1), (2**20 + 5, 16385), (3 * 2**20 - 1, 1
 @pytest.mark.parametrize("B,n", PARTITION_CASES)
 def test_partitioned_insert_equals_oracle(B, n):
     """Slice-partitioned inserts (forced on) give the oracle's filter,
-    across slice counts 1..6, ragged tiles and tails."""
+    across slice counts 8..41 (4 MiB slices for inserts), ragged tiles and tails."""
     keys = inp.stream(130 + B % 11, 0, n)
     f = sb.Filter(B).set_partitioning(sb.PARTITION_ON)
     f.insert(to_dev(keys))
