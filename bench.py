@@ -35,6 +35,12 @@ DOMINANT_KERNEL = "find_kernel"
 # Algorithmic HBM bytes per lookup with an L2-resident filter: the 8-byte
 # hash read once plus its 1/8-byte share of the packed result.
 LOOKUP_HBM_BYTES_L2_RESIDENT = 8.0 + 1.0 / 8.0
+# Measured ceilings of random 32-byte block reads on GB300 (the random-sector
+# microbenchmark, paper_2101_01719_gb300/microbench/random_sector.cu and
+# tma_gather.cu): blocks resident in L2, and blocks in HBM (where every
+# random block costs about 128 bytes of DRAM traffic).
+RANDOM_BLOCK_CEILING_L2 = 293.0   # G blocks/s
+RANDOM_BLOCK_CEILING_HBM = 40.8   # G blocks/s
 # ... and with a filter larger than L2: plus one 32-byte block read.
 LOOKUP_HBM_BYTES_HBM_RESIDENT = 8.0 + 32.0 + 1.0 / 8.0
 # Insert: the hash, plus a 32-byte block read and written back when the
@@ -354,12 +360,26 @@ def run_ours(args):
         staged = e2e_run(sb.PIPE_COPY)
         direct = e2e_run(sb.PIPE_DIRECT)
         best = "staged" if staged >= direct else "direct"
+        # the host link alone: one pinned host-to-device copy of the lookups
+        dq = torch.empty_like(qry)
+        dq.copy_(h_q, non_blocking=True)
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        for _ in range(3):
+            dq.copy_(h_q, non_blocking=True)
+        torch.cuda.synchronize()
+        link_gbs = 3 * h_q.numel() * 8 / (time.perf_counter() - a) / 1e9
+        del dq
         e2e = {"value": max(staged, direct), "unit": UNIT,
                "h2d_bytes_per_step": 8 * keys_per_step,
                "d2h_bytes_per_step": 4 * sb.out_words(w.n_lookup),
                "path": "sbbf_insert_hashes_host / sbbf_find_hashes_host on pinned host "
                        "buffers, pipe mode %s" % best,
-               "staged_copies": round(staged, 3), "direct_access": round(direct, 3)}
+               "staged_copies": round(staged, 3), "direct_access": round(direct, 3),
+               "h2d_link_gbs": round(link_gbs, 1)}
+        # host bytes moved per second by the e2e calls, against the link alone
+        step_bytes = e2e["h2d_bytes_per_step"] + e2e["d2h_bytes_per_step"]
+        e2e["link_frac"] = round(e2e["value"] / keys_per_step * step_bytes / link_gbs, 4)
         del h_ins, h_q, h_out, pipe
 
     peak, peak_kind = measured_peaks()
@@ -399,7 +419,17 @@ def run_ours(args):
                      "bytes_per_key": per_key, "traffic": traffic,
                      "insert": {"achieved": round(ins_achieved, 1), "unit": "GB/s",
                                 "frac": round(ins_achieved / peak, 4),
-                                "bytes_per_key": ins_per_key}},
+                                "bytes_per_key": ins_per_key},
+                     # what actually bounds a random-block lookup: one random
+                     # 32-byte block per key at the measured random-read rate
+                     "random_block_ceiling": {
+                         "where": "L2" if l2_resident else "HBM",
+                         "value": (RANDOM_BLOCK_CEILING_L2 if l2_resident
+                                   else RANDOM_BLOCK_CEILING_HBM),
+                         "unit": "G blocks/s",
+                         "frac": round(w.n_lookup / (find_ms / 1e3) / 1e9
+                                       / (RANDOM_BLOCK_CEILING_L2 if l2_resident
+                                          else RANDOM_BLOCK_CEILING_HBM), 4)}},
         "rows": {"insert_gkeys_s": round(w.n_insert / (insert_ms / 1e3) / 1e9, 3),
                  "lookup_gkeys_s": round(w.n_lookup / (find_ms / 1e3) / 1e9, 3),
                  "insert_ms": round(insert_ms, 5), "lookup_ms": round(find_ms, 5),
