@@ -55,9 +55,6 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
-// Keys per thread per load round of the count pass (16-byte loads of two
-// consecutive keys, so every round of a CTA reads a contiguous span).
-constexpr int kKeysPerThread = 16;
 constexpr int kCountThreads = 1024;
 
 // Adds 1 to bins[p] for every valid lane's p.  With few bins (kFew) a warp
@@ -103,39 +100,112 @@ __host__ __device__ __forceinline__ uint64_t range_keys(uint64_t n, uint32_t cta
   return (r + 1) & ~1ull;
 }
 
-// hist[c * n_slices + p] = keys of CTA c's range that fall in slice p.
+// ---- bulk copies into shared memory ------------------------------------------
+
+constexpr uint64_t kWaitNs = 2000ull * 1000 * 1000;  // a tile copy is microseconds
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Polls the mbarrier phase with the given parity; false after kWaitNs.
+__device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; "
+        "selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+}
+
+// One thread: copy `bytes` (a multiple of 16, 16-byte aligned ends) from
+// global src to shared dst, completing on mbarrier bar (armed here; a
+// zero-byte copy just arrives).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (bytes == 0) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+    return;
+  }
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// hist[c * n_slices + p] = keys of CTA c's range that fall in slice p.  The
+// range streams through shared memory in tiles of kCountTile keys,
+// double-buffered bulk copies like the scatter's (plain loads when the key
+// array is not 16-byte aligned or a copy did not complete in time), so the
+// histogram atomics of one tile overlap the copy of the next.
+constexpr uint32_t kCountTile = 8192;
+
 template <bool kFew>
-__global__ void __launch_bounds__(kCountThreads)
+__global__ void __launch_bounds__(kCountThreads, 1)
     count_kernel(const uint64_t* __restrict__ hashes, uint64_t n, uint32_t nb, int shift,
                  uint32_t n_slices, uint64_t range, unsigned* __restrict__ hist) {
-  extern __shared__ unsigned s_cnt[];
+  extern __shared__ __align__(16) unsigned long long smem[];
+  uint64_t* s_buf0 = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* s_buf1 = s_buf0 + kCountTile;
+  unsigned* s_cnt = reinterpret_cast<unsigned*>(s_buf1 + kCountTile);
+  __shared__ __align__(8) unsigned long long s_bar[2];
   for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x) s_cnt[i] = 0;
-  __syncthreads();
   const uint64_t pol = policy_evict_first();
-  const bool vec = (reinterpret_cast<uintptr_t>(hashes) & 15) == 0;
   const uint64_t a = static_cast<uint64_t>(blockIdx.x) * range;
   const uint64_t b = a + range < n ? a + range : n;
-  const uint64_t per_round = static_cast<uint64_t>(kKeysPerThread) * blockDim.x;
-  for (uint64_t t0 = a; t0 < b; t0 += per_round) {
-    uint64_t h[kKeysPerThread];
-    bool ok[kKeysPerThread];
-#pragma unroll
-    for (int i = 0; i < kKeysPerThread; i += 2) {
-      const uint64_t k = t0 + static_cast<uint64_t>(i / 2) * 2 * blockDim.x + 2 * threadIdx.x;
-      ok[i] = k < b;
-      ok[i + 1] = k + 1 < b;
-      if (vec && ok[i + 1]) {
-        load_keys2(hashes + k, pol, h[i], h[i + 1]);
-      } else {
-        h[i] = ok[i] ? load_key1(hashes + k, pol) : 0;
-        h[i + 1] = ok[i + 1] ? load_key1(hashes + k + 1, pol) : 0;
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < kKeysPerThread; ++i)
-      count_warp<kFew>(s_cnt, n_slices, ok[i], ok[i] ? slice_of(h[i], nb, shift) : 0u);
+  const uint64_t n_tiles = a < b ? (b - a + kCountTile - 1) / kCountTile : 0;
+  bool bulk = (reinterpret_cast<uintptr_t>(hashes) & 15) == 0 && n_tiles > 0;
+  const uint32_t bar0 = smem_u32(&s_bar[0]), bar1 = smem_u32(&s_bar[1]);
+  if (threadIdx.x == 0 && bulk) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  auto issue = [&](uint64_t t) {
+    const uint64_t t0 = a + t * kCountTile;
+    const uint64_t m = b - t0 < kCountTile ? b - t0 : kCountTile;
+    bulk_load((t & 1) ? s_buf1 : s_buf0, hashes + t0, static_cast<uint32_t>((m & ~1ull) * 8),
+              (t & 1) ? bar1 : bar0);
+  };
+  if (threadIdx.x == 0 && bulk) issue(0);
+  uint32_t parity = 0;
+  for (uint64_t t = 0; t < n_tiles; ++t) {
+    const uint64_t t0 = a + t * kCountTile;
+    const uint32_t m = static_cast<uint32_t>(b - t0 < kCountTile ? b - t0 : kCountTile);
+    const int cur = static_cast<int>(t & 1);
+    uint64_t* s_in = cur ? s_buf1 : s_buf0;
+    if (bulk) {
+      if (threadIdx.x == 0 && t + 1 < n_tiles) issue(t + 1);
+      const bool ok = wait_phase(cur ? bar1 : bar0, (parity >> cur) & 1);
+      parity ^= 1u << cur;
+      bulk = __syncthreads_and(ok);
+      if (bulk && (m & 1) && threadIdx.x == 0) s_in[m - 1] = load_key1(hashes + t0 + m - 1, pol);
+      __syncthreads();
+    }
+    for (uint32_t j0 = 0; j0 < m; j0 += blockDim.x) {
+      const uint32_t j = j0 + threadIdx.x;
+      const bool v = j < m;
+      const uint64_t key = !v ? 0 : bulk ? s_in[j] : load_key1(hashes + t0 + j, pol);
+      count_warp<kFew>(s_cnt, n_slices, v, v ? slice_of(key, nb, shift) : 0u);
+    }
+    __syncthreads();  // this buffer's readers are done before it is refilled
+  }
   for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x)
     hist[static_cast<uint64_t>(blockIdx.x) * n_slices + i] = s_cnt[i];
 }
@@ -223,54 +293,6 @@ __device__ __forceinline__ void cta_exclusive_scan(unsigned* vals, uint32_t n, u
     run += v;
   }
   __syncthreads();
-}
-
-// ---- bulk copies into shared memory ------------------------------------------
-
-constexpr uint64_t kWaitNs = 2000ull * 1000 * 1000;  // a tile copy is microseconds
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Polls the mbarrier phase with the given parity; false after kWaitNs.
-__device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity) {
-  const uint64_t t0 = global_ns();
-  for (;;) {
-    uint32_t done;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; "
-        "selp.u32 %0, 1, 0, p; }"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (global_ns() - t0 > kWaitNs) return false;
-  }
-}
-
-// One thread: copy `bytes` (a multiple of 16, 16-byte aligned ends) from
-// global src to shared dst, completing on mbarrier bar (armed here; a
-// zero-byte copy just arrives).
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  if (bytes == 0) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-    return;
-  }
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-  asm volatile(
-      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
 }
 
 // Shared memory of the scatter: two input tiles, the sorted tile, the
@@ -694,7 +716,15 @@ sbbf_status partition(const uint64_t* hashes, uint64_t n, uint32_t num_blocks, u
   const int shift = slice_shift(num_blocks, with_index);
   const uint32_t ctas = partition_ctas();
   const uint64_t range = range_keys(n, ctas);
-  const size_t count_smem = 4ull * n_slices;
+  const size_t count_smem = 16ull * kCountTile + 4ull * n_slices;
+  static const bool count_attr = [] {
+    cudaFuncSetAttribute(count_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(kSmemBudget));
+    cudaFuncSetAttribute(count_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(kSmemBudget));
+    return true;
+  }();
+  (void)count_attr;
   if (few)
     count_kernel<true><<<ctas, kCountThreads, count_smem, s>>>(hashes, n, num_blocks, shift,
                                                               n_slices, range, ps.hist);
