@@ -296,17 +296,19 @@ __device__ __forceinline__ void cta_exclusive_scan(unsigned* vals, uint32_t n, u
 }
 
 // Shared memory of the scatter: two input tiles, the sorted tile, the
-// per-slice cursors (u64), counts and run starts (u32), and the tile
-// positions of the sorted keys (u16, lookups only).
+// per-slice output cursors (u64) and counts / run starts / rank cursors
+// (u32), and the tile positions of the sorted keys (u16, lookups only).
 __host__ __device__ constexpr size_t scatter_smem_bytes(uint32_t tile, uint32_t n_slices,
                                                         bool with_index) {
-  return 3ull * 8 * tile + 16ull * n_slices + (with_index ? 2ull * tile : 0);
+  return 3ull * 8 * tile + 12ull * n_slices + (with_index ? 2ull * tile : 0);
 }
 
 // Keys into slice order.  CTA c streams its range in tiles of kT keys: the
-// tile is counted per slice, counting-sorted into shared memory, and each
+// tile is counted per slice, the counts are scanned in place into run starts
+// that then serve as rank cursors (one shared atomic places a key), and each
 // slice's run is written at the CTA's cursor for that slice (from the scan),
-// which then advances.  Tile t+1 is bulk-copied into the other buffer while
+// kept during the tile as cursor minus run start so that a key's output
+// position is one add.  Tile t+1 is bulk-copied into the other buffer while
 // tile t is processed.  The copies need a 16-byte aligned key array; with
 // any other alignment, or if a copy ever failed to complete in time, the
 // CTA reads the keys straight from global memory instead.
@@ -321,8 +323,7 @@ __global__ void __launch_bounds__(kPartThreads, 1)
   uint64_t* s_sorted = s_buf1 + kT;
   unsigned long long* s_cursor = reinterpret_cast<unsigned long long*>(s_sorted + kT);
   unsigned* s_cnt = reinterpret_cast<unsigned*>(s_cursor + n_slices);
-  unsigned* s_off = s_cnt + n_slices;
-  uint16_t* s_pos = reinterpret_cast<uint16_t*>(s_off + n_slices);  // kIndex
+  uint16_t* s_pos = reinterpret_cast<uint16_t*>(s_cnt + n_slices);  // kIndex
   __shared__ unsigned warp_sums[32];
   __shared__ __align__(8) unsigned long long s_bar[2];
 
@@ -330,8 +331,10 @@ __global__ void __launch_bounds__(kPartThreads, 1)
   if (a >= n) return;  // the whole CTA: nothing of the key array is ours
   const uint64_t b = a + range < n ? a + range : n;
   const uint64_t n_tiles = (b - a + kT - 1) / kT;
-  for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x)
+  for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x) {
     s_cursor[i] = base[static_cast<uint64_t>(blockIdx.x) * n_slices + i];
+    s_cnt[i] = 0;
+  }
   bool bulk = (reinterpret_cast<uintptr_t>(hashes) & 15) == 0;  // uniform over the CTA
   const uint32_t bar0 = smem_u32(&s_bar[0]), bar1 = smem_u32(&s_bar[1]);
   if (threadIdx.x == 0 && bulk) {
@@ -360,51 +363,50 @@ __global__ void __launch_bounds__(kPartThreads, 1)
     if (bulk) {
       // the other buffer's last reader finished at the previous tile's end
       if (threadIdx.x == 0 && t + 1 < n_tiles) issue(t + 1);
+      // an odd last key lies past the copied span: stored before the barrier
+      if ((m & 1) && threadIdx.x == 0) s_in[m - 1] = load_key1(hashes + t0 + m - 1, pol);
       const bool ok = wait_phase(cur ? bar1 : bar0, (parity >> cur) & 1);
       parity ^= 1u << cur;
       bulk = __syncthreads_and(ok);  // all threads agree; on failure never use the buffers again
-      if (bulk && (m & 1) && threadIdx.x == 0) s_in[m - 1] = load_key1(hashes + t0 + m - 1, pol);
     }
     const bool from_smem = bulk;
     auto key_at = [&](uint32_t j) -> uint64_t {
       return from_smem ? s_in[j] : load_key1(hashes + t0 + j, pol);
     };
-    for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x) s_cnt[i] = 0;
-    __syncthreads();
     for (uint32_t j0 = 0; j0 < m; j0 += blockDim.x) {
       const uint32_t j = j0 + threadIdx.x;
       const bool v = j < m;
       count_warp<kFew>(s_cnt, n_slices, v, v ? slice_of(key_at(j), nb, shift) : 0u);
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x) s_off[i] = s_cnt[i];
-    __syncthreads();
-    cta_exclusive_scan(s_off, n_slices, warp_sums);  // local run starts
-    for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x) s_cnt[i] = 0;
-    __syncthreads();
+    cta_exclusive_scan(s_cnt, n_slices, warp_sums);  // counts -> run starts (ends with a barrier)
+    for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x) s_cursor[i] -= s_cnt[i];
+    __syncthreads();  // run starts are read before the rank atomics move them
     for (uint32_t j0 = 0; j0 < m; j0 += blockDim.x) {
       const uint32_t j = j0 + threadIdx.x;
       const bool v = j < m;
       const uint64_t key = v ? key_at(j) : 0;
       const uint32_t q = v ? slice_of(key, nb, shift) : 0u;
-      const unsigned r = rank_warp<kFew>(s_cnt, n_slices, v, q);
+      const unsigned at = rank_warp<kFew>(s_cnt, n_slices, v, q);  // run start + rank
       if (v) {
-        s_sorted[s_off[q] + r] = key;
-        if (kIndex) s_pos[s_off[q] + r] = static_cast<uint16_t>(j);
+        s_sorted[at] = key;
+        if (kIndex) s_pos[at] = static_cast<uint16_t>(j);
       }
     }
     __syncthreads();
     for (uint32_t j = threadIdx.x; j < m; j += blockDim.x) {
       const uint64_t key = s_sorted[j];
-      const uint32_t q = slice_of(key, nb, shift);
-      const unsigned long long pos = s_cursor[q] + (j - s_off[q]);
+      const unsigned long long pos = s_cursor[slice_of(key, nb, shift)] + j;
       if (pos < n) {  // in range unless the input changed between the passes
         out[pos] = key;
         if (kIndex) out_idx[pos] = static_cast<uint32_t>(t0 + s_pos[j]);
       }
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x) s_cursor[i] += s_cnt[i];
+    for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x) {
+      s_cursor[i] += s_cnt[i];  // s_cnt[i] is now the run's end: the cursor advances by its length
+      s_cnt[i] = 0;
+    }
     __syncthreads();
   }
 }
