@@ -717,10 +717,8 @@ def run_reference(args):
             "ms_per_step": round(1e3 * elapsed / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic (seeded splitmix64 hashes)",
-            "config": {"workload": w.name, "num_blocks": num_blocks, "lanes": args.lanes,
-                   "keys": ("64-bit hashes" if args.keys == "hashes"
-                            else "%s keys, XXH64 in the kernels" % args.keys),
-                       "n_insert": w.n_insert, "n_lookup": w.n_lookup,
+            "config": {"workload": w.name, "num_blocks": w.num_blocks, "lanes": 8,
+                       "keys": "64-bit hashes", "n_insert": w.n_insert, "n_lookup": w.n_lookup,
                        "member_frac": w.member_frac},
             "cpu_baseline": {"value": cb["value"], "unit": UNIT, "cores": cb["cores"],
                              "kind": "oracle", "sample": cb["sample"]},
