@@ -29,7 +29,7 @@ def test_reference_arm_prints_the_contract_line():
 
 def test_bench_uses_no_undefined_names():
     tree = ast.parse(open(os.path.join(ROOT, "bench.py")).read())
-    defined = set(dir(builtins))
+    defined = set(dir(builtins)) | {"__file__", "__name__"}
     for node in ast.walk(tree):
         if isinstance(node, (ast.Import, ast.ImportFrom)):
             defined.update((a.asname or a.name).split(".")[0] for a in node.names)
