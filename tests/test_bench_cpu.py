@@ -27,17 +27,39 @@ def test_reference_arm_prints_the_contract_line():
     assert line["e2e"]["h2d_bytes_per_step"] == 0
 
 
+def _stored_names(node):
+    names = set()
+    for n in ast.walk(node):
+        if isinstance(n, (ast.Import, ast.ImportFrom)):
+            names.update((a.asname or a.name).split(".")[0] for a in n.names)
+        elif isinstance(n, (ast.FunctionDef, ast.ClassDef)):
+            names.add(n.name)
+        elif isinstance(n, ast.Name) and isinstance(n.ctx, (ast.Store, ast.Del)):
+            names.add(n.id)
+        elif isinstance(n, ast.arg):
+            names.add(n.arg)
+    return names
+
+
 def test_bench_uses_no_undefined_names():
+    """Each top-level function may use builtins, module-level names and the
+    names it (or a function nested in it) binds -- not a local of another
+    function."""
     tree = ast.parse(open(os.path.join(ROOT, "bench.py")).read())
-    defined = set(dir(builtins)) | {"__file__", "__name__"}
-    for node in ast.walk(tree):
+    module = set(dir(builtins)) | {"__file__", "__name__"}
+    for node in tree.body:
         if isinstance(node, (ast.Import, ast.ImportFrom)):
-            defined.update((a.asname or a.name).split(".")[0] for a in node.names)
+            module.update((a.asname or a.name).split(".")[0] for a in node.names)
         elif isinstance(node, (ast.FunctionDef, ast.ClassDef)):
-            defined.add(node.name)
-        elif isinstance(node, ast.Name) and isinstance(node.ctx, (ast.Store, ast.Del)):
-            defined.add(node.id)
-        elif isinstance(node, ast.arg):
-            defined.add(node.arg)
-    used = {n.id for n in ast.walk(tree) if isinstance(n, ast.Name) and isinstance(n.ctx, ast.Load)}
-    assert not (used - defined), sorted(used - defined)
+            module.add(node.name)
+        elif isinstance(node, (ast.Assign, ast.AnnAssign, ast.AugAssign)):
+            module |= _stored_names(node)
+    missing = {}
+    for node in tree.body:
+        if isinstance(node, (ast.FunctionDef, ast.ClassDef)):
+            scope = module | _stored_names(node)
+            used = {n.id for n in ast.walk(node)
+                    if isinstance(n, ast.Name) and isinstance(n.ctx, ast.Load)}
+            if used - scope:
+                missing[node.name] = sorted(used - scope)
+    assert not missing, missing
