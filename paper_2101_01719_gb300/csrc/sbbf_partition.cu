@@ -631,26 +631,50 @@ uint32_t scatter_tile(uint32_t n_slices, bool with_index) {
 // ranges).
 uint32_t partition_ctas() { return static_cast<uint32_t>(sm_count()); }
 
-// Blocks per slice, 2^shift.  A slice's blocks stay in L2 from its prefetch
-// until its last key is processed, so about two slices plus the keys in
-// flight must fit there.  For inserts slices get smaller as long as the
-// partition's fan-out stays near kTargetSlices (the scatter's runs per tile
-// shrink with more slices), between 4 and 32 MiB: measured 67.6 against 60.3
-// G inserts/s on a 2 GiB filter.  Lookups keep 32 MiB slices: their scatter
-// also writes 4-byte positions, whose shorter runs cost more than the smaller
-// slices gain (59.1 against 62.2 G lookups/s on the same filter).
-int slice_shift(uint32_t num_blocks, bool lookup) {
-  if (lookup) return kMaxSliceShift;
+uint32_t slices_at(uint32_t num_blocks, int shift) {
+  return static_cast<uint32_t>((static_cast<uint64_t>(num_blocks) + (1ull << shift) - 1) >> shift);
+}
+
+// Smallest slice shift lookups may take: 4 MiB, or larger until at most 1024
+// slices (the scatter's shared-memory tables).
+int lookup_min_shift(uint32_t num_blocks) {
   int shift = kMinSliceShift;
-  while (shift < kMaxSliceShift &&
-         ((static_cast<uint64_t>(num_blocks) + (1ull << shift) - 1) >> shift) > kTargetSlices)
-    ++shift;
+  while (shift < kMaxSliceShift && slices_at(num_blocks, shift) > 1024) ++shift;
   return shift;
 }
 
-uint32_t slices_of(uint32_t num_blocks, bool lookup) {
-  const int shift = slice_shift(num_blocks, lookup);
-  return static_cast<uint32_t>((static_cast<uint64_t>(num_blocks) + (1ull << shift) - 1) >> shift);
+int find_occupancy() {
+  static const int occ = occupancy(sliced_find_kernel, 256);
+  return occ;
+}
+
+// Blocks per slice, 2^shift.  A slice's blocks stay in L2 from its prefetch
+// until its last key is processed, so a slice plus the keys in flight (and
+// those prefetched ahead) must fit there.  For inserts slices get smaller as
+// long as the partition's fan-out stays near kTargetSlices (the scatter's runs
+// per tile shrink with more slices), between 4 and 32 MiB: measured 67.6
+// against 60.3 G inserts/s on a 2 GiB filter.  For lookups the slice stream
+// was measured to keep its reads exact while slice + 1.5 windows of filter
+// bytes stayed below ~48 MiB (2 GiB filter: 62 MB live, 5.85 GB of DRAM reads
+// for 3.5 GB of keys and filter; 46 MB, 4.31 GB), while the scatter of 4-byte
+// positions pays for every extra slice: lookups take the largest slice (at
+// most 32 MiB) within that budget, no smaller than lookup_min_shift.
+int slice_shift(uint32_t num_blocks, uint64_t n, bool lookup) {
+  if (lookup) {
+    const double filter_bytes = 32.0 * num_blocks;
+    const unsigned grid = grid_for((n + 63) / 64, 8, find_occupancy());
+    const int rounds = sliced_rounds(grid, n, 32ull * num_blocks, 2);
+    const double window_bytes = static_cast<double>(grid) * 8 * rounds * 64 * filter_bytes /
+                                static_cast<double>(n);
+    const double slice_max = 48.0 * 1024 * 1024 - 1.5 * window_bytes;
+    const int floor_shift = lookup_min_shift(num_blocks);
+    int shift = kMaxSliceShift;
+    while (shift > floor_shift && 32.0 * static_cast<double>(1ull << shift) > slice_max) --shift;
+    return shift;
+  }
+  int shift = kMinSliceShift;
+  while (shift < kMaxSliceShift && slices_at(num_blocks, shift) > kTargetSlices) ++shift;
+  return shift;
 }
 
 }  // namespace
@@ -658,7 +682,9 @@ uint32_t slices_of(uint32_t num_blocks, bool lookup) {
 // Scratch bytes for a partitioned insert (or, with_index, lookup) of n keys
 // into num_blocks blocks.
 uint64_t partition_scratch_bytes(uint32_t num_blocks, uint64_t n, bool with_index) {
-  const uint64_t s = slices_of(num_blocks, with_index);
+  // lookups: the most slices their rule can pick, so any piece fits
+  const uint64_t s = with_index ? slices_at(num_blocks, lookup_min_shift(num_blocks))
+                                : slices_at(num_blocks, slice_shift(num_blocks, n, false));
   const uint64_t g = partition_ctas();
   return align256(4 * g * s) + align256(8 * g * s) + align256(8 * (s + 1)) + 256 +
          align256(8 * n) + (with_index ? align256(4 * n) : 0);
@@ -712,10 +738,9 @@ sbbf_status launch_scatter(const uint64_t* hashes, uint64_t n, uint32_t nb, int 
 
 // Steps 1-3: per-CTA counts, offsets and bases, and the slice-ordered keys
 // (and positions).
-sbbf_status partition(const uint64_t* hashes, uint64_t n, uint32_t num_blocks, uint32_t n_slices,
-                      const PartScratch& ps, bool with_index, cudaStream_t s) {
+sbbf_status partition(const uint64_t* hashes, uint64_t n, uint32_t num_blocks, int shift,
+                      uint32_t n_slices, const PartScratch& ps, bool with_index, cudaStream_t s) {
   const bool few = n_slices <= kFewSlices;
-  const int shift = slice_shift(num_blocks, with_index);
   const uint32_t ctas = partition_ctas();
   const uint64_t range = range_keys(n, ctas);
   const size_t count_smem = 16ull * kCountTile + 4ull * n_slices;
@@ -738,23 +763,16 @@ sbbf_status partition(const uint64_t* hashes, uint64_t n, uint32_t num_blocks, u
   scan_kernel<<<1, 1024, 0, s>>>(ps.hist, ctas, n_slices, ps.offsets, ps.base);
   if ((st = launch_status()) != SBBF_OK) return st;
   const bool big = scatter_tile(n_slices, with_index) == 8192;
+  const auto args = [&](auto launch) {
+    return launch(hashes, n, num_blocks, shift, n_slices, range, ctas, ps, s);
+  };
   if (few)
-    return with_index ? launch_scatter<true, true, 8192>(hashes, n, num_blocks, shift, n_slices, range,
-                                                         ctas, ps, s)
-                      : launch_scatter<true, false, 8192>(hashes, n, num_blocks, shift, n_slices, range,
-                                                          ctas, ps, s);
+    return with_index ? args(launch_scatter<true, true, 8192>)
+                      : args(launch_scatter<true, false, 8192>);
   if (with_index)
-    return big ? launch_scatter<false, true, 8192>(hashes, n, num_blocks, shift, n_slices, range, ctas,
-                                                   ps, s)
-               : launch_scatter<false, true, 4096>(hashes, n, num_blocks, shift, n_slices, range, ctas,
-                                                   ps, s);
-  return big ? launch_scatter<false, false, 8192>(hashes, n, num_blocks, shift, n_slices, range, ctas,
-                                                  ps, s)
-             : launch_scatter<false, false, 4096>(hashes, n, num_blocks, shift, n_slices, range, ctas,
-                                                  ps, s);
+    return big ? args(launch_scatter<false, true, 8192>) : args(launch_scatter<false, true, 4096>);
+  return big ? args(launch_scatter<false, false, 8192>) : args(launch_scatter<false, false, 4096>);
 }
-
-
 
 }  // namespace
 
@@ -763,17 +781,18 @@ sbbf_status partition(const uint64_t* hashes, uint64_t n, uint32_t num_blocks, u
 sbbf_status launch_insert_partitioned(uint32_t* words, uint32_t num_blocks, const uint64_t* hashes,
                                       uint64_t n, void* scratch, cudaStream_t s) {
   if (n == 0) return SBBF_OK;
-  const uint32_t n_slices = slices_of(num_blocks, false);
+  const int shift = slice_shift(num_blocks, n, false);
+  const uint32_t n_slices = slices_at(num_blocks, shift);
   if (n_slices == 0 || n_slices > kMaxSlices) return SBBF_EINVAL;
   const PartScratch ps = carve(scratch, partition_ctas(), n_slices, n);
-  sbbf_status st = partition(hashes, n, num_blocks, n_slices, ps, false, s);
+  sbbf_status st = partition(hashes, n, num_blocks, shift, n_slices, ps, false, s);
   if (st != SBBF_OK) return st;
   SBBF_CUDA(cudaMemsetAsync(ps.tiles, 0, 8, s));
   static int occ_ins = occupancy(sliced_insert_kernel, 256);
   const unsigned grid = grid_for((n + 63) / 64, 8, occ_ins);
   const int rounds = sliced_rounds(grid, n, 32ull * num_blocks, 1);
-  sliced_insert_kernel<<<grid, 256, 0, s>>>(words, num_blocks, slice_shift(num_blocks, false),
-                                            ps.sorted, n, ps.offsets, n_slices, ps.tiles, rounds);
+  sliced_insert_kernel<<<grid, 256, 0, s>>>(words, num_blocks, shift, ps.sorted, n, ps.offsets,
+                                            n_slices, ps.tiles, rounds);
   return launch_status();
 }
 
@@ -785,22 +804,21 @@ sbbf_status launch_find_partitioned(const uint32_t* words, uint32_t num_blocks,
                                     const uint64_t* hashes, uint64_t n, uint32_t* d_out,
                                     void* scratch, cudaStream_t s) {
   if (n == 0) return SBBF_OK;
-  const uint32_t n_slices = slices_of(num_blocks, true);
-  if (n_slices == 0 || n_slices > kMaxSlices) return SBBF_EINVAL;
   for (uint64_t off = 0; off < n; off += kMaxIndexedKeys) {
     const uint64_t m = n - off < kMaxIndexedKeys ? n - off : kMaxIndexedKeys;
+    const int shift = slice_shift(num_blocks, m, true);
+    const uint32_t n_slices = slices_at(num_blocks, shift);
+    if (n_slices == 0 || n_slices > kMaxSlices) return SBBF_EINVAL;
     const PartScratch ps = carve(scratch, partition_ctas(), n_slices, m);
-    sbbf_status st = partition(hashes + off, m, num_blocks, n_slices, ps, true, s);
+    sbbf_status st = partition(hashes + off, m, num_blocks, shift, n_slices, ps, true, s);
     if (st != SBBF_OK) return st;
     uint32_t* out = d_out + off / 32;
     SBBF_CUDA(cudaMemsetAsync(out, 0, 4 * ((m + 31) / 32), s));
     SBBF_CUDA(cudaMemsetAsync(ps.tiles, 0, 8, s));
-    static int occ_find = occupancy(sliced_find_kernel, 256);
-    const unsigned grid = grid_for((m + 63) / 64, 8, occ_find);
+    const unsigned grid = grid_for((m + 63) / 64, 8, find_occupancy());
     const int rounds = sliced_rounds(grid, m, 32ull * num_blocks, 2);
-    sliced_find_kernel<<<grid, 256, 0, s>>>(words, num_blocks, slice_shift(num_blocks, true),
-                                            ps.sorted, ps.idx, m, ps.offsets, n_slices, ps.tiles,
-                                            out, rounds);
+    sliced_find_kernel<<<grid, 256, 0, s>>>(words, num_blocks, shift, ps.sorted, ps.idx, m,
+                                            ps.offsets, n_slices, ps.tiles, out, rounds);
     st = launch_status();
     if (st != SBBF_OK) return st;
   }
