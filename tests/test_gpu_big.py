@@ -93,13 +93,14 @@ def test_three_billion_inserts_sampled_parity(w):
     assert abs((hits - members) - lam) <= 6 * np.sqrt(lam) + 0.02 * lam + 10
 
 
-def test_partitioned_paths_over_1184_slices():
-    """A 1300-slice (40.6 GiB) filter takes the scatter's 4096-key tiles for
-    lookups (the index no longer fits beside 8192-key tiles).  A few million
-    keys are inserted and looked up partitioned; the touched blocks are
-    rebuilt by the oracle, every member hits, and every answer equals the
-    unpartitioned lookup of the same filter."""
-    B, n = 1300 * 2**20 + 17, 4_000_001
+def test_partitioned_paths_over_1578_slices():
+    """A 1600-slice (50 GiB) filter takes the scatter's 4096-key tiles for
+    lookups (8192-key tiles, their positions and 1600 slice tables no longer
+    fit in shared memory together).  A few million keys are inserted and looked
+    up partitioned; the touched blocks are rebuilt by the oracle, every member
+    hits, and every answer equals the unpartitioned lookup of the same
+    filter."""
+    B, n = 1600 * 2**20 + 17, 4_000_001
     keys = inp.stream(160, 0, n)
     f = sb.Filter(B).set_partitioning(sb.PARTITION_ON)
     f.insert(to_dev(keys))
