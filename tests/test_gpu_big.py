@@ -93,14 +93,16 @@ def test_three_billion_inserts_sampled_parity(w):
     assert abs((hits - members) - lam) <= 6 * np.sqrt(lam) + 0.02 * lam + 10
 
 
-def test_partitioned_paths_over_1578_slices():
-    """A 1600-slice (50 GiB) filter takes the scatter's 4096-key tiles for
-    lookups (8192-key tiles, their positions and 1600 slice tables no longer
-    fit in shared memory together).  A few million keys are inserted and looked
-    up partitioned; the touched blocks are rebuilt by the oracle, every member
+@pytest.mark.parametrize("slices", [1600, 3000])
+def test_partitioned_paths_with_small_scatter_tiles(slices):
+    """Filters of 1600 slices (50 GiB) and 3000 slices (94 GiB) take the
+    scatter's 4096-key tiles: for lookups past ~1578 slices and for inserts
+    past ~2944 (8192-key tiles, positions and slice tables no longer fit in
+    shared memory together).  A few million keys are inserted and looked up
+    partitioned; the touched blocks are rebuilt by the oracle, every member
     hits, and every answer equals the unpartitioned lookup of the same
     filter."""
-    B, n = 1600 * 2**20 + 17, 4_000_001
+    B, n = slices * 2**20 + 17, 4_000_001
     keys = inp.stream(160, 0, n)
     f = sb.Filter(B).set_partitioning(sb.PARTITION_ON)
     f.insert(to_dev(keys))
