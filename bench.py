@@ -692,7 +692,18 @@ def cpu_baseline(w, seconds: float, steps: int = 1):
         t_find += time.perf_counter() - a
         n_find += reps * sample
     value = (n_ins + n_find) / (t_ins + t_find) / 1e9
+    # the oracle as written, on one thread: a 1M-insert / 2M-lookup sample
+    g = oracle.new_filter(w.num_blocks)
+    ns = min(w.n_insert, 1 << 20)
+    a = time.perf_counter()
+    oracle.insert(g, w.num_blocks, keys[:ns])
+    st_ins = ns / (time.perf_counter() - a) / 1e6
+    a = time.perf_counter()
+    oracle.find(f, w.num_blocks, q[: 1 << 21])
+    st_find = (1 << 21) / (time.perf_counter() - a) / 1e6
     return {"value": round(value, 5), "unit": UNIT, "cores": used, "kind": "oracle",
+            "single_thread_insert_mkeys_s": round(st_ins, 2),
+            "single_thread_lookup_mkeys_s": round(st_find, 2),
             "sample": "%d inserts + %d lookups (%d x a %d-query prefix of the lookup stream), "
                       "scalar C oracle on %d threads" % (n_ins, n_find, n_find // sample,
                                                           sample, used),
