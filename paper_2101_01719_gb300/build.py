@@ -42,14 +42,12 @@ def _newest(paths):
     return max((os.path.getmtime(p) for p in paths), default=0.0)
 
 
-def _compile(nvcc, src, debug):
+def _compile(nvcc, src):
     name = os.path.splitext(os.path.basename(src))[0]
     obj = os.path.join(BUILD, name + ".o")
     cmd = [nvcc, *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xptxas", "-v",
            "-Xcompiler", "-fPIC,-O2,-Wall", "-I", INCLUDE, "-I", CSRC,
            "-c", src, "-o", obj]
-    if debug:
-        cmd += ["-DSBBF_DEBUG=1"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     with open(os.path.join(BUILD, "ptxas_%s.txt" % name), "w") as fh:
         fh.write(r.stderr)
@@ -58,7 +56,7 @@ def _compile(nvcc, src, debug):
     return obj
 
 
-def build(force: bool = False, debug: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False) -> str:
     """Compile every csrc/*.cu for sm_103a and link libsbbf.so (skipped when
     the library is newer than every source and header)."""
     srcs = _sources()
@@ -68,7 +66,7 @@ def build(force: bool = False, debug: bool = False, verbose: bool = False) -> st
     nvcc = _nvcc()
     workers = min(len(srcs), max(1, os.cpu_count() or 1))
     with concurrent.futures.ThreadPoolExecutor(workers) as ex:
-        objs = list(ex.map(lambda s: _compile(nvcc, s, debug), srcs))
+        objs = list(ex.map(lambda s: _compile(nvcc, s), srcs))
     tmp = LIB + ".tmp.%d" % os.getpid()
     cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)

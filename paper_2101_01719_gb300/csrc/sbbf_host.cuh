@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstddef>
 #include <cstdint>
@@ -10,6 +11,18 @@
 #include "sbbf.h"
 
 namespace sbbf {
+
+// Names the enclosing scope for profilers and tracers (an NVTX range: the
+// entry point's name around its kernels; nothing happens unless a tool such
+// as ncu --nvtx or nsys is attached).
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
+#define SBBF_TRACE() ::sbbf::TraceRange sbbf_trace_range_(__func__)
+#define SBBF_TRACE_NAMED(name) ::sbbf::TraceRange sbbf_trace_range_(name)
 
 // Records a failing CUDA call for sbbf_last_cuda_error() and maps it.
 sbbf_status record_cuda(cudaError_t e);

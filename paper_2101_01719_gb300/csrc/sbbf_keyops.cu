@@ -114,6 +114,7 @@ extern "C" {
 
 sbbf_status sbbf_hash_keys(const void* d_keys, uint32_t key_bytes, size_t n, uint64_t seed,
                            uint64_t* d_hashes, sbbf_stream_t stream) {
+  SBBF_TRACE();
   if (!fixed_keys_ok(d_keys, key_bytes, n)) return SBBF_EINVAL;
   if (n == 0) return SBBF_OK;
   if (!d_hashes || (reinterpret_cast<uintptr_t>(d_hashes) & 7)) return SBBF_EINVAL;
@@ -124,6 +125,7 @@ sbbf_status sbbf_hash_keys(const void* d_keys, uint32_t key_bytes, size_t n, uin
 
 sbbf_status sbbf_hash_bytes(const uint8_t* d_data, const uint64_t* d_offsets, size_t n,
                             uint64_t seed, uint64_t* d_hashes, sbbf_stream_t stream) {
+  SBBF_TRACE();
   if (!bytes_ok(d_data, d_offsets, n)) return SBBF_EINVAL;
   if (n == 0) return SBBF_OK;
   if (!d_hashes || (reinterpret_cast<uintptr_t>(d_hashes) & 7)) return SBBF_EINVAL;
@@ -132,6 +134,7 @@ sbbf_status sbbf_hash_bytes(const uint8_t* d_data, const uint64_t* d_offsets, si
 
 sbbf_status sbbf_insert_keys(sbbf_t* f, const void* d_keys, uint32_t key_bytes, size_t n,
                              uint64_t seed, sbbf_stream_t stream) {
+  SBBF_TRACE();
   if (!f || !on_device(f) || !fixed_keys_ok(d_keys, key_bytes, n)) return SBBF_EINVAL;
   if (key_bytes == 8)
     return insert_src(f, Key64Input{static_cast<const uint64_t*>(d_keys), seed}, n, stream);
@@ -140,6 +143,7 @@ sbbf_status sbbf_insert_keys(sbbf_t* f, const void* d_keys, uint32_t key_bytes, 
 
 sbbf_status sbbf_find_keys(const sbbf_t* f, const void* d_keys, uint32_t key_bytes, size_t n,
                            uint64_t seed, uint32_t* d_out_bits, sbbf_stream_t stream) {
+  SBBF_TRACE();
   if (!f || !on_device(f) || !fixed_keys_ok(d_keys, key_bytes, n)) return SBBF_EINVAL;
   if (n == 0) return SBBF_OK;
   if (!d_out_bits || (reinterpret_cast<uintptr_t>(d_out_bits) & 3)) return SBBF_EINVAL;
@@ -152,6 +156,7 @@ sbbf_status sbbf_find_keys(const sbbf_t* f, const void* d_keys, uint32_t key_byt
 
 sbbf_status sbbf_insert_bytes(sbbf_t* f, const uint8_t* d_data, const uint64_t* d_offsets,
                               size_t n, uint64_t seed, sbbf_stream_t stream) {
+  SBBF_TRACE();
   if (!f || !on_device(f) || !bytes_ok(d_data, d_offsets, n)) return SBBF_EINVAL;
   return insert_src(f, BytesInput{d_data, d_offsets, seed}, n, stream);
 }
@@ -159,6 +164,7 @@ sbbf_status sbbf_insert_bytes(sbbf_t* f, const uint8_t* d_data, const uint64_t* 
 sbbf_status sbbf_find_bytes(const sbbf_t* f, const uint8_t* d_data, const uint64_t* d_offsets,
                             size_t n, uint64_t seed, uint32_t* d_out_bits,
                             sbbf_stream_t stream) {
+  SBBF_TRACE();
   if (!f || !on_device(f) || !bytes_ok(d_data, d_offsets, n)) return SBBF_EINVAL;
   if (n == 0) return SBBF_OK;
   if (!d_out_bits || (reinterpret_cast<uintptr_t>(d_out_bits) & 3)) return SBBF_EINVAL;

@@ -270,12 +270,14 @@ sbbf_status sbbf_multi_device_words(const sbbf_multi_t* m, uint32_t** d_words, s
 }
 
 sbbf_status sbbf_multi_clear(sbbf_multi_t* m, sbbf_stream_t stream) {
+  SBBF_TRACE();
   if (!on_device(m)) return SBBF_EINVAL;
   return launch_clear(m->words, m->total_blocks * 8, stream);
 }
 
 sbbf_status sbbf_multi_copy_to_host(const sbbf_multi_t* m, uint32_t* h_words, size_t bytes,
                                     sbbf_stream_t stream) {
+  SBBF_TRACE();
   if (!m || !h_words) return SBBF_EINVAL;
   const size_t need = static_cast<size_t>(m->total_blocks) * 32;
   if (bytes < need) return SBBF_EINVAL;
@@ -286,6 +288,7 @@ sbbf_status sbbf_multi_copy_to_host(const sbbf_multi_t* m, uint32_t* h_words, si
 
 sbbf_status sbbf_multi_insert(sbbf_multi_t* m, const uint64_t* d_hashes, const uint32_t* d_ids,
                               size_t n, sbbf_stream_t stream) {
+  SBBF_TRACE();
   if (!on_device(m)) return SBBF_EINVAL;
   if (n == 0) return SBBF_OK;
   if (!d_hashes || !d_ids || (reinterpret_cast<uintptr_t>(d_hashes) & 7) ||
@@ -297,6 +300,7 @@ sbbf_status sbbf_multi_insert(sbbf_multi_t* m, const uint64_t* d_hashes, const u
 
 sbbf_status sbbf_multi_find(const sbbf_multi_t* m, const uint64_t* d_hashes, const uint32_t* d_ids,
                             size_t n, uint32_t* d_out_bits, sbbf_stream_t stream) {
+  SBBF_TRACE();
   if (!on_device(m)) return SBBF_EINVAL;
   if (n == 0) return SBBF_OK;
   if (!d_hashes || !d_ids || !d_out_bits || (reinterpret_cast<uintptr_t>(d_hashes) & 7) ||
@@ -309,6 +313,7 @@ sbbf_status sbbf_multi_find(const sbbf_multi_t* m, const uint64_t* d_hashes, con
 sbbf_status sbbf_multi_insert_segments(sbbf_multi_t* m, const uint64_t* d_hashes,
                                        const uint64_t* d_offsets, size_t n,
                                        sbbf_stream_t stream) {
+  SBBF_TRACE();
   if (!on_device(m)) return SBBF_EINVAL;
   if (n == 0) return SBBF_OK;
   if (!d_hashes || !d_offsets || (reinterpret_cast<uintptr_t>(d_hashes) & 7) ||
@@ -321,6 +326,7 @@ sbbf_status sbbf_multi_insert_segments(sbbf_multi_t* m, const uint64_t* d_hashes
 sbbf_status sbbf_multi_find_segments(const sbbf_multi_t* m, const uint64_t* d_hashes,
                                      const uint64_t* d_offsets, size_t n, uint32_t* d_out_bits,
                                      sbbf_stream_t stream) {
+  SBBF_TRACE();
   if (!on_device(m)) return SBBF_EINVAL;
   if (n == 0) return SBBF_OK;
   if (!d_hashes || !d_offsets || !d_out_bits || (reinterpret_cast<uintptr_t>(d_hashes) & 7) ||
@@ -332,6 +338,7 @@ sbbf_status sbbf_multi_find_segments(const sbbf_multi_t* m, const uint64_t* d_ha
 
 sbbf_status sbbf_multi_insert_each(sbbf_multi_t* m, const uint64_t* d_hashes,
                                    const uint64_t* h_offsets, sbbf_stream_t stream) {
+  SBBF_TRACE();
   if (!on_device(m) || !h_offsets || !d_hashes) return SBBF_EINVAL;
   for (uint32_t t = 0; t < m->n_filters; ++t) {
     if (h_offsets[t + 1] < h_offsets[t]) return SBBF_EINVAL;
@@ -348,6 +355,7 @@ sbbf_status sbbf_multi_insert_each(sbbf_multi_t* m, const uint64_t* d_hashes,
 sbbf_status sbbf_multi_find_each(const sbbf_multi_t* m, const uint64_t* d_hashes,
                                  const uint64_t* h_offsets, uint32_t* d_out_bits,
                                  sbbf_stream_t stream) {
+  SBBF_TRACE();
   if (!on_device(m) || !h_offsets || !d_hashes || !d_out_bits) return SBBF_EINVAL;
   for (uint32_t t = 0; t < m->n_filters; ++t) {
     if (h_offsets[t + 1] < h_offsets[t]) return SBBF_EINVAL;
@@ -405,6 +413,7 @@ sbbf_status sbbf_multi_set_tuning(sbbf_multi_t* m, int op, int form, int threads
 sbbf_status sbbf_multi_tune(sbbf_multi_t* m, int op, int form, const uint64_t* d_hashes,
                             const void* d_offsets_or_ids, size_t n, sbbf_stream_t stream,
                             float* best_ms) {
+  SBBF_TRACE();
   if (!on_device(m) || !d_hashes || !d_offsets_or_ids || n == 0) return SBBF_EINVAL;
   if ((op != SBBF_OP_INSERT && op != SBBF_OP_FIND) ||
       (form != SBBF_FORM_SEGMENTS && form != SBBF_FORM_TAGGED))
@@ -585,6 +594,7 @@ sbbf_status sbbf_multi_graph_launch(sbbf_multi_graph_t* g, const uint64_t* d_ins
                                     const uint64_t* d_ins_offsets, size_t n_ins,
                                     const uint64_t* d_q, const uint64_t* d_q_offsets, size_t n_q,
                                     uint32_t* d_out_bits, sbbf_stream_t stream) {
+  SBBF_TRACE();
   if (!g || !on_device(g->m)) return SBBF_EINVAL;
   if ((n_ins && (!d_ins || !d_ins_offsets)) || (n_q && (!d_q || !d_q_offsets || !d_out_bits)))
     return SBBF_EINVAL;

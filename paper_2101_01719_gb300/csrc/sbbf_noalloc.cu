@@ -142,6 +142,7 @@ extern "C" sbbf_status sbbf_multi_find_noalloc(const uint32_t* d_arena,
                                                size_t n, uint32_t* d_out_bits,
                                                unsigned long long* d_invalid_count,
                                                sbbf_stream_t stream) {
+  SBBF_TRACE();
   if (n_filters == 0 || !d_arena || !d_num_blocks) return SBBF_EINVAL;
   if (n_filters > SBBF_NOALLOC_MAX_FILTERS) return SBBF_ERANGE;
   if (n > 0 && (!d_hashes || !d_ids || !d_out_bits)) return SBBF_EINVAL;

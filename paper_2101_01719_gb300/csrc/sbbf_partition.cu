@@ -780,6 +780,7 @@ sbbf_status partition(const uint64_t* hashes, uint64_t n, uint32_t num_blocks, i
 // partition_scratch_bytes(num_blocks, n, false) bytes of device memory.
 sbbf_status launch_insert_partitioned(uint32_t* words, uint32_t num_blocks, const uint64_t* hashes,
                                       uint64_t n, void* scratch, cudaStream_t s) {
+  SBBF_TRACE_NAMED("sbbf_partitioned_insert");
   if (n == 0) return SBBF_OK;
   const int shift = slice_shift(num_blocks, n, false);
   const uint32_t n_slices = slices_at(num_blocks, shift);
@@ -803,6 +804,7 @@ sbbf_status launch_insert_partitioned(uint32_t* words, uint32_t num_blocks, cons
 sbbf_status launch_find_partitioned(const uint32_t* words, uint32_t num_blocks,
                                     const uint64_t* hashes, uint64_t n, uint32_t* d_out,
                                     void* scratch, cudaStream_t s) {
+  SBBF_TRACE_NAMED("sbbf_partitioned_find");
   if (n == 0) return SBBF_OK;
   for (uint64_t off = 0; off < n; off += kMaxIndexedKeys) {
     const uint64_t m = n - off < kMaxIndexedKeys ? n - off : kMaxIndexedKeys;

@@ -129,6 +129,7 @@ sbbf_status sbbf_host_pipe_destroy(sbbf_host_pipe_t* p) {
 
 sbbf_status sbbf_insert_hashes_host(sbbf_t* f, sbbf_host_pipe_t* p, const uint64_t* h_hashes,
                                     size_t n, sbbf_stream_t stream) {
+  SBBF_TRACE();
   if (!f || !p || f->device != current_device() || p->device != f->device) return SBBF_EINVAL;
   if (n == 0) return SBBF_OK;
   if (!h_hashes) return SBBF_EINVAL;
@@ -152,6 +153,7 @@ sbbf_status sbbf_insert_hashes_host(sbbf_t* f, sbbf_host_pipe_t* p, const uint64
 
 sbbf_status sbbf_find_hashes_host(const sbbf_t* f, sbbf_host_pipe_t* p, const uint64_t* h_hashes,
                                   size_t n, uint32_t* h_out_bits, sbbf_stream_t stream) {
+  SBBF_TRACE();
   if (!f || !p || f->device != current_device() || p->device != f->device) return SBBF_EINVAL;
   if (n == 0) return SBBF_OK;
   if (!h_hashes || !h_out_bits) return SBBF_EINVAL;

@@ -210,6 +210,7 @@ size_t sbbf_serialized_size(const sbbf_t* f) {
 }
 
 sbbf_status sbbf_serialize(const sbbf_t* f, void* h_buf, size_t bytes, sbbf_stream_t stream) {
+  SBBF_TRACE();
   if (!f || !h_buf) return SBBF_EINVAL;
   const size_t payload = filter_bytes(f);
   if (bytes < kNativeHeader + payload) return SBBF_EINVAL;
@@ -229,6 +230,7 @@ sbbf_status sbbf_serialize(const sbbf_t* f, void* h_buf, size_t bytes, sbbf_stre
 }
 
 sbbf_status sbbf_deserialize(const void* h_buf, size_t bytes, sbbf_t** out) {
+  SBBF_TRACE();
   if (!h_buf || !out) return SBBF_EINVAL;
   *out = nullptr;
   const uint8_t* in = static_cast<const uint8_t*>(h_buf);
@@ -313,6 +315,7 @@ size_t sbbf_parquet_size(const sbbf_t* f) {
 
 sbbf_status sbbf_export_parquet(const sbbf_t* f, uint8_t* h_buf, size_t bytes, size_t* written,
                                 sbbf_stream_t stream) {
+  SBBF_TRACE();
   if (!f || !h_buf || f->lanes != 8) return SBBF_EINVAL;
   const uint64_t total = filter_bytes(f);
   size_t h = 0;
@@ -339,6 +342,7 @@ sbbf_status sbbf_export_parquet(const sbbf_t* f, uint8_t* h_buf, size_t bytes, s
 
 sbbf_status sbbf_import_parquet(const uint8_t* h_buf, size_t bytes, sbbf_t** out,
                                 size_t* consumed) {
+  SBBF_TRACE();
   if (!h_buf || !out) return SBBF_EINVAL;
   *out = nullptr;
   uint64_t nbytes = 0;

@@ -311,6 +311,7 @@ sbbf_status make_resident(sbbf_server_t* s, uint32_t f, uint64_t extra,
 
 // Forms and launches one window from the pending requests (lock held).
 sbbf_status launch_window(sbbf_server_t* s, bool* launched) {
+  SBBF_TRACE_NAMED("sbbf_server_window");
   *launched = false;
   int slot = -1;
   for (size_t i = 0; i < s->slots.size(); ++i)

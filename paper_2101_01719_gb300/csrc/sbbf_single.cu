@@ -231,12 +231,14 @@ sbbf_status sbbf_device_words(const sbbf_t* f, uint32_t** d_words, size_t* bytes
 }
 
 sbbf_status sbbf_clear(sbbf_t* f, sbbf_stream_t stream) {
+  SBBF_TRACE();
   if (!f || !on_device(f)) return SBBF_EINVAL;
   return launch_clear(f->words, filter_words(f), stream);
 }
 
 sbbf_status sbbf_insert_hashes(sbbf_t* f, const uint64_t* d_hashes, size_t n,
                                sbbf_stream_t stream) {
+  SBBF_TRACE();
   if (!f || !on_device(f)) return SBBF_EINVAL;
   if (n == 0) return SBBF_OK;
   if (!d_hashes || (reinterpret_cast<uintptr_t>(d_hashes) & 7)) return SBBF_EINVAL;
@@ -260,6 +262,7 @@ sbbf_status sbbf_set_partitioning(sbbf_t* f, int mode) {
 
 sbbf_status sbbf_find_hashes(const sbbf_t* f, const uint64_t* d_hashes, size_t n,
                              uint32_t* d_out_bits, sbbf_stream_t stream) {
+  SBBF_TRACE();
   if (!f || !on_device(f)) return SBBF_EINVAL;
   if (n == 0) return SBBF_OK;
   if (!d_hashes || !d_out_bits || (reinterpret_cast<uintptr_t>(d_hashes) & 7) ||
@@ -278,6 +281,7 @@ sbbf_status sbbf_find_hashes(const sbbf_t* f, const uint64_t* d_hashes, size_t n
 }
 
 sbbf_status sbbf_union(sbbf_t* dst, const sbbf_t* src, sbbf_stream_t stream) {
+  SBBF_TRACE();
   if (!dst || !src || dst->num_blocks != src->num_blocks || dst->lanes != src->lanes)
     return SBBF_EINVAL;
   if (!on_device(dst) || !on_device(src)) return SBBF_EINVAL;
@@ -287,6 +291,7 @@ sbbf_status sbbf_union(sbbf_t* dst, const sbbf_t* src, sbbf_stream_t stream) {
 
 sbbf_status sbbf_copy_to_host(const sbbf_t* f, uint32_t* h_words, size_t bytes,
                               sbbf_stream_t stream) {
+  SBBF_TRACE();
   if (!f || !h_words) return SBBF_EINVAL;
   const size_t need = filter_bytes(f);
   if (bytes < need) return SBBF_EINVAL;
