@@ -24,6 +24,18 @@ struct TraceRange {
 #define SBBF_TRACE() ::sbbf::TraceRange sbbf_trace_range_(__func__)
 #define SBBF_TRACE_NAMED(name) ::sbbf::TraceRange sbbf_trace_range_(name)
 
+// Runs an entry point's body and maps any C++ exception from the host-side
+// bookkeeping (container growth, thread creation) to SBBF_ENOMEM: nothing
+// throws across the C ABI.
+template <class F>
+sbbf_status guarded(F&& body) noexcept {
+  try {
+    return body();
+  } catch (...) {
+    return SBBF_ENOMEM;
+  }
+}
+
 // Records a failing CUDA call for sbbf_last_cuda_error() and maps it.
 sbbf_status record_cuda(cudaError_t e);
 

@@ -46,7 +46,10 @@ inline int cached_occupancy(const void* func, int threads) {
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, func, threads, 0) != cudaSuccess || n < 1)
     n = 1;
-  cache[key] = n;
+  try {
+    cache[key] = n;
+  } catch (...) {  // out of host memory: answer without caching
+  }
   return n;
 }
 

@@ -199,46 +199,48 @@ sbbf_status count_mismatch(const uint32_t* a, const uint32_t* b, uint64_t n,
 extern "C" {
 
 sbbf_status sbbf_multi_create(const uint32_t* h_num_blocks, uint32_t n_filters, sbbf_multi_t** out) {
-  if (!out || !h_num_blocks || n_filters == 0) return SBBF_EINVAL;
-  *out = nullptr;
-  uint64_t total = 0;
-  for (uint32_t t = 0; t < n_filters; ++t) {
-    if (h_num_blocks[t] == 0) return SBBF_EINVAL;
-    total += h_num_blocks[t];
-  }
-  sbbf_multi_t* m = new (std::nothrow) sbbf_multi_t();
-  if (!m) return SBBF_ENOMEM;
-  m->n_filters = n_filters;
-  m->total_blocks = total;
-  m->device = current_device();
-  m->tune_find_seg = m->tune_find_tag = kDefaultFind;
-  m->tune_insert_seg = m->tune_insert_tag = kDefaultInsert;
-  m->h_dir.resize(n_filters);
-  uint64_t base = 0;
-  for (uint32_t t = 0; t < n_filters; ++t) {
-    m->h_dir[t] = FilterRef{base, h_num_blocks[t], 0};
-    base += h_num_blocks[t];
-  }
-  cudaError_t e = cudaMalloc(&m->words, total * 32);
-  if (e == cudaSuccess) e = cudaMalloc(&m->d_dir, sizeof(FilterRef) * n_filters);
-  if (e == cudaSuccess) e = cudaMalloc(&m->d_invalid, sizeof(unsigned long long));
-  if (e == cudaSuccess) e = cudaMalloc(&m->d_tiles, 2 * sizeof(unsigned long long));
-  if (e == cudaSuccess)
-    e = cudaMemcpy(m->d_dir, m->h_dir.data(), sizeof(FilterRef) * n_filters,
-                   cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemset(m->d_invalid, 0, sizeof(unsigned long long));
-  sbbf_status st = e == cudaSuccess ? SBBF_OK : record_cuda(e);
-  if (st == SBBF_OK) st = launch_clear(m->words, total * 8, nullptr);
-  if (st == SBBF_OK) {
-    e = cudaStreamSynchronize(nullptr);
-    if (e != cudaSuccess) st = record_cuda(e);
-  }
-  if (st != SBBF_OK) {
-    sbbf_multi_destroy(m);
-    return st;
-  }
-  *out = m;
-  return SBBF_OK;
+  return guarded([&]() -> sbbf_status {
+    if (!out || !h_num_blocks || n_filters == 0) return SBBF_EINVAL;
+    *out = nullptr;
+    uint64_t total = 0;
+    for (uint32_t t = 0; t < n_filters; ++t) {
+      if (h_num_blocks[t] == 0) return SBBF_EINVAL;
+      total += h_num_blocks[t];
+    }
+    sbbf_multi_t* m = new (std::nothrow) sbbf_multi_t();
+    if (!m) return SBBF_ENOMEM;
+    m->n_filters = n_filters;
+    m->total_blocks = total;
+    m->device = current_device();
+    m->tune_find_seg = m->tune_find_tag = kDefaultFind;
+    m->tune_insert_seg = m->tune_insert_tag = kDefaultInsert;
+    m->h_dir.resize(n_filters);
+    uint64_t base = 0;
+    for (uint32_t t = 0; t < n_filters; ++t) {
+      m->h_dir[t] = FilterRef{base, h_num_blocks[t], 0};
+      base += h_num_blocks[t];
+    }
+    cudaError_t e = cudaMalloc(&m->words, total * 32);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_dir, sizeof(FilterRef) * n_filters);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_invalid, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_tiles, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(m->d_dir, m->h_dir.data(), sizeof(FilterRef) * n_filters,
+                     cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(m->d_invalid, 0, sizeof(unsigned long long));
+    sbbf_status st = e == cudaSuccess ? SBBF_OK : record_cuda(e);
+    if (st == SBBF_OK) st = launch_clear(m->words, total * 8, nullptr);
+    if (st == SBBF_OK) {
+      e = cudaStreamSynchronize(nullptr);
+      if (e != cudaSuccess) st = record_cuda(e);
+    }
+    if (st != SBBF_OK) {
+      sbbf_multi_destroy(m);
+      return st;
+    }
+    *out = m;
+    return SBBF_OK;
+  });
 }
 
 sbbf_status sbbf_multi_destroy(sbbf_multi_t* m) {
@@ -288,88 +290,100 @@ sbbf_status sbbf_multi_copy_to_host(const sbbf_multi_t* m, uint32_t* h_words, si
 
 sbbf_status sbbf_multi_insert(sbbf_multi_t* m, const uint64_t* d_hashes, const uint32_t* d_ids,
                               size_t n, sbbf_stream_t stream) {
-  SBBF_TRACE();
-  if (!on_device(m)) return SBBF_EINVAL;
-  if (n == 0) return SBBF_OK;
-  if (!d_hashes || !d_ids || (reinterpret_cast<uintptr_t>(d_hashes) & 7) ||
-      (reinterpret_cast<uintptr_t>(d_ids) & 3))
-    return SBBF_EINVAL;
-  return launch_insert_t(m->tune_insert_tag, m->words, tag_resolver(m, d_ids), d_hashes, n, stream,
-                         m->d_tiles);
+  return guarded([&]() -> sbbf_status {
+    SBBF_TRACE();
+    if (!on_device(m)) return SBBF_EINVAL;
+    if (n == 0) return SBBF_OK;
+    if (!d_hashes || !d_ids || (reinterpret_cast<uintptr_t>(d_hashes) & 7) ||
+        (reinterpret_cast<uintptr_t>(d_ids) & 3))
+      return SBBF_EINVAL;
+    return launch_insert_t(m->tune_insert_tag, m->words, tag_resolver(m, d_ids), d_hashes, n, stream,
+                           m->d_tiles);
+  });
 }
 
 sbbf_status sbbf_multi_find(const sbbf_multi_t* m, const uint64_t* d_hashes, const uint32_t* d_ids,
                             size_t n, uint32_t* d_out_bits, sbbf_stream_t stream) {
-  SBBF_TRACE();
-  if (!on_device(m)) return SBBF_EINVAL;
-  if (n == 0) return SBBF_OK;
-  if (!d_hashes || !d_ids || !d_out_bits || (reinterpret_cast<uintptr_t>(d_hashes) & 7) ||
-      (reinterpret_cast<uintptr_t>(d_ids) & 3) || (reinterpret_cast<uintptr_t>(d_out_bits) & 3))
-    return SBBF_EINVAL;
-  return launch_find_t(m->tune_find_tag, m->words, tag_resolver(m, d_ids), d_hashes, n,
-                       d_out_bits, stream, m->d_tiles + 1);
+  return guarded([&]() -> sbbf_status {
+    SBBF_TRACE();
+    if (!on_device(m)) return SBBF_EINVAL;
+    if (n == 0) return SBBF_OK;
+    if (!d_hashes || !d_ids || !d_out_bits || (reinterpret_cast<uintptr_t>(d_hashes) & 7) ||
+        (reinterpret_cast<uintptr_t>(d_ids) & 3) || (reinterpret_cast<uintptr_t>(d_out_bits) & 3))
+      return SBBF_EINVAL;
+    return launch_find_t(m->tune_find_tag, m->words, tag_resolver(m, d_ids), d_hashes, n,
+                         d_out_bits, stream, m->d_tiles + 1);
+  });
 }
 
 sbbf_status sbbf_multi_insert_segments(sbbf_multi_t* m, const uint64_t* d_hashes,
                                        const uint64_t* d_offsets, size_t n,
                                        sbbf_stream_t stream) {
-  SBBF_TRACE();
-  if (!on_device(m)) return SBBF_EINVAL;
-  if (n == 0) return SBBF_OK;
-  if (!d_hashes || !d_offsets || (reinterpret_cast<uintptr_t>(d_hashes) & 7) ||
-      (reinterpret_cast<uintptr_t>(d_offsets) & 7))
-    return SBBF_EINVAL;
-  return launch_insert_t(m->tune_insert_seg, m->words, seg_resolver(m, d_offsets), d_hashes, n,
-                         stream, m->d_tiles);
+  return guarded([&]() -> sbbf_status {
+    SBBF_TRACE();
+    if (!on_device(m)) return SBBF_EINVAL;
+    if (n == 0) return SBBF_OK;
+    if (!d_hashes || !d_offsets || (reinterpret_cast<uintptr_t>(d_hashes) & 7) ||
+        (reinterpret_cast<uintptr_t>(d_offsets) & 7))
+      return SBBF_EINVAL;
+    return launch_insert_t(m->tune_insert_seg, m->words, seg_resolver(m, d_offsets), d_hashes, n,
+                           stream, m->d_tiles);
+  });
 }
 
 sbbf_status sbbf_multi_find_segments(const sbbf_multi_t* m, const uint64_t* d_hashes,
                                      const uint64_t* d_offsets, size_t n, uint32_t* d_out_bits,
                                      sbbf_stream_t stream) {
-  SBBF_TRACE();
-  if (!on_device(m)) return SBBF_EINVAL;
-  if (n == 0) return SBBF_OK;
-  if (!d_hashes || !d_offsets || !d_out_bits || (reinterpret_cast<uintptr_t>(d_hashes) & 7) ||
-      (reinterpret_cast<uintptr_t>(d_offsets) & 7) || (reinterpret_cast<uintptr_t>(d_out_bits) & 3))
-    return SBBF_EINVAL;
-  return launch_find_t(m->tune_find_seg, m->words, seg_resolver(m, d_offsets), d_hashes, n,
-                       d_out_bits, stream, m->d_tiles + 1);
+  return guarded([&]() -> sbbf_status {
+    SBBF_TRACE();
+    if (!on_device(m)) return SBBF_EINVAL;
+    if (n == 0) return SBBF_OK;
+    if (!d_hashes || !d_offsets || !d_out_bits || (reinterpret_cast<uintptr_t>(d_hashes) & 7) ||
+        (reinterpret_cast<uintptr_t>(d_offsets) & 7) || (reinterpret_cast<uintptr_t>(d_out_bits) & 3))
+      return SBBF_EINVAL;
+    return launch_find_t(m->tune_find_seg, m->words, seg_resolver(m, d_offsets), d_hashes, n,
+                         d_out_bits, stream, m->d_tiles + 1);
+  });
 }
 
 sbbf_status sbbf_multi_insert_each(sbbf_multi_t* m, const uint64_t* d_hashes,
                                    const uint64_t* h_offsets, sbbf_stream_t stream) {
-  SBBF_TRACE();
-  if (!on_device(m) || !h_offsets || !d_hashes) return SBBF_EINVAL;
-  for (uint32_t t = 0; t < m->n_filters; ++t) {
-    if (h_offsets[t + 1] < h_offsets[t]) return SBBF_EINVAL;
-    const uint64_t cnt = h_offsets[t + 1] - h_offsets[t];
-    if (cnt == 0) continue;
-    sbbf_status st = launch_insert_t(kDefaultInsert, m->words + 8 * m->h_dir[t].base,
-                                     OneFilter{m->h_dir[t].num_blocks}, d_hashes + h_offsets[t],
-                                     cnt, stream);
-    if (st != SBBF_OK) return st;
-  }
-  return SBBF_OK;
+  return guarded([&]() -> sbbf_status {
+    SBBF_TRACE();
+    if (!on_device(m) || !h_offsets || !d_hashes) return SBBF_EINVAL;
+    for (uint32_t t = 0; t < m->n_filters; ++t) {
+      if (h_offsets[t + 1] < h_offsets[t]) return SBBF_EINVAL;
+      const uint64_t cnt = h_offsets[t + 1] - h_offsets[t];
+      if (cnt == 0) continue;
+      sbbf_status st = launch_insert_t(kDefaultInsert, m->words + 8 * m->h_dir[t].base,
+                                       OneFilter{m->h_dir[t].num_blocks}, d_hashes + h_offsets[t],
+                                       cnt, stream);
+      if (st != SBBF_OK) return st;
+    }
+    return SBBF_OK;
+  });
 }
 
 sbbf_status sbbf_multi_find_each(const sbbf_multi_t* m, const uint64_t* d_hashes,
                                  const uint64_t* h_offsets, uint32_t* d_out_bits,
                                  sbbf_stream_t stream) {
-  SBBF_TRACE();
-  if (!on_device(m) || !h_offsets || !d_hashes || !d_out_bits) return SBBF_EINVAL;
-  for (uint32_t t = 0; t < m->n_filters; ++t) {
-    if (h_offsets[t + 1] < h_offsets[t]) return SBBF_EINVAL;
-    const uint64_t cnt = h_offsets[t + 1] - h_offsets[t];
-    if (cnt == 0) continue;
-    if (h_offsets[t] % 32) return SBBF_EINVAL;  // each filter's answers start a fresh word
-    Tuning tf = kDefaultFind;
-    tf.l1_bypass = static_cast<uint64_t>(m->h_dir[t].num_blocks) * 32 > kL1BypassBytes;
-    sbbf_status st = launch_find_t(tf, m->words + 8 * m->h_dir[t].base,
-                                   OneFilter{m->h_dir[t].num_blocks}, d_hashes + h_offsets[t], cnt,
-                                   d_out_bits + h_offsets[t] / 32, stream);
-    if (st != SBBF_OK) return st;
-  }
-  return SBBF_OK;
+  return guarded([&]() -> sbbf_status {
+    SBBF_TRACE();
+    if (!on_device(m) || !h_offsets || !d_hashes || !d_out_bits) return SBBF_EINVAL;
+    for (uint32_t t = 0; t < m->n_filters; ++t) {
+      if (h_offsets[t + 1] < h_offsets[t]) return SBBF_EINVAL;
+      const uint64_t cnt = h_offsets[t + 1] - h_offsets[t];
+      if (cnt == 0) continue;
+      if (h_offsets[t] % 32) return SBBF_EINVAL;  // each filter's answers start a fresh word
+      Tuning tf = kDefaultFind;
+      tf.l1_bypass = static_cast<uint64_t>(m->h_dir[t].num_blocks) * 32 > kL1BypassBytes;
+      sbbf_status st = launch_find_t(tf, m->words + 8 * m->h_dir[t].base,
+                                     OneFilter{m->h_dir[t].num_blocks}, d_hashes + h_offsets[t], cnt,
+                                     d_out_bits + h_offsets[t] / 32, stream);
+      if (st != SBBF_OK) return st;
+    }
+    return SBBF_OK;
+  });
 }
 
 sbbf_status sbbf_multi_invalid_count(sbbf_multi_t* m, uint64_t* count, sbbf_stream_t stream) {
@@ -399,187 +413,193 @@ sbbf_status sbbf_multi_get_tuning(const sbbf_multi_t* m, int op, int form, int* 
 
 sbbf_status sbbf_multi_set_tuning(sbbf_multi_t* m, int op, int form, int threads, int lanes,
                                   int unroll, int l1_bypass) {
-  const Tuning t{threads, lanes, unroll, l1_bypass};
-  if (!m || !tuning_valid(t) || (op != SBBF_OP_INSERT && op != SBBF_OP_FIND) ||
-      (form != SBBF_FORM_SEGMENTS && form != SBBF_FORM_TAGGED))
-    return SBBF_EINVAL;
-  Tuning& dst = op == SBBF_OP_INSERT
-                    ? (form == SBBF_FORM_SEGMENTS ? m->tune_insert_seg : m->tune_insert_tag)
-                    : (form == SBBF_FORM_SEGMENTS ? m->tune_find_seg : m->tune_find_tag);
-  dst = t;
-  return SBBF_OK;
+  return guarded([&]() -> sbbf_status {
+    const Tuning t{threads, lanes, unroll, l1_bypass};
+    if (!m || !tuning_valid(t) || (op != SBBF_OP_INSERT && op != SBBF_OP_FIND) ||
+        (form != SBBF_FORM_SEGMENTS && form != SBBF_FORM_TAGGED))
+      return SBBF_EINVAL;
+    Tuning& dst = op == SBBF_OP_INSERT
+                      ? (form == SBBF_FORM_SEGMENTS ? m->tune_insert_seg : m->tune_insert_tag)
+                      : (form == SBBF_FORM_SEGMENTS ? m->tune_find_seg : m->tune_find_tag);
+    dst = t;
+    return SBBF_OK;
+  });
 }
 
 sbbf_status sbbf_multi_tune(sbbf_multi_t* m, int op, int form, const uint64_t* d_hashes,
                             const void* d_offsets_or_ids, size_t n, sbbf_stream_t stream,
                             float* best_ms) {
-  SBBF_TRACE();
-  if (!on_device(m) || !d_hashes || !d_offsets_or_ids || n == 0) return SBBF_EINVAL;
-  if ((op != SBBF_OP_INSERT && op != SBBF_OP_FIND) ||
-      (form != SBBF_FORM_SEGMENTS && form != SBBF_FORM_TAGGED))
-    return SBBF_EINVAL;
-  const uint64_t n_s = std::min<uint64_t>(n, 1ull << 24);  // tuning sample: a prefix
-  const CacheKey key{gpu_name(), op, form, ilog2(m->total_blocks), ilog2(n_s)};
-  Tuning& dst = op == SBBF_OP_INSERT
-                    ? (form == SBBF_FORM_SEGMENTS ? m->tune_insert_seg : m->tune_insert_tag)
-                    : (form == SBBF_FORM_SEGMENTS ? m->tune_find_seg : m->tune_find_tag);
-  {
-    std::lock_guard<std::mutex> lock(g_tune_mu);
-    auto it = g_tune_cache.find(key);
-    if (it != g_tune_cache.end()) {
-      dst = it->second;
-      if (best_ms) *best_ms = -1.0f;
-      return SBBF_OK;
+  return guarded([&]() -> sbbf_status {
+    SBBF_TRACE();
+    if (!on_device(m) || !d_hashes || !d_offsets_or_ids || n == 0) return SBBF_EINVAL;
+    if ((op != SBBF_OP_INSERT && op != SBBF_OP_FIND) ||
+        (form != SBBF_FORM_SEGMENTS && form != SBBF_FORM_TAGGED))
+      return SBBF_EINVAL;
+    const uint64_t n_s = std::min<uint64_t>(n, 1ull << 24);  // tuning sample: a prefix
+    const CacheKey key{gpu_name(), op, form, ilog2(m->total_blocks), ilog2(n_s)};
+    Tuning& dst = op == SBBF_OP_INSERT
+                      ? (form == SBBF_FORM_SEGMENTS ? m->tune_insert_seg : m->tune_insert_tag)
+                      : (form == SBBF_FORM_SEGMENTS ? m->tune_find_seg : m->tune_find_tag);
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) {
+        dst = it->second;
+        if (best_ms) *best_ms = -1.0f;
+        return SBBF_OK;
+      }
     }
-  }
-  cudaStream_t s = stream;
-  DeviceBuf cnt, tiles;
-  SBBF_CUDA(cnt.alloc(sizeof(unsigned long long)));
-  SBBF_CUDA(tiles.alloc(sizeof(unsigned long long)));
-  unsigned long long* tile_ctr = tiles.as<unsigned long long>();
+    cudaStream_t s = stream;
+    DeviceBuf cnt, tiles;
+    SBBF_CUDA(cnt.alloc(sizeof(unsigned long long)));
+    SBBF_CUDA(tiles.alloc(sizeof(unsigned long long)));
+    unsigned long long* tile_ctr = tiles.as<unsigned long long>();
 
-  // Sample offsets (segment form): the prefix of n_s keys, clipped.
-  DeviceBuf d_off_s;
-  const uint64_t* off_s = nullptr;
-  uint64_t blocks_touched = m->total_blocks;
-  if (form == SBBF_FORM_SEGMENTS) {
-    std::vector<uint64_t> h_off(m->n_filters + 1);
-    SBBF_CUDA(cudaMemcpyAsync(h_off.data(), d_offsets_or_ids, 8 * h_off.size(),
-                              cudaMemcpyDeviceToHost, s));
-    SBBF_CUDA(cudaStreamSynchronize(s));
-    uint32_t last = 0;
-    for (auto& o : h_off) o = std::min<uint64_t>(o, n_s);
-    for (uint32_t t = 0; t < m->n_filters; ++t)
-      if (h_off[t] < n_s) last = t;
-    blocks_touched = m->h_dir[last].base + m->h_dir[last].num_blocks;
-    SBBF_CUDA(d_off_s.alloc(8 * h_off.size()));
-    SBBF_CUDA(cudaMemcpyAsync(d_off_s.p, h_off.data(), 8 * h_off.size(), cudaMemcpyHostToDevice, s));
-    SBBF_CUDA(cudaStreamSynchronize(s));
-    off_s = d_off_s.as<uint64_t>();
-  }
-  const uint32_t* ids = static_cast<const uint32_t*>(d_offsets_or_ids);
-  Tuning best = dst;
-  sbbf_status st;
-  if (op == SBBF_OP_FIND) {
-    const uint64_t words = (n_s + 31) / 32;
-    DeviceBuf ref, got;
-    SBBF_CUDA(ref.alloc(4 * words));
-    SBBF_CUDA(got.alloc(4 * words));
-    auto run_into = [&](const Tuning& t, uint32_t* out) -> sbbf_status {
-      return form == SBBF_FORM_SEGMENTS
-                 ? launch_find_t(t, m->words, seg_resolver(m, off_s), d_hashes, n_s, out, s,
-                                 tile_ctr)
-                 : launch_find_t(t, m->words, tag_resolver(m, ids), d_hashes, n_s, out, s,
-                                 tile_ctr);
-    };
-    st = run_into(kDefaultFind, ref.as<uint32_t>());
-    if (st != SBBF_OK) return st;
-    st = search(
-        op, kDefaultFind, s, [&](const Tuning& t) { return run_into(t, got.as<uint32_t>()); },
-        [&]() { return cudaSuccess; },
-        [&](uint64_t* bad) {
-          return count_mismatch(ref.as<uint32_t>(), got.as<uint32_t>(), words,
-                                cnt.as<unsigned long long>(), s, bad);
-        },
-        &best, best_ms);
-  } else {
-    // Inserts run into scratch copies of the touched part of the arena.
-    const uint64_t n_words = blocks_touched * 8;
-    DeviceBuf ref, scratch;
-    if (ref.alloc(4 * n_words) != cudaSuccess || scratch.alloc(4 * n_words) != cudaSuccess) {
-      cudaGetLastError();
-      return SBBF_ENOMEM;
+    // Sample offsets (segment form): the prefix of n_s keys, clipped.
+    DeviceBuf d_off_s;
+    const uint64_t* off_s = nullptr;
+    uint64_t blocks_touched = m->total_blocks;
+    if (form == SBBF_FORM_SEGMENTS) {
+      std::vector<uint64_t> h_off(m->n_filters + 1);
+      SBBF_CUDA(cudaMemcpyAsync(h_off.data(), d_offsets_or_ids, 8 * h_off.size(),
+                                cudaMemcpyDeviceToHost, s));
+      SBBF_CUDA(cudaStreamSynchronize(s));
+      uint32_t last = 0;
+      for (auto& o : h_off) o = std::min<uint64_t>(o, n_s);
+      for (uint32_t t = 0; t < m->n_filters; ++t)
+        if (h_off[t] < n_s) last = t;
+      blocks_touched = m->h_dir[last].base + m->h_dir[last].num_blocks;
+      SBBF_CUDA(d_off_s.alloc(8 * h_off.size()));
+      SBBF_CUDA(cudaMemcpyAsync(d_off_s.p, h_off.data(), 8 * h_off.size(), cudaMemcpyHostToDevice, s));
+      SBBF_CUDA(cudaStreamSynchronize(s));
+      off_s = d_off_s.as<uint64_t>();
     }
-    auto run_into = [&](const Tuning& t, uint32_t* arena) -> sbbf_status {
-      return form == SBBF_FORM_SEGMENTS
-                 ? launch_insert_t(t, arena, seg_resolver(m, off_s), d_hashes, n_s, s, tile_ctr)
-                 : launch_insert_t(t, arena, tag_resolver(m, ids), d_hashes, n_s, s, tile_ctr);
-    };
-    st = launch_clear(ref.as<uint32_t>(), n_words, s);
-    if (st == SBBF_OK) st = run_into(kDefaultInsert, ref.as<uint32_t>());
+    const uint32_t* ids = static_cast<const uint32_t*>(d_offsets_or_ids);
+    Tuning best = dst;
+    sbbf_status st;
+    if (op == SBBF_OP_FIND) {
+      const uint64_t words = (n_s + 31) / 32;
+      DeviceBuf ref, got;
+      SBBF_CUDA(ref.alloc(4 * words));
+      SBBF_CUDA(got.alloc(4 * words));
+      auto run_into = [&](const Tuning& t, uint32_t* out) -> sbbf_status {
+        return form == SBBF_FORM_SEGMENTS
+                   ? launch_find_t(t, m->words, seg_resolver(m, off_s), d_hashes, n_s, out, s,
+                                   tile_ctr)
+                   : launch_find_t(t, m->words, tag_resolver(m, ids), d_hashes, n_s, out, s,
+                                   tile_ctr);
+      };
+      st = run_into(kDefaultFind, ref.as<uint32_t>());
+      if (st != SBBF_OK) return st;
+      st = search(
+          op, kDefaultFind, s, [&](const Tuning& t) { return run_into(t, got.as<uint32_t>()); },
+          [&]() { return cudaSuccess; },
+          [&](uint64_t* bad) {
+            return count_mismatch(ref.as<uint32_t>(), got.as<uint32_t>(), words,
+                                  cnt.as<unsigned long long>(), s, bad);
+          },
+          &best, best_ms);
+    } else {
+      // Inserts run into scratch copies of the touched part of the arena.
+      const uint64_t n_words = blocks_touched * 8;
+      DeviceBuf ref, scratch;
+      if (ref.alloc(4 * n_words) != cudaSuccess || scratch.alloc(4 * n_words) != cudaSuccess) {
+        cudaGetLastError();
+        return SBBF_ENOMEM;
+      }
+      auto run_into = [&](const Tuning& t, uint32_t* arena) -> sbbf_status {
+        return form == SBBF_FORM_SEGMENTS
+                   ? launch_insert_t(t, arena, seg_resolver(m, off_s), d_hashes, n_s, s, tile_ctr)
+                   : launch_insert_t(t, arena, tag_resolver(m, ids), d_hashes, n_s, s, tile_ctr);
+      };
+      st = launch_clear(ref.as<uint32_t>(), n_words, s);
+      if (st == SBBF_OK) st = run_into(kDefaultInsert, ref.as<uint32_t>());
+      if (st != SBBF_OK) return st;
+      st = search(
+          op, kDefaultInsert, s, [&](const Tuning& t) { return run_into(t, scratch.as<uint32_t>()); },
+          [&]() {
+            return launch_clear(scratch.as<uint32_t>(), n_words, s) == SBBF_OK ? cudaSuccess
+                                                                               : cudaErrorUnknown;
+          },
+          [&](uint64_t* bad) {
+            return count_mismatch(ref.as<uint32_t>(), scratch.as<uint32_t>(), n_words,
+                                  cnt.as<unsigned long long>(), s, bad);
+          },
+          &best, best_ms);
+      // the tagged sample also counted its invalid ids once per run: reset
+      if (form == SBBF_FORM_TAGGED)
+        SBBF_CUDA(cudaMemsetAsync(m->d_invalid, 0, sizeof(unsigned long long), s));
+    }
     if (st != SBBF_OK) return st;
-    st = search(
-        op, kDefaultInsert, s, [&](const Tuning& t) { return run_into(t, scratch.as<uint32_t>()); },
-        [&]() {
-          return launch_clear(scratch.as<uint32_t>(), n_words, s) == SBBF_OK ? cudaSuccess
-                                                                             : cudaErrorUnknown;
-        },
-        [&](uint64_t* bad) {
-          return count_mismatch(ref.as<uint32_t>(), scratch.as<uint32_t>(), n_words,
-                                cnt.as<unsigned long long>(), s, bad);
-        },
-        &best, best_ms);
-    // the tagged sample also counted its invalid ids once per run: reset
-    if (form == SBBF_FORM_TAGGED)
+    if (op == SBBF_OP_FIND && form == SBBF_FORM_TAGGED)
       SBBF_CUDA(cudaMemsetAsync(m->d_invalid, 0, sizeof(unsigned long long), s));
-  }
-  if (st != SBBF_OK) return st;
-  if (op == SBBF_OP_FIND && form == SBBF_FORM_TAGGED)
-    SBBF_CUDA(cudaMemsetAsync(m->d_invalid, 0, sizeof(unsigned long long), s));
-  SBBF_CUDA(cudaStreamSynchronize(s));
-  dst = best;
-  std::lock_guard<std::mutex> lock(g_tune_mu);
-  g_tune_cache[key] = best;
-  return SBBF_OK;
+    SBBF_CUDA(cudaStreamSynchronize(s));
+    dst = best;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = best;
+    return SBBF_OK;
+  });
 }
 
 // ---- CUDA graph: batched inserts then lookups, one graph launch ---------------
 
 sbbf_status sbbf_multi_graph_create(sbbf_multi_t* m, sbbf_multi_graph_t** out) {
-  if (!on_device(m) || !out) return SBBF_EINVAL;
-  *out = nullptr;
-  sbbf_multi_graph_t* g = new (std::nothrow) sbbf_multi_graph_t();
-  if (!g) return SBBF_ENOMEM;
-  g->m = m;
-  g->ti = m->tune_insert_seg;
-  g->tf = m->tune_find_seg;
-  auto fail = [&](cudaError_t e) {
-    if (g->exec) cudaGraphExecDestroy(g->exec);
-    if (g->graph) cudaGraphDestroy(g->graph);
-    delete g;
-    return record_cuda(e);
-  };
-  cudaError_t e = cudaGraphCreate(&g->graph, 0);
-  if (e != cudaSuccess) return fail(e);
-  // Both work counters are zeroed by a memset node ahead of the two kernels.
-  cudaMemsetParams mp = {};
-  mp.dst = m->d_tiles;
-  mp.value = 0;
-  mp.elementSize = 4;
-  mp.width = 4;  // 16 bytes: both 64-bit counters
-  mp.height = 1;
-  mp.pitch = 0;
-  e = cudaGraphAddMemsetNode(&g->memset_node, g->graph, nullptr, 0, &mp);
-  if (e != cudaSuccess) return fail(e);
-  // Placeholder arguments; every launch sets the real ones.
-  Segments r = seg_resolver(m, nullptr);
-  uint32_t* words = m->words;
-  HashInput h(nullptr);
-  uint64_t n = 0;
-  uint32_t* o = nullptr;
-  unsigned long long* ti = m->d_tiles;
-  unsigned long long* tf = m->d_tiles + 1;
-  void* iargs[] = {&words, &r, &h, &n, &ti};
-  void* fargs[] = {&words, &r, &h, &n, &o, &tf};
-  cudaKernelNodeParams ip = {};
-  ip.func = reinterpret_cast<void*>(g->ti.lanes == 8 ? insert_kernel<Segments, true>
-                                                     : insert_kernel<Segments, false>);
-  ip.gridDim = dim3(1);
-  ip.blockDim = dim3(g->ti.threads);
-  ip.kernelParams = iargs;
-  e = cudaGraphAddKernelNode(&g->insert_node, g->graph, &g->memset_node, 1, &ip);
-  if (e != cudaSuccess) return fail(e);
-  cudaKernelNodeParams fp = {};
-  fp.func = reinterpret_cast<void*>(find_kernel_for<Segments>(g->tf));
-  fp.gridDim = dim3(1);
-  fp.blockDim = dim3(g->tf.threads);
-  fp.kernelParams = fargs;
-  e = cudaGraphAddKernelNode(&g->find_node, g->graph, &g->insert_node, 1, &fp);
-  if (e != cudaSuccess) return fail(e);
-  e = cudaGraphInstantiate(&g->exec, g->graph, 0);
-  if (e != cudaSuccess) return fail(e);
-  *out = g;
-  return SBBF_OK;
+  return guarded([&]() -> sbbf_status {
+    if (!on_device(m) || !out) return SBBF_EINVAL;
+    *out = nullptr;
+    sbbf_multi_graph_t* g = new (std::nothrow) sbbf_multi_graph_t();
+    if (!g) return SBBF_ENOMEM;
+    g->m = m;
+    g->ti = m->tune_insert_seg;
+    g->tf = m->tune_find_seg;
+    auto fail = [&](cudaError_t e) {
+      if (g->exec) cudaGraphExecDestroy(g->exec);
+      if (g->graph) cudaGraphDestroy(g->graph);
+      delete g;
+      return record_cuda(e);
+    };
+    cudaError_t e = cudaGraphCreate(&g->graph, 0);
+    if (e != cudaSuccess) return fail(e);
+    // Both work counters are zeroed by a memset node ahead of the two kernels.
+    cudaMemsetParams mp = {};
+    mp.dst = m->d_tiles;
+    mp.value = 0;
+    mp.elementSize = 4;
+    mp.width = 4;  // 16 bytes: both 64-bit counters
+    mp.height = 1;
+    mp.pitch = 0;
+    e = cudaGraphAddMemsetNode(&g->memset_node, g->graph, nullptr, 0, &mp);
+    if (e != cudaSuccess) return fail(e);
+    // Placeholder arguments; every launch sets the real ones.
+    Segments r = seg_resolver(m, nullptr);
+    uint32_t* words = m->words;
+    HashInput h(nullptr);
+    uint64_t n = 0;
+    uint32_t* o = nullptr;
+    unsigned long long* ti = m->d_tiles;
+    unsigned long long* tf = m->d_tiles + 1;
+    void* iargs[] = {&words, &r, &h, &n, &ti};
+    void* fargs[] = {&words, &r, &h, &n, &o, &tf};
+    cudaKernelNodeParams ip = {};
+    ip.func = reinterpret_cast<void*>(g->ti.lanes == 8 ? insert_kernel<Segments, true>
+                                                       : insert_kernel<Segments, false>);
+    ip.gridDim = dim3(1);
+    ip.blockDim = dim3(g->ti.threads);
+    ip.kernelParams = iargs;
+    e = cudaGraphAddKernelNode(&g->insert_node, g->graph, &g->memset_node, 1, &ip);
+    if (e != cudaSuccess) return fail(e);
+    cudaKernelNodeParams fp = {};
+    fp.func = reinterpret_cast<void*>(find_kernel_for<Segments>(g->tf));
+    fp.gridDim = dim3(1);
+    fp.blockDim = dim3(g->tf.threads);
+    fp.kernelParams = fargs;
+    e = cudaGraphAddKernelNode(&g->find_node, g->graph, &g->insert_node, 1, &fp);
+    if (e != cudaSuccess) return fail(e);
+    e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (e != cudaSuccess) return fail(e);
+    *out = g;
+    return SBBF_OK;
+  });
 }
 
 sbbf_status sbbf_multi_graph_destroy(sbbf_multi_graph_t* g) {
@@ -594,40 +614,42 @@ sbbf_status sbbf_multi_graph_launch(sbbf_multi_graph_t* g, const uint64_t* d_ins
                                     const uint64_t* d_ins_offsets, size_t n_ins,
                                     const uint64_t* d_q, const uint64_t* d_q_offsets, size_t n_q,
                                     uint32_t* d_out_bits, sbbf_stream_t stream) {
-  SBBF_TRACE();
-  if (!g || !on_device(g->m)) return SBBF_EINVAL;
-  if ((n_ins && (!d_ins || !d_ins_offsets)) || (n_q && (!d_q || !d_q_offsets || !d_out_bits)))
-    return SBBF_EINVAL;
-  if ((reinterpret_cast<uintptr_t>(d_ins) & 7) || (reinterpret_cast<uintptr_t>(d_q) & 7) ||
-      (reinterpret_cast<uintptr_t>(d_ins_offsets) & 7) ||
-      (reinterpret_cast<uintptr_t>(d_q_offsets) & 7) ||
-      (reinterpret_cast<uintptr_t>(d_out_bits) & 3))
-    return SBBF_EINVAL;
-  sbbf_multi_t* m = g->m;
-  Segments ri = seg_resolver(m, d_ins_offsets), rf = seg_resolver(m, d_q_offsets);
-  uint32_t* words = m->words;
-  HashInput hi(d_ins), hq(d_q);
-  uint64_t ni = n_ins, nq = n_q;
-  uint32_t* o = d_out_bits;
-  unsigned long long* ti = m->d_tiles;
-  unsigned long long* tf = m->d_tiles + 1;
-  void* iargs[] = {&words, &ri, &hi, &ni, &ti};
-  void* fargs[] = {&words, &rf, &hq, &nq, &o, &tf};
-  cudaKernelNodeParams ip = {}, fp = {};
-  SBBF_CUDA(cudaGraphKernelNodeGetParams(g->insert_node, &ip));
-  SBBF_CUDA(cudaGraphKernelNodeGetParams(g->find_node, &fp));
-  const int occ_i = cached_occupancy(ip.func, g->ti.threads);
-  // n == 0 launches one CTA whose loop body never runs.
-  ip.gridDim = dim3(grid_for((ni + 63) / 64, g->ti.threads / 32, occ_i));
-  fp.gridDim = dim3(find_grid(g->tf, nq, fp.func));
-  ip.kernelParams = iargs;
-  fp.kernelParams = fargs;
-  ip.extra = nullptr;
-  fp.extra = nullptr;
-  SBBF_CUDA(cudaGraphExecKernelNodeSetParams(g->exec, g->insert_node, &ip));
-  SBBF_CUDA(cudaGraphExecKernelNodeSetParams(g->exec, g->find_node, &fp));
-  SBBF_CUDA(cudaGraphLaunch(g->exec, stream));
-  return SBBF_OK;
+  return guarded([&]() -> sbbf_status {
+    SBBF_TRACE();
+    if (!g || !on_device(g->m)) return SBBF_EINVAL;
+    if ((n_ins && (!d_ins || !d_ins_offsets)) || (n_q && (!d_q || !d_q_offsets || !d_out_bits)))
+      return SBBF_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_ins) & 7) || (reinterpret_cast<uintptr_t>(d_q) & 7) ||
+        (reinterpret_cast<uintptr_t>(d_ins_offsets) & 7) ||
+        (reinterpret_cast<uintptr_t>(d_q_offsets) & 7) ||
+        (reinterpret_cast<uintptr_t>(d_out_bits) & 3))
+      return SBBF_EINVAL;
+    sbbf_multi_t* m = g->m;
+    Segments ri = seg_resolver(m, d_ins_offsets), rf = seg_resolver(m, d_q_offsets);
+    uint32_t* words = m->words;
+    HashInput hi(d_ins), hq(d_q);
+    uint64_t ni = n_ins, nq = n_q;
+    uint32_t* o = d_out_bits;
+    unsigned long long* ti = m->d_tiles;
+    unsigned long long* tf = m->d_tiles + 1;
+    void* iargs[] = {&words, &ri, &hi, &ni, &ti};
+    void* fargs[] = {&words, &rf, &hq, &nq, &o, &tf};
+    cudaKernelNodeParams ip = {}, fp = {};
+    SBBF_CUDA(cudaGraphKernelNodeGetParams(g->insert_node, &ip));
+    SBBF_CUDA(cudaGraphKernelNodeGetParams(g->find_node, &fp));
+    const int occ_i = cached_occupancy(ip.func, g->ti.threads);
+    // n == 0 launches one CTA whose loop body never runs.
+    ip.gridDim = dim3(grid_for((ni + 63) / 64, g->ti.threads / 32, occ_i));
+    fp.gridDim = dim3(find_grid(g->tf, nq, fp.func));
+    ip.kernelParams = iargs;
+    fp.kernelParams = fargs;
+    ip.extra = nullptr;
+    fp.extra = nullptr;
+    SBBF_CUDA(cudaGraphExecKernelNodeSetParams(g->exec, g->insert_node, &ip));
+    SBBF_CUDA(cudaGraphExecKernelNodeSetParams(g->exec, g->find_node, &fp));
+    SBBF_CUDA(cudaGraphLaunch(g->exec, stream));
+    return SBBF_OK;
+  });
 }
 
 }  // extern "C"

@@ -488,8 +488,8 @@ void worker_loop(sbbf_server_t* s) {
     bool launched = false;
     if (!s->paused && s->n_pending > 0 &&
         s->inflight.size() < s->cfg.max_inflight_windows && s->error == SBBF_OK) {
-      const sbbf_status rc = launch_window(s, &launched);
-      if (rc != SBBF_OK) s->error = rc;
+      const sbbf_status rc = guarded([&] { return launch_window(s, &launched); });
+      if (rc != SBBF_OK) s->error = rc;  // sticky: waiters return it
     }
     if (launched) {
       s->cv.notify_all();
@@ -566,7 +566,12 @@ sbbf_status sbbf_server_create(const sbbf_server_config_t* cfg, sbbf_server_t** 
     uint64_t keep = UINT64_MAX;
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
   }
-  s->worker = std::thread(worker_loop, s);
+  try {
+    s->worker = std::thread(worker_loop, s);
+  } catch (...) {
+    free_server(s);
+    return SBBF_ENOMEM;
+  }
   *out = s;
   return SBBF_OK;
 }
@@ -586,223 +591,256 @@ sbbf_status sbbf_server_destroy(sbbf_server_t* s) {
 }
 
 sbbf_status sbbf_server_add_filter(sbbf_server_t* s, uint32_t num_blocks, uint32_t* id) {
-  if (!s || !id || num_blocks == 0) return SBBF_EINVAL;
-  std::lock_guard<std::mutex> lk(s->mu);
-  FilterState f;
-  f.num_blocks = num_blocks;
-  s->filters.push_back(f);
-  s->queues.emplace_back();
-  *id = static_cast<uint32_t>(s->filters.size() - 1);
-  return SBBF_OK;
+  return guarded([&]() -> sbbf_status {
+    if (!s || !id || num_blocks == 0) return SBBF_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    FilterState f;
+    f.num_blocks = num_blocks;
+    s->filters.reserve(s->filters.size() + 1);
+    s->queues.reserve(s->queues.size() + 1);
+    s->filters.push_back(f);
+    s->queues.emplace_back();
+    *id = static_cast<uint32_t>(s->filters.size() - 1);
+    return SBBF_OK;
+  });
 }
 
 sbbf_status sbbf_server_submit(sbbf_server_t* s, const sbbf_request_t* r, uint64_t* ticket) {
-  if (!s || !r || !ticket) return SBBF_EINVAL;
-  if (r->op != SBBF_OP_INSERT && r->op != SBBF_OP_FIND) return SBBF_EINVAL;
-  if (r->n > 0 && (!r->d_hashes || (r->op == SBBF_OP_FIND && !r->d_out_bits))) return SBBF_EINVAL;
-  if ((reinterpret_cast<uintptr_t>(r->d_hashes) & 7) || (reinterpret_cast<uintptr_t>(r->d_out_bits) & 3))
-    return SBBF_EINVAL;
-  Pending p;
-  p.req = *r;
-  p.dev_bytes = 0;
-  p.t_submit = now_ns();
-  if (r->n && device_resident(r->d_hashes)) p.dev_bytes += 8 * r->n;
-  if (r->n && r->op == SBBF_OP_FIND && device_resident(r->d_out_bits)) p.dev_bytes += 4 * ((r->n + 31) / 32);
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
-    if (r->filter >= s->filters.size()) return SBBF_EINVAL;
-    if (s->error != SBBF_OK) return s->error;
-    if (s->n_pending >= s->cfg.max_pending_requests) return SBBF_EBUSY;
-    if (s->filters[r->filter].bytes() + p.dev_bytes > s->cfg.budget_bytes) return SBBF_EBUSY;
-    p.ticket = s->done_ns.size();
-    s->done_ns.push_back(r->n == 0 ? now_ns() : 0);
-    s->status.push_back(SBBF_OK);
-    if (r->n > 0) {
-      std::deque<Pending>& q = s->queues[r->filter];
-      if (q.empty()) s->heads.insert({p.ticket, r->filter});
-      q.push_back(p);
-      ++s->n_pending;
+  return guarded([&]() -> sbbf_status {
+    if (!s || !r || !ticket) return SBBF_EINVAL;
+    if (r->op != SBBF_OP_INSERT && r->op != SBBF_OP_FIND) return SBBF_EINVAL;
+    if (r->n > 0 && (!r->d_hashes || (r->op == SBBF_OP_FIND && !r->d_out_bits))) return SBBF_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(r->d_hashes) & 7) || (reinterpret_cast<uintptr_t>(r->d_out_bits) & 3))
+      return SBBF_EINVAL;
+    Pending p;
+    p.req = *r;
+    p.dev_bytes = 0;
+    p.t_submit = now_ns();
+    if (r->n && device_resident(r->d_hashes)) p.dev_bytes += 8 * r->n;
+    if (r->n && r->op == SBBF_OP_FIND && device_resident(r->d_out_bits)) p.dev_bytes += 4 * ((r->n + 31) / 32);
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (r->filter >= s->filters.size()) return SBBF_EINVAL;
+      if (s->error != SBBF_OK) return s->error;
+      if (s->n_pending >= s->cfg.max_pending_requests) return SBBF_EBUSY;
+      if (s->filters[r->filter].bytes() + p.dev_bytes > s->cfg.budget_bytes) return SBBF_EBUSY;
+      p.ticket = s->done_ns.size();
+      // every step that can throw comes before the first change of state
+      s->done_ns.reserve(p.ticket + 1);
+      s->status.reserve(p.ticket + 1);
+      if (r->n > 0) {
+        std::deque<Pending>& q = s->queues[r->filter];
+        const bool was_empty = q.empty();
+        q.push_back(p);
+        if (was_empty) {
+          try {
+            s->heads.insert({p.ticket, r->filter});
+          } catch (...) {
+            q.pop_back();
+            throw;
+          }
+        }
+        ++s->n_pending;
+      }
+      s->done_ns.push_back(r->n == 0 ? now_ns() : 0);
+      s->status.push_back(SBBF_OK);
+      *ticket = p.ticket;
     }
-    *ticket = p.ticket;
-  }
-  s->cv.notify_all();
-  return SBBF_OK;
+    s->cv.notify_all();
+    return SBBF_OK;
+  });
 }
 
 sbbf_status sbbf_server_poll(sbbf_server_t* s, uint64_t ticket, int* done) {
-  if (!s || !done) return SBBF_EINVAL;
-  std::lock_guard<std::mutex> lk(s->mu);
-  if (ticket >= s->done_ns.size()) return SBBF_EINVAL;
-  *done = s->done_ns[ticket] != 0;
-  return *done ? static_cast<sbbf_status>(s->status[ticket]) : SBBF_OK;
+  return guarded([&]() -> sbbf_status {
+    if (!s || !done) return SBBF_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (ticket >= s->done_ns.size()) return SBBF_EINVAL;
+    *done = s->done_ns[ticket] != 0;
+    return *done ? static_cast<sbbf_status>(s->status[ticket]) : SBBF_OK;
+  });
 }
 
 sbbf_status sbbf_server_wait(sbbf_server_t* s, uint64_t ticket, uint64_t timeout_ns) {
-  if (!s) return SBBF_EINVAL;
-  std::unique_lock<std::mutex> lk(s->mu);
-  if (ticket >= s->done_ns.size()) return SBBF_EINVAL;
-  return wait_ticket(s, lk, ticket, timeout_ns ? now_ns() + timeout_ns : 0);
+  return guarded([&]() -> sbbf_status {
+    if (!s) return SBBF_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (ticket >= s->done_ns.size()) return SBBF_EINVAL;
+    return wait_ticket(s, lk, ticket, timeout_ns ? now_ns() + timeout_ns : 0);
+  });
 }
 
 sbbf_status sbbf_server_drain(sbbf_server_t* s, uint64_t timeout_ns) {
-  if (!s) return SBBF_EINVAL;
-  const uint64_t deadline = timeout_ns ? now_ns() + timeout_ns : 0;
-  std::unique_lock<std::mutex> lk(s->mu);
-  while (s->n_pending > 0 || !s->inflight.empty()) {
-    if (s->error != SBBF_OK) return s->error;
-    if (deadline && now_ns() >= deadline) return SBBF_ETIMEOUT;
-    s->cv.wait_for(lk, std::chrono::microseconds(200));
-  }
-  return s->error;
+  return guarded([&]() -> sbbf_status {
+    if (!s) return SBBF_EINVAL;
+    const uint64_t deadline = timeout_ns ? now_ns() + timeout_ns : 0;
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (s->n_pending > 0 || !s->inflight.empty()) {
+      if (s->error != SBBF_OK) return s->error;
+      if (deadline && now_ns() >= deadline) return SBBF_ETIMEOUT;
+      s->cv.wait_for(lk, std::chrono::microseconds(200));
+    }
+    return s->error;
+  });
 }
 
 sbbf_status sbbf_server_copy_filter(sbbf_server_t* s, uint32_t id, uint32_t* h_words, size_t bytes) {
-  if (!s || !h_words) return SBBF_EINVAL;
-  sbbf_status rc = sbbf_server_drain(s, 0);
-  if (rc != SBBF_OK) return rc;
-  std::lock_guard<std::mutex> lk(s->mu);
-  if (id >= s->filters.size()) return SBBF_EINVAL;
-  const FilterState& f = s->filters[id];
-  if (bytes < f.bytes()) return SBBF_EINVAL;
-  if (f.d_words) {
-    SBBF_CUDA(cudaMemcpyAsync(h_words, f.d_words, f.bytes(), cudaMemcpyDeviceToHost, s->stream));
-    SBBF_CUDA(cudaStreamSynchronize(s->stream));
-  } else {
-    SBBF_CUDA(cudaStreamSynchronize(s->stream));  // a pending eviction copy
-    if (f.written && f.h_words) std::memcpy(h_words, f.h_words, f.bytes());
-    else std::memset(h_words, 0, f.bytes());
-  }
-  return SBBF_OK;
+  return guarded([&]() -> sbbf_status {
+    if (!s || !h_words) return SBBF_EINVAL;
+    sbbf_status rc = sbbf_server_drain(s, 0);
+    if (rc != SBBF_OK) return rc;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (id >= s->filters.size()) return SBBF_EINVAL;
+    const FilterState& f = s->filters[id];
+    if (bytes < f.bytes()) return SBBF_EINVAL;
+    if (f.d_words) {
+      SBBF_CUDA(cudaMemcpyAsync(h_words, f.d_words, f.bytes(), cudaMemcpyDeviceToHost, s->stream));
+      SBBF_CUDA(cudaStreamSynchronize(s->stream));
+    } else {
+      SBBF_CUDA(cudaStreamSynchronize(s->stream));  // a pending eviction copy
+      if (f.written && f.h_words) std::memcpy(h_words, f.h_words, f.bytes());
+      else std::memset(h_words, 0, f.bytes());
+    }
+    return SBBF_OK;
+  });
 }
 
 sbbf_status sbbf_server_prefill(sbbf_server_t* s, uint32_t id, const uint64_t* d_hashes, size_t n) {
-  if (!s) return SBBF_EINVAL;
-  sbbf_status rc = sbbf_server_drain(s, 0);
-  if (rc != SBBF_OK) return rc;
-  std::lock_guard<std::mutex> lk(s->mu);
-  if (id >= s->filters.size() || (n && !d_hashes)) return SBBF_EINVAL;
-  std::vector<char> none(s->filters.size(), 0);
-  rc = make_resident(s, id, 0, none);
-  if (rc != SBBF_OK) return rc;
-  FilterState& f = s->filters[id];
-  f.written = true;
-  f.host_valid = false;
-  f.last_use = ++s->window_seq;
-  rc = launch_insert(f.d_words, f.num_blocks, d_hashes, n, s->stream);
-  if (rc != SBBF_OK) return rc;
-  SBBF_CUDA(cudaStreamSynchronize(s->stream));
-  return SBBF_OK;
+  return guarded([&]() -> sbbf_status {
+    if (!s) return SBBF_EINVAL;
+    sbbf_status rc = sbbf_server_drain(s, 0);
+    if (rc != SBBF_OK) return rc;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (id >= s->filters.size() || (n && !d_hashes)) return SBBF_EINVAL;
+    std::vector<char> none(s->filters.size(), 0);
+    rc = make_resident(s, id, 0, none);
+    if (rc != SBBF_OK) return rc;
+    FilterState& f = s->filters[id];
+    f.written = true;
+    f.host_valid = false;
+    f.last_use = ++s->window_seq;
+    rc = launch_insert(f.d_words, f.num_blocks, d_hashes, n, s->stream);
+    if (rc != SBBF_OK) return rc;
+    SBBF_CUDA(cudaStreamSynchronize(s->stream));
+    return SBBF_OK;
+  });
 }
 
 sbbf_status sbbf_server_stats(sbbf_server_t* s, sbbf_server_stats_t* out) {
-  if (!s || !out) return SBBF_EINVAL;
-  std::lock_guard<std::mutex> lk(s->mu);
-  *out = s->stats;
-  out->resident_bytes = s->resident_bytes;
-  return SBBF_OK;
+  return guarded([&]() -> sbbf_status {
+    if (!s || !out) return SBBF_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    *out = s->stats;
+    out->resident_bytes = s->resident_bytes;
+    return SBBF_OK;
+  });
 }
 
 sbbf_status sbbf_server_replay(sbbf_server_t* s, const sbbf_request_t* reqs,
                                const uint64_t* arrival_ns, size_t n, uint64_t* latency_ns) {
-  if (!s || (n && (!reqs || !arrival_ns || !latency_ns))) return SBBF_EINVAL;
-  std::vector<uint64_t> tickets(n);
-  const uint64_t t0 = now_ns();
-  for (size_t i = 0; i < n; ++i) {
-    while (now_ns() < t0 + arrival_ns[i]) {
-    }  // arrival time of request i
-    sbbf_status rc;
-    while ((rc = sbbf_server_submit(s, &reqs[i], &tickets[i])) == SBBF_EBUSY &&
-           s->cfg.max_pending_requests > 0) {
-      std::this_thread::sleep_for(std::chrono::microseconds(5));  // queue full: back-pressure
-      std::lock_guard<std::mutex> lk(s->mu);
-      if (s->error != SBBF_OK) return s->error;
-      if (s->filters[reqs[i].filter].bytes() > s->cfg.budget_bytes) return SBBF_EBUSY;
+  return guarded([&]() -> sbbf_status {
+    if (!s || (n && (!reqs || !arrival_ns || !latency_ns))) return SBBF_EINVAL;
+    std::vector<uint64_t> tickets(n);
+    const uint64_t t0 = now_ns();
+    for (size_t i = 0; i < n; ++i) {
+      while (now_ns() < t0 + arrival_ns[i]) {
+      }  // arrival time of request i
+      sbbf_status rc;
+      while ((rc = sbbf_server_submit(s, &reqs[i], &tickets[i])) == SBBF_EBUSY &&
+             s->cfg.max_pending_requests > 0) {
+        std::this_thread::sleep_for(std::chrono::microseconds(5));  // queue full: back-pressure
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->error != SBBF_OK) return s->error;
+        if (s->filters[reqs[i].filter].bytes() > s->cfg.budget_bytes) return SBBF_EBUSY;
+      }
+      if (rc != SBBF_OK) return rc;
     }
-    if (rc != SBBF_OK) return rc;
-  }
-  std::unique_lock<std::mutex> lk(s->mu);
-  for (size_t i = 0; i < n; ++i) {
-    sbbf_status rc = wait_ticket(s, lk, tickets[i], 0);
-    if (rc != SBBF_OK) return rc;
-    latency_ns[i] = s->done_ns[tickets[i]] - (t0 + arrival_ns[i]);
-  }
-  return SBBF_OK;
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (size_t i = 0; i < n; ++i) {
+      sbbf_status rc = wait_ticket(s, lk, tickets[i], 0);
+      if (rc != SBBF_OK) return rc;
+      latency_ns[i] = s->done_ns[tickets[i]] - (t0 + arrival_ns[i]);
+    }
+    return SBBF_OK;
+  });
 }
 
 sbbf_status sbbf_server_replay_serial(sbbf_server_t* s, const sbbf_request_t* reqs,
                                       const uint64_t* arrival_ns, size_t n,
                                       uint64_t* latency_ns) {
-  if (!s || (n && (!reqs || !arrival_ns || !latency_ns))) return SBBF_EINVAL;
-  sbbf_status rc = sbbf_server_drain(s, 0);
-  if (rc != SBBF_OK) return rc;
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
-    s->paused = true;  // this thread owns the stream until the replay ends
-  }
-  constexpr size_t kEvents = 1024;
-  std::vector<cudaEvent_t> ev(kEvents, nullptr);
-  cudaError_t e = cudaSuccess;
-  for (auto& x : ev)
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
-  size_t done = 0, launched = 0;  // only recorded events are ever queried
-  const uint64_t t0 = now_ns();
-  auto retire = [&](bool block) -> sbbf_status {  // stamps finished requests in order
-    while (done < launched) {
-      const cudaError_t q = block ? cudaEventSynchronize(ev[done % kEvents])
-                                  : cudaEventQuery(ev[done % kEvents]);
-      if (q == cudaErrorNotReady) return SBBF_OK;
-      if (q != cudaSuccess) return record_cuda(q);
-      latency_ns[done] = now_ns() - (t0 + arrival_ns[done]);
-      ++done;
-      if (block) return SBBF_OK;
+  return guarded([&]() -> sbbf_status {
+    if (!s || (n && (!reqs || !arrival_ns || !latency_ns))) return SBBF_EINVAL;
+    sbbf_status rc = sbbf_server_drain(s, 0);
+    if (rc != SBBF_OK) return rc;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->paused = true;  // this thread owns the stream until the replay ends
     }
-    return SBBF_OK;
-  };
-  rc = e == cudaSuccess ? SBBF_OK : record_cuda(e);
-  for (size_t i = 0; i < n && rc == SBBF_OK; ++i) {
-    while (now_ns() < t0 + arrival_ns[i]) {
-      rc = retire(false);
-      if (rc != SBBF_OK) break;
-    }
-    if (rc != SBBF_OK) break;
-    while (i - done >= kEvents && rc == SBBF_OK) rc = retire(true);  // event ring full
-    if (rc != SBBF_OK) break;
-    std::lock_guard<std::mutex> lk(s->mu);
-    const sbbf_request_t& r = reqs[i];
-    if (r.filter >= s->filters.size()) {
-      rc = SBBF_EINVAL;
-      break;
-    }
-    std::vector<char> none(s->filters.size(), 0);
-    rc = make_resident(s, r.filter, 0, none);
-    if (rc != SBBF_OK) break;
-    FilterState& f = s->filters[r.filter];
-    f.last_use = ++s->window_seq;
-    if (r.n) {
-      if (r.op == SBBF_OP_INSERT) {
-        f.written = true;
-        f.host_valid = false;
-        rc = launch_insert(f.d_words, f.num_blocks, r.d_hashes, r.n, s->stream);
-      } else {
-        rc = launch_find(f.d_words, f.num_blocks, r.d_hashes, r.n, r.d_out_bits, s->stream);
+    constexpr size_t kEvents = 1024;
+    std::vector<cudaEvent_t> ev(kEvents, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (auto& x : ev)
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+    size_t done = 0, launched = 0;  // only recorded events are ever queried
+    const uint64_t t0 = now_ns();
+    auto retire = [&](bool block) -> sbbf_status {  // stamps finished requests in order
+      while (done < launched) {
+        const cudaError_t q = block ? cudaEventSynchronize(ev[done % kEvents])
+                                    : cudaEventQuery(ev[done % kEvents]);
+        if (q == cudaErrorNotReady) return SBBF_OK;
+        if (q != cudaSuccess) return record_cuda(q);
+        latency_ns[done] = now_ns() - (t0 + arrival_ns[done]);
+        ++done;
+        if (block) return SBBF_OK;
       }
-      ++s->stats.launches;
+      return SBBF_OK;
+    };
+    rc = e == cudaSuccess ? SBBF_OK : record_cuda(e);
+    for (size_t i = 0; i < n && rc == SBBF_OK; ++i) {
+      while (now_ns() < t0 + arrival_ns[i]) {
+        rc = retire(false);
+        if (rc != SBBF_OK) break;
+      }
+      if (rc != SBBF_OK) break;
+      while (i - done >= kEvents && rc == SBBF_OK) rc = retire(true);  // event ring full
+      if (rc != SBBF_OK) break;
+      std::lock_guard<std::mutex> lk(s->mu);
+      const sbbf_request_t& r = reqs[i];
+      if (r.filter >= s->filters.size()) {
+        rc = SBBF_EINVAL;
+        break;
+      }
+      std::vector<char> none(s->filters.size(), 0);
+      rc = make_resident(s, r.filter, 0, none);
+      if (rc != SBBF_OK) break;
+      FilterState& f = s->filters[r.filter];
+      f.last_use = ++s->window_seq;
+      if (r.n) {
+        if (r.op == SBBF_OP_INSERT) {
+          f.written = true;
+          f.host_valid = false;
+          rc = launch_insert(f.d_words, f.num_blocks, r.d_hashes, r.n, s->stream);
+        } else {
+          rc = launch_find(f.d_words, f.num_blocks, r.d_hashes, r.n, r.d_out_bits, s->stream);
+        }
+        ++s->stats.launches;
+      }
+      if (rc == SBBF_OK) {
+        const cudaError_t er = cudaEventRecord(ev[i % kEvents], s->stream);
+        if (er != cudaSuccess) rc = record_cuda(er);
+        else launched = i + 1;
+      }
     }
-    if (rc == SBBF_OK) {
-      const cudaError_t er = cudaEventRecord(ev[i % kEvents], s->stream);
-      if (er != cudaSuccess) rc = record_cuda(er);
-      else launched = i + 1;
+    while (rc == SBBF_OK && done < launched) rc = retire(true);
+    for (auto& x : ev)
+      if (x) cudaEventDestroy(x);
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->paused = false;
     }
-  }
-  while (rc == SBBF_OK && done < launched) rc = retire(true);
-  for (auto& x : ev)
-    if (x) cudaEventDestroy(x);
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
-    s->paused = false;
-  }
-  s->cv.notify_all();
-  return rc;
+    s->cv.notify_all();
+    return rc;
+  });
 }
 
 }  // extern "C"
