@@ -310,6 +310,41 @@ def test_config_c1_full_size():
     assert hit[member].all()
 
 
+def test_bench_step_as_cuda_graph():
+    """The benchmark's timed step as it runs there: clear, insert 1M, look up
+    256M, captured once as a CUDA graph and replayed; after two replays the
+    words are the oracle's, the first 8M answers equal the oracle's and 1M
+    sampled answers across the batch do too."""
+    w = wl.C1
+    f = sb.Filter(w.num_blocks)
+    ins = wl.gen_inserts(w, 0, w.n_insert, device=dev())
+    q = wl.gen_queries(w, 0, w.n_lookup)
+    out = torch.empty(sb.out_words(w.n_lookup), dtype=torch.int32, device=dev())
+
+    def step():
+        f.clear()
+        f.insert(ins)
+        f.find(q, out=out)
+
+    step()  # eager warm-up
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    out.fill_(-1)
+    f.words.fill_(-1)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    keys = inp.stream(w.cfg, 0, w.n_insert)
+    ref = _oracle_filter(w.num_blocks, keys)
+    assert np.array_equal(f.to_numpy(), ref)
+    head = 8 * 2**20
+    assert np.array_equal(bits_np(out[: head // 32]),
+                          oracle.find(ref, w.num_blocks, u64_np(q[:head])))
+    _sampled_lookup_check(w, f, ref, None, out, 0, w.n_lookup, 1 << 20, 7)
+
+
 def test_config_c2_full_size():
     """100M hashes into 4,194,304 blocks in 16M batches: words bit-exact; 1B
     lookups: first 4M in full and 1M sampled."""
