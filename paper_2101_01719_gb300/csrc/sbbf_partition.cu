@@ -18,12 +18,15 @@
 //      tile by slice there and writes each slice's run at its own cursor, so
 //      consecutive threads write consecutive addresses;
 //   4. insert or look up the slice-ordered keys with the in-order dynamic
-//      tile schedule; the tiles of slice q bulk-prefetch slice q + 1 into L2,
-//      so the filter is read from DRAM sequentially and hit in L2 when the
-//      keys arrive.
+//      tile schedule; every claimed tile bulk-prefetches into L2 the filter
+//      bytes of the keys a slice ahead, so the filter is read from DRAM
+//      sequentially and hit in L2 when the keys arrive;
+//   5. lookups only: the answers, written in slice order, go back to key
+//      order one sub-range of positions at a time, each in shared memory.
 // Inserts commute (OR), so the order within a slice does not matter and the
-// filter equals the unpartitioned insert bit for bit; lookups carry each
-// key's original position and set that bit of the result.
+// filter equals the unpartitioned insert bit for bit; lookups keep each key's
+// original position (written by the scatter) and answer exactly as the
+// unpartitioned lookup.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -94,10 +97,23 @@ __device__ __forceinline__ unsigned rank_warp(unsigned* ranks, uint32_t n_slices
 }
 
 // Keys [c * R, min(n, (c + 1) * R)) belong to CTA c of the count and scatter
-// passes (R even, so a range starts 16-byte aligned whenever the array does).
+// passes.  R is a multiple of 32: a range starts 16-byte aligned whenever the
+// array does, and a lookup's result words split between ranges without
+// sharing a word.
 __host__ __device__ __forceinline__ uint64_t range_keys(uint64_t n, uint32_t ctas) {
   const uint64_t r = (n + ctas - 1) / ctas;
-  return (r + 1) & ~1ull;
+  return (r + 31) & ~31ull;
+}
+
+// Lookups map answers back to key order by sub-range: kSubKeys consecutive
+// positions of a CTA's range (a multiple of every scatter tile).  The scatter
+// records its slice cursors at each sub-range start, so the keys of sub-range
+// u of CTA c that fall in slice q sit at sorted positions
+// [marks[c][u][q], marks[c][u + 1][q]).
+constexpr uint32_t kSubKeys = 1u << 18;
+
+__host__ __device__ __forceinline__ uint32_t sub_ranges(uint64_t range) {
+  return static_cast<uint32_t>((range + kSubKeys - 1) / kSubKeys);
 }
 
 // ---- bulk copies into shared memory ------------------------------------------
@@ -311,12 +327,17 @@ __host__ __device__ constexpr size_t scatter_smem_bytes(uint32_t tile, uint32_t 
 // position is one add.  Tile t+1 is bulk-copied into the other buffer while
 // tile t is processed.  The copies need a 16-byte aligned key array; with
 // any other alignment, or if a copy ever failed to complete in time, the
-// CTA reads the keys straight from global memory instead.
+// CTA reads the keys straight from global memory instead.  Lookups (kIndex)
+// also write each key's original position, and the cursors at every
+// sub-range start (and after the last tile) to marks[c][u][q], `rows` rows
+// per CTA.
 template <bool kFew, bool kIndex, uint32_t kT>
 __global__ void __launch_bounds__(kPartThreads, 1)
     scatter_kernel(const uint64_t* __restrict__ hashes, uint64_t n, uint32_t nb, int shift,
                    uint32_t n_slices, uint64_t range, const unsigned long long* __restrict__ base,
-                   uint64_t* __restrict__ out, uint32_t* __restrict__ out_idx) {
+                   uint64_t* __restrict__ out, uint32_t* __restrict__ out_idx,
+                   uint32_t* __restrict__ marks, uint32_t rows) {
+  static_assert(kSubKeys % kT == 0, "a sub-range is a whole number of tiles");
   extern __shared__ __align__(16) unsigned long long smem[];
   uint64_t* s_buf0 = reinterpret_cast<uint64_t*>(smem);
   uint64_t* s_buf1 = s_buf0 + kT;
@@ -355,11 +376,18 @@ __global__ void __launch_bounds__(kPartThreads, 1)
   uint32_t parity = 0;  // bit i: phase parity expected next on buffer i
   const uint64_t pol = policy_evict_first();
 
+  uint32_t* my_marks = kIndex ? marks + static_cast<uint64_t>(blockIdx.x) * rows * n_slices
+                              : nullptr;
   for (uint64_t t = 0; t < n_tiles; ++t) {
     const uint64_t t0 = a + t * kT;
     const uint32_t m = static_cast<uint32_t>(b - t0 < kT ? b - t0 : kT);
     const int cur = static_cast<int>(t & 1);
     uint64_t* s_in = cur ? s_buf1 : s_buf0;
+    if (kIndex && t % (kSubKeys / kT) == 0) {  // cursors are true cursors between tiles
+      uint32_t* row = my_marks + (t / (kSubKeys / kT)) * n_slices;
+      for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x)
+        row[i] = static_cast<uint32_t>(s_cursor[i]);
+    }
     if (bulk) {
       // the other buffer's last reader finished at the previous tile's end
       if (threadIdx.x == 0 && t + 1 < n_tiles) issue(t + 1);
@@ -408,6 +436,11 @@ __global__ void __launch_bounds__(kPartThreads, 1)
       s_cnt[i] = 0;
     }
     __syncthreads();
+  }
+  if (kIndex) {
+    uint32_t* row = my_marks + static_cast<uint64_t>(sub_ranges(b - a)) * n_slices;
+    for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x)
+      row[i] = static_cast<uint32_t>(s_cursor[i]);
   }
 }
 
@@ -532,16 +565,30 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Slice-ordered lookups of keys[0..n) (original positions idx[]), with the
-// same schedule and streaming prefetch as the sliced insert.  A key found in
-// the filter sets bit idx of `out` (zeroed beforehand) with one atomicOr;
-// misses write nothing.
-__global__ void __launch_bounds__(256)
+// Bits of x (16 bits) at the even positions and of y at the odd positions
+// of a 32-bit word.
+__device__ __forceinline__ uint32_t spread16(uint32_t x) {
+  x = (x | (x << 8)) & 0x00FF00FFu;
+  x = (x | (x << 4)) & 0x0F0F0F0Fu;
+  x = (x | (x << 2)) & 0x33333333u;
+  return (x | (x << 1)) & 0x55555555u;
+}
+
+__device__ __forceinline__ uint32_t interleave16(uint32_t x, uint32_t y) {
+  return spread16(x) | (spread16(y) << 1);
+}
+
+// Slice-ordered lookups of keys[0..n), with the same schedule and streaming
+// prefetch as the sliced insert.  The answers are written in sorted order,
+// packed like the unpartitioned lookup's (bit k of the pair of words 2g, 2g+1
+// answers sorted position 64g + k); unscatter_kernel moves them to the keys'
+// original positions.
+__global__ void __launch_bounds__(256, 4)
     sliced_find_kernel(const uint32_t* __restrict__ words, uint32_t nb, int shift,
-                       const uint64_t* __restrict__ keys, const uint32_t* __restrict__ idx,
-                       uint64_t n, const unsigned long long* __restrict__ offsets,
-                       uint32_t n_slices, unsigned long long* __restrict__ tiles,
-                       uint32_t* __restrict__ out, int rounds) {
+                       const uint64_t* __restrict__ keys, uint64_t n,
+                       const unsigned long long* __restrict__ offsets, uint32_t n_slices,
+                       unsigned long long* __restrict__ tiles, uint32_t* __restrict__ sorted_bits,
+                       int rounds) {
   __shared__ unsigned long long s_tile;
   const unsigned wpc = blockDim.x >> 5, wic = threadIdx.x >> 5, lane = lane_id();
   const uint64_t n_groups = (n + 63) >> 6;
@@ -591,16 +638,112 @@ __global__ void __launch_bounds__(256)
       }
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
+        // bit l of b0 / b1: key 2l / 2l + 1 of the group
+        const uint32_t b0 = __ballot_sync(
+            0xFFFFFFFFu, k[u] < n && block_has(w[u][0], static_cast<uint32_t>(h[u][0])));
+        const uint32_t b1 = __ballot_sync(
+            0xFFFFFFFFu, k[u] + 1 < n && block_has(w[u][1], static_cast<uint32_t>(h[u][1])));
+        const uint64_t g = g0 + static_cast<uint64_t>(r + u) * wpc + wic;
+        if (lane == 0 && g < n_groups)
+          *reinterpret_cast<uint2*>(sorted_bits + 2 * g) =
+              make_uint2(interleave16(b0 & 0xFFFFu, b1 & 0xFFFFu), interleave16(b0 >> 16, b1 >> 16));
+      }
+    }
+  }
+}
+
+// Answers back into key order.  CTA (c, u) owns the original positions
+// [lo, hi): sub-range u of scatter CTA c's key range.  The scatter put the
+// keys of that sub-range that fall in slice q at sorted positions
+// [marks[c][u][q], marks[c][u + 1][q]).  The CTA lists the answer words that
+// overlap these runs (shared memory holds each run's bounds and the list
+// offset of its first word); a lane takes one word, masks it to its run, and
+// for each found key -- each set bit -- loads the key's original position
+// and sets its bit in a shared-memory copy of the sub-range's result words,
+// four bits per round so that their loads overlap.  The words are then
+// stored whole: every result word belongs to exactly one CTA, so there are
+// no global atomics and no zeroing pass.  Positions and runs are clamped to
+// their buffers, so keys that changed between the passes give wrong answers,
+// never an access out of bounds.
+constexpr int kUnscatterThreads = 512;
+
+__host__ __device__ constexpr size_t unscatter_smem_bytes(uint32_t n_slices) {
+  return 4ull * (kSubKeys / 32) + 4ull * 3 * n_slices;
+}
+
+__global__ void __launch_bounds__(kUnscatterThreads)
+    unscatter_kernel(const uint32_t* __restrict__ sorted_bits, const uint32_t* __restrict__ idx,
+                     const uint32_t* __restrict__ marks, uint64_t n, uint64_t range, uint32_t rows,
+                     uint32_t n_slices, uint32_t* __restrict__ out) {
+  extern __shared__ __align__(16) uint32_t s_mem[];
+  uint32_t* s_out = s_mem;                           // result words of the sub-range
+  uint32_t* s_lo = s_out + kSubKeys / 32;            // run q: sorted positions [s_lo, s_hi)
+  uint32_t* s_hi = s_lo + n_slices;
+  uint32_t* s_item = s_hi + n_slices;                // list offset of run q's first word
+  __shared__ unsigned warp_sums[32];
+  __shared__ uint32_t s_last;
+  const uint32_t subs = rows - 1;
+  const uint32_t c = blockIdx.x / subs, u = blockIdx.x % subs;
+  const uint64_t a = static_cast<uint64_t>(c) * range;
+  const uint64_t end = a + range < n ? a + range : n;
+  const uint64_t lo = a + static_cast<uint64_t>(u) * kSubKeys;
+  if (lo >= end) return;  // the whole CTA
+  const uint64_t hi = lo + kSubKeys < end ? lo + kSubKeys : end;
+  const uint32_t n_words = static_cast<uint32_t>((hi - lo + 31) / 32);
+  const uint32_t* m0 = marks + (static_cast<uint64_t>(c) * rows + u) * n_slices;
+  const uint32_t* m1 = m0 + n_slices;
+  for (uint32_t i = threadIdx.x; i < n_words; i += blockDim.x) s_out[i] = 0;
+  for (uint32_t q = threadIdx.x; q < n_slices; q += blockDim.x) {
+    const uint32_t p1 = static_cast<uint32_t>(m1[q] < n ? m1[q] : n);
+    const uint32_t p0 = m0[q] < p1 ? m0[q] : p1;
+    s_lo[q] = p0;
+    s_hi[q] = p1;
+    const uint32_t words = p1 > p0 ? ((p1 - 1) >> 5) - (p0 >> 5) + 1 : 0u;
+    s_item[q] = words;  // scanned next
+    if (q == n_slices - 1) s_last = words;
+  }
+  __syncthreads();
+  cta_exclusive_scan(s_item, n_slices, warp_sums);
+  const uint32_t items = s_item[n_slices - 1] + s_last;
+  const unsigned lane = threadIdx.x & 31;
+  for (uint32_t i0 = threadIdx.x & ~31u; i0 < items; i0 += blockDim.x) {
+    const uint32_t i = i0 + lane;
+    uint32_t bits = 0, base = 0;
+    if (i < items) {
+      uint32_t l = 0, r = n_slices;  // the run holding item i: last q with s_item[q] <= i
+      while (r - l > 1) {
+        const uint32_t mid = (l + r) >> 1;
+        if (s_item[mid] <= i) l = mid; else r = mid;
+      }
+      const uint32_t w = (s_lo[l] >> 5) + (i - s_item[l]);
+      base = 32 * w;
+      const uint32_t from = s_lo[l] > base ? s_lo[l] - base : 0u;
+      const uint32_t to = s_hi[l] - base < 32 ? s_hi[l] - base : 32u;
+      const uint32_t mask = (to == 32 ? 0xFFFFFFFFu : (1u << to) - 1) & ~((1u << from) - 1);
+      bits = __ldg(sorted_bits + w) & mask;
+    }
+    while (__any_sync(0xFFFFFFFFu, bits != 0)) {
+      uint32_t j[4];
+      bool has[4];
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          if (k[u] + e < n && block_has(w[u][e], static_cast<uint32_t>(h[u][e]))) {
-            const uint32_t j = idx[k[u] + e];
-            atomicOr(out + (j >> 5), 1u << (j & 31));
-          }
+      for (int e = 0; e < 4; ++e) {
+        has[e] = bits != 0;
+        const uint32_t p = base + (has[e] ? __ffs(bits) - 1 : 0u);
+        bits &= bits - 1;
+        j[e] = has[e] ? __ldg(idx + p) : 0u;
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (has[e] && j[e] >= lo && j[e] < hi) {
+          const uint32_t o = static_cast<uint32_t>(j[e] - lo);
+          atomicOr(&s_out[o >> 5], 1u << (o & 31));
         }
       }
     }
   }
+  __syncthreads();
+  uint32_t* dst = out + lo / 32;
+  for (uint32_t i = threadIdx.x; i < n_words; i += blockDim.x) dst[i] = s_out[i];
 }
 
 inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
@@ -648,30 +791,51 @@ int find_occupancy() {
   return occ;
 }
 
-// Blocks per slice, 2^shift.  A slice's blocks stay in L2 from its prefetch
-// until its last key is processed, so a slice plus the keys in flight (and
-// those prefetched ahead) must fit there.  For inserts slices get smaller as
-// long as the partition's fan-out stays near kTargetSlices (the scatter's runs
-// per tile shrink with more slices), between 4 and 32 MiB: measured 67.6
-// against 60.3 G inserts/s on a 2 GiB filter.  For lookups the slice stream
-// was measured to keep its reads exact while slice + 1.5 windows of filter
-// bytes stayed below ~48 MiB (2 GiB filter: 62 MB live, 5.85 GB of DRAM reads
-// for 3.5 GB of keys and filter; 46 MB, 4.31 GB), while the scatter of 4-byte
-// positions pays for every extra slice: lookups take the largest slice (at
-// most 32 MiB) within that budget, no smaller than lookup_min_shift.
-int slice_shift(uint32_t num_blocks, uint64_t n, bool lookup) {
-  if (lookup) {
-    const double filter_bytes = 32.0 * num_blocks;
-    const unsigned grid = grid_for((n + 63) / 64, 8, find_occupancy());
-    const int rounds = sliced_rounds(grid, n, 32ull * num_blocks, 2);
-    const double window_bytes = static_cast<double>(grid) * 8 * rounds * 64 * filter_bytes /
-                                static_cast<double>(n);
-    const double slice_max = 48.0 * 1024 * 1024 - 1.5 * window_bytes;
-    const int floor_shift = lookup_min_shift(num_blocks);
-    int shift = kMaxSliceShift;
-    while (shift > floor_shift && 32.0 * static_cast<double>(1ull << shift) > slice_max) --shift;
-    return shift;
+// The slice stream keeps its reads exact while a slice plus 1.5 windows of
+// filter bytes stay below ~48 MiB of L2 (measured on a 2 GiB filter: 62 MB
+// live, 5.85 GB of DRAM reads for 3.5 GB of keys and filter; 46 MB, 4.31 GB).
+constexpr double kLiveBytes = 48.0 * 1024 * 1024;
+
+// Slice shift, grid and tile rounds of a partitioned lookup of n keys.  A
+// slice's blocks stay in L2 from its prefetch until its last key is
+// processed, so a slice plus the keys in flight (and those prefetched ahead)
+// must fit there, while the scatter of 4-byte positions pays for every extra
+// slice: lookups take the largest slice (at most 32 MiB, no smaller than
+// lookup_min_shift) within the live-set budget.  When even that slice leaves
+// too little room -- sparse batches, many filter bytes per key -- the grid
+// shrinks (to one CTA per SM at least) until the window fits beside it.
+struct FindPlan {
+  int shift;
+  unsigned grid;
+  int rounds;
+};
+
+FindPlan find_plan(uint32_t num_blocks, uint64_t n) {
+  const double per_key = 32.0 * num_blocks / static_cast<double>(n);
+  unsigned grid = grid_for((n + 63) / 64, 8, find_occupancy());
+  const int rounds = sliced_rounds(grid, n, 32ull * num_blocks, 2);
+  const double keys_per_cta = 8.0 * rounds * 64;
+  const double window = grid * keys_per_cta * per_key;
+  const int floor_shift = lookup_min_shift(num_blocks);
+  int shift = kMaxSliceShift;
+  while (shift > floor_shift && 32.0 * static_cast<double>(1ull << shift) + 1.5 * window > kLiveBytes)
+    --shift;
+  const double room = (kLiveBytes - 32.0 * static_cast<double>(1ull << shift)) / 1.5;
+  if (window > room) {
+    const double cap = room / per_key / keys_per_cta;
+    const unsigned floor_grid = static_cast<unsigned>(sm_count());
+    unsigned g = cap < grid ? static_cast<unsigned>(cap) : grid;
+    grid = g > floor_grid ? g : (floor_grid < grid ? floor_grid : grid);
   }
+  return {shift, grid, rounds};
+}
+
+// Blocks per slice, 2^shift.  For inserts slices get smaller as long as the
+// partition's fan-out stays near kTargetSlices (the scatter's runs per tile
+// shrink with more slices), between 4 and 32 MiB: measured 67.6 against
+// 60.3 G inserts/s on a 2 GiB filter.  Lookups: find_plan.
+int slice_shift(uint32_t num_blocks, uint64_t n, bool lookup) {
+  if (lookup) return find_plan(num_blocks, n).shift;
   int shift = kMinSliceShift;
   while (shift < kMaxSliceShift && slices_at(num_blocks, shift) > kTargetSlices) ++shift;
   return shift;
@@ -686,8 +850,13 @@ uint64_t partition_scratch_bytes(uint32_t num_blocks, uint64_t n, bool with_inde
   const uint64_t s = with_index ? slices_at(num_blocks, lookup_min_shift(num_blocks))
                                 : slices_at(num_blocks, slice_shift(num_blocks, n, false));
   const uint64_t g = partition_ctas();
-  return align256(4 * g * s) + align256(8 * g * s) + align256(8 * (s + 1)) + 256 +
-         align256(8 * n) + (with_index ? align256(4 * n) : 0);
+  uint64_t bytes = align256(4 * g * s) + align256(8 * g * s) + align256(8 * (s + 1)) + 256 +
+                   align256(8 * n);
+  if (with_index) {
+    const uint64_t rows = sub_ranges(range_keys(n, static_cast<uint32_t>(g))) + 1;
+    bytes += align256(4 * n) + align256(8 * ((n + 63) / 64)) + align256(4 * g * rows * s);
+  }
+  return bytes;
 }
 
 // Largest batch a partitioned lookup handles in one pass (32-bit positions).
@@ -700,8 +869,11 @@ struct PartScratch {
   unsigned long long* base;        // [ctas][n_slices]
   unsigned long long* offsets;     // [n_slices + 1]
   unsigned long long* tiles;       // dynamic-schedule counter
-  uint64_t* sorted;
-  uint32_t* idx;
+  uint64_t* sorted;                // [n]
+  uint32_t* idx;                   // [n] original positions (lookups)
+  uint32_t* sorted_bits;           // [2 * ceil(n / 64)] answers in sorted order (lookups)
+  uint32_t* marks;                 // [ctas][rows][n_slices] sub-range cursors (lookups)
+  uint32_t rows;
 };
 
 PartScratch carve(void* scratch, uint32_t ctas, uint32_t n_slices, uint64_t n) {
@@ -719,6 +891,11 @@ PartScratch carve(void* scratch, uint32_t ctas, uint32_t n_slices, uint64_t n) {
   r.sorted = reinterpret_cast<uint64_t*>(p);
   p += align256(8 * n);
   r.idx = reinterpret_cast<uint32_t*>(p);
+  p += align256(4 * n);
+  r.sorted_bits = reinterpret_cast<uint32_t*>(p);
+  p += align256(8 * ((n + 63) / 64));
+  r.marks = reinterpret_cast<uint32_t*>(p);
+  r.rows = sub_ranges(range_keys(n, ctas)) + 1;
   return r;
 }
 
@@ -732,7 +909,8 @@ sbbf_status launch_scatter(const uint64_t* hashes, uint64_t n, uint32_t nb, int 
       static_cast<int>(kSmemBudget));
   if (attr != cudaSuccess) return record_cuda(attr);
   scatter_kernel<kFew, kIndex, kT><<<ctas, kPartThreads, smem, s>>>(
-      hashes, n, nb, shift, n_slices, range, ps.base, ps.sorted, kIndex ? ps.idx : nullptr);
+      hashes, n, nb, shift, n_slices, range, ps.base, ps.sorted, kIndex ? ps.idx : nullptr,
+      kIndex ? ps.marks : nullptr, ps.rows);
   return launch_status();
 }
 
@@ -798,9 +976,10 @@ sbbf_status launch_insert_partitioned(uint32_t* words, uint32_t num_blocks, cons
 }
 
 // Partitioned lookup of d_hashes[0..n) into the packed bitmask d_out (the
-// same bits as the unpartitioned lookup).  `scratch` holds at least
-// partition_scratch_bytes(num_blocks, min(n, 2^31), true) bytes; batches
-// larger than 2^31 keys run in pieces of 2^31 (a multiple of 32).
+// same bits as the unpartitioned lookup; every word of the answer is
+// written).  `scratch` holds at least partition_scratch_bytes(num_blocks,
+// min(n, 2^31), true) bytes; batches larger than 2^31 keys run in pieces of
+// 2^31 (a multiple of 32).
 sbbf_status launch_find_partitioned(const uint32_t* words, uint32_t num_blocks,
                                     const uint64_t* hashes, uint64_t n, uint32_t* d_out,
                                     void* scratch, cudaStream_t s) {
@@ -808,21 +987,25 @@ sbbf_status launch_find_partitioned(const uint32_t* words, uint32_t num_blocks,
   if (n == 0) return SBBF_OK;
   for (uint64_t off = 0; off < n; off += kMaxIndexedKeys) {
     const uint64_t m = n - off < kMaxIndexedKeys ? n - off : kMaxIndexedKeys;
-    const int shift = slice_shift(num_blocks, m, true);
-    const uint32_t n_slices = slices_at(num_blocks, shift);
+    const FindPlan plan = find_plan(num_blocks, m);
+    const uint32_t n_slices = slices_at(num_blocks, plan.shift);
     if (n_slices == 0 || n_slices > kMaxSlices) return SBBF_EINVAL;
-    const PartScratch ps = carve(scratch, partition_ctas(), n_slices, m);
-    sbbf_status st = partition(hashes + off, m, num_blocks, shift, n_slices, ps, true, s);
+    const uint32_t ctas = partition_ctas();
+    const PartScratch ps = carve(scratch, ctas, n_slices, m);
+    sbbf_status st = partition(hashes + off, m, num_blocks, plan.shift, n_slices, ps, true, s);
     if (st != SBBF_OK) return st;
-    uint32_t* out = d_out + off / 32;
-    SBBF_CUDA(cudaMemsetAsync(out, 0, 4 * ((m + 31) / 32), s));
     SBBF_CUDA(cudaMemsetAsync(ps.tiles, 0, 8, s));
-    const unsigned grid = grid_for((m + 63) / 64, 8, find_occupancy());
-    const int rounds = sliced_rounds(grid, m, 32ull * num_blocks, 2);
-    sliced_find_kernel<<<grid, 256, 0, s>>>(words, num_blocks, shift, ps.sorted, ps.idx, m,
-                                            ps.offsets, n_slices, ps.tiles, out, rounds);
-    st = launch_status();
-    if (st != SBBF_OK) return st;
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        unscatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmemBudget));
+    if (attr != cudaSuccess) return record_cuda(attr);
+    sliced_find_kernel<<<plan.grid, 256, 0, s>>>(words, num_blocks, plan.shift, ps.sorted, m,
+                                                 ps.offsets, n_slices, ps.tiles, ps.sorted_bits,
+                                                 plan.rounds);
+    if ((st = launch_status()) != SBBF_OK) return st;
+    unscatter_kernel<<<ctas * (ps.rows - 1), kUnscatterThreads, unscatter_smem_bytes(n_slices),
+                       s>>>(ps.sorted_bits, ps.idx, ps.marks, m, range_keys(m, ctas), ps.rows,
+                            n_slices, d_out + off / 32);
+    if ((st = launch_status()) != SBBF_OK) return st;
   }
   return SBBF_OK;
 }

@@ -436,3 +436,25 @@ def test_partitioned_find_equals_oracle(B, n):
     assert got[-1] == 0xFFFFFFFF  # nothing written past the answers
     f.set_partitioning(sb.PARTITION_OFF)
     assert np.array_equal(bits_np(f.find(to_dev(q))), oracle.find(ref, B, q))
+
+
+def test_partitioned_find_many_sub_ranges():
+    """A batch large enough that every scatter range spans several answer
+    sub-ranges (2^18 positions each), members spread through it, a ragged
+    last range and tail: each answer lands at its original position exactly
+    as the oracle says, and nothing is written past the answers."""
+    B, n = 9 * 2**20 + 7, 100_000_037
+    keys = inp.stream(150, 0, 12_000_000)
+    q = np.concatenate([inp.stream(150, 1, n - keys.size), keys])
+    q = q[np.random.default_rng(150).permutation(n)]
+    ref = oracle.new_filter(B)
+    oracle.insert_mt(ref, B, keys, oracle.num_cores())
+    f = sb.Filter(B)
+    f.words.copy_(torch.from_numpy(ref.view(np.int32)).to(dev()))
+    f.set_partitioning(sb.PARTITION_ON)
+    out = torch.full((sb.out_words(n) + 1,), -1, dtype=torch.int32, device=dev())
+    f.find(to_dev(q), out=out)
+    got = bits_np(out)
+    exp, _ = oracle.find_mt(ref, B, q, oracle.num_cores())
+    assert np.array_equal(got[: sb.out_words(n)], exp)
+    assert got[-1] == 0xFFFFFFFF
