@@ -65,6 +65,9 @@ def parse_args(argv=None):
                         "with XXH64 inside the kernels instead of precomputed hashes")
     p.add_argument("--lanes", type=int, choices=[4, 8, 16], default=8,
                    help="measurement variant: 4- or 16-lane blocks (same filter bytes)")
+    p.add_argument("--partition", choices=["auto", "on", "off"], default="auto",
+                   help="single-filter workloads: the filter's partitioning mode (auto: the "
+                        "library's rule)")
     p.add_argument("--eager", action="store_true",
                    help="launch each kernel from Python instead of replaying CUDA graphs")
     p.add_argument("--requests", type=int, default=0,
@@ -109,6 +112,21 @@ def max_over_ranks(dist, value: float, device=None) -> float:
 def aggregate(units_per_rank: list[int], seconds_max: float) -> float:
     """Whole-job throughput: every rank's units over the slowest rank's time."""
     return sum(units_per_rank) / seconds_max
+
+
+def step_kernels(f, batches, n_lookup, raw_keys):
+    """Kernels one single-filter step launches: the clear, each insert batch
+    and the lookup, partitioned or not (sbbf_partition_applies; the kernel
+    counts of each path are stated in sbbf.h)."""
+    hashing = 1 if raw_keys else 0
+    n = 1
+    for _, cnt in batches:
+        n += (4 + hashing) if f.partition_applies(cnt) else 1
+    if f.partition_applies(n_lookup, lookup=True):
+        n += 5 * ((n_lookup + 2**31 - 1) // 2**31) + hashing
+    else:
+        n += 1
+    return n
 
 
 def lookup_slice_start(rank: int, n_lookup: int) -> int:
@@ -247,8 +265,10 @@ def run_ours(args):
     out = torch.empty(sb.out_words(w.n_lookup), dtype=torch.int32, device=dev)
     num_blocks = w.num_blocks * 8 // args.lanes  # the same filter bytes at any lane count
     f = sb.Filter(num_blocks, device=dev, lanes=args.lanes)
+    f.set_partitioning({"auto": sb.PARTITION_AUTO, "on": sb.PARTITION_ON,
+                        "off": sb.PARTITION_OFF}[args.partition])
     torch.cuda.synchronize()
-    variant = args.keys != "hashes" or args.lanes != 8
+    variant = args.keys != "hashes" or args.lanes != 8 or args.partition != "auto"
     do_insert = f.insert if args.keys == "hashes" else f.insert_keys
     do_find = ((lambda q, out: f.find(q, out=out)) if args.keys == "hashes"
                else (lambda q, out: f.find_keys(q, out=out)))
@@ -407,6 +427,8 @@ def run_ours(args):
                    "keys": ("64-bit hashes" if args.keys == "hashes"
                             else "%s keys, XXH64 in the kernels" % args.keys),
                    "filter_bytes": w.filter_bytes, "n_insert": w.n_insert,
+                   "partitioned": {"insert": f.partition_applies(batches[0][1]),
+                                   "lookup": f.partition_applies(w.n_lookup, lookup=True)},
                    "launch": "eager" if args.eager else "CUDA graph of the step",
                    "n_lookup": w.n_lookup, "member_frac": w.member_frac,
                    "l2": "inputs larger than L2 (%.1f GiB lookup stream per step)"
@@ -435,7 +457,7 @@ def run_ours(args):
                  "insert_ms": round(insert_ms, 5), "lookup_ms": round(find_ms, 5),
                  "lookup_hits": hits, "lookup_hit_frac": round(hits / w.n_lookup, 5)},
         "e2e": e2e,
-        "gpu_launches": (2 + len(batches)) * args.steps,
+        "gpu_launches": step_kernels(f, batches, w.n_lookup, args.keys != "hashes") * args.steps,
         "clocks": clocks,
     }
     if variant:

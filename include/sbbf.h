@@ -147,8 +147,9 @@ sbbf_status sbbf_insert_hashes(sbbf_t *f, const uint64_t *d_hashes, size_t n,
  * with each slice prefetched into L2, which turns random DRAM accesses into
  * L2 hits for filters larger than L2.  Results are identical either way
  * (inserts commute; a lookup's answer is set at its original position).  The
- * scratch -- 8 bytes per hash for inserts, 12 for lookups (at most 2^31
- * hashes at a time), plus 24 bytes per slice -- is allocated with cudaMalloc
+ * scratch -- 8 bytes per hash for inserts, 12.125 for lookups (at most 2^31
+ * hashes at a time), plus per slice 12 bytes per SM and, for lookups, 4
+ * bytes per SM and per 2^18 hashes -- is allocated with cudaMalloc
  * (synchronous) when a batch needs more than the filter holds, kept by the
  * filter and freed by sbbf_destroy; partitioned calls on one filter must
  * therefore be ordered on one stream.
@@ -161,6 +162,18 @@ sbbf_status sbbf_insert_hashes(sbbf_t *f, const uint64_t *d_hashes, size_t n,
  * Errors: SBBF_EINVAL (NULL filter or unknown mode). */
 enum { SBBF_PARTITION_AUTO = 0, SBBF_PARTITION_OFF = 1, SBBF_PARTITION_ON = 2 };
 sbbf_status sbbf_set_partitioning(sbbf_t *f, int mode);
+
+/* Whether a batch of n hashes takes the partitioned path under the filter's
+ * current mode: for sbbf_insert_hashes / sbbf_insert_keys / sbbf_insert_bytes
+ * (lookup = 0) or the matching lookups (lookup != 0).  The answer is the
+ * decision before any scratch allocation (in automatic mode a failed
+ * allocation still falls back to the unpartitioned path).  A partitioned
+ * insert runs four kernels (count, scan, scatter, slice-ordered insert), a
+ * partitioned lookup five per piece of at most 2^31 hashes (count, scan,
+ * scatter, slice-ordered lookup, answers back to key order); raw keys add
+ * one hashing kernel.  *applies is set to 1 or 0.
+ * Errors: SBBF_EINVAL (NULL filter or applies). */
+sbbf_status sbbf_partition_applies(const sbbf_t *f, size_t n, int lookup, int *applies);
 
 /* Look up d_hashes[0..n) (appendix find_hash for each) into the packed
  * bitmask d_out_bits of (n + 31) / 32 words (caller-owned, 4-byte aligned).

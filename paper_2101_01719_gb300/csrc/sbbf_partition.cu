@@ -1011,3 +1011,9 @@ sbbf_status launch_find_partitioned(const uint32_t* words, uint32_t num_blocks,
 }
 
 }  // namespace sbbf
+
+sbbf_status sbbf_partition_applies(const sbbf_t* f, size_t n, int lookup, int* applies) {
+  if (!f || !applies) return SBBF_EINVAL;
+  *applies = sbbf::want_partition(f, n, lookup ? 2 : 1) ? 1 : 0;
+  return SBBF_OK;
+}

@@ -55,6 +55,7 @@ SIGNATURES = {
     "sbbf_clear": (_int, [_P, _P]),
     "sbbf_insert_hashes": (_int, [_P, _P, _sz, _P]),
     "sbbf_set_partitioning": (_int, [_P, _int]),
+    "sbbf_partition_applies": (_int, [_P, _sz, _int, _P]),
     "sbbf_find_hashes": (_int, [_P, _P, _sz, _P, _P]),
     "sbbf_union": (_int, [_P, _P, _P]),
     "sbbf_copy_to_host": (_int, [_P, _P, _sz, _P]),
@@ -361,6 +362,14 @@ class Filter:
         """PARTITION_AUTO / PARTITION_OFF / PARTITION_ON (see sbbf.h)."""
         check(lib().sbbf_set_partitioning(self._h, mode), "sbbf_set_partitioning")
         return self
+
+    def partition_applies(self, n: int, lookup: bool = False) -> bool:
+        """Whether a batch of n hashes (inserts, or lookups) takes the
+        partitioned path under the current mode."""
+        v = _c.c_int(0)
+        check(lib().sbbf_partition_applies(self._h, n, 1 if lookup else 0, _c.byref(v)),
+              "sbbf_partition_applies")
+        return bool(v.value)
 
     def insert(self, hashes: torch.Tensor, stream=None):
         ptr = _hashes_ptr(hashes, self.device)

@@ -438,6 +438,21 @@ def test_partitioned_find_equals_oracle(B, n):
     assert np.array_equal(bits_np(f.find(to_dev(q))), oracle.find(ref, B, q))
 
 
+def test_partition_applies_follows_the_rule():
+    """sbbf_partition_applies reports the automatic rule (at least 4Mi hashes,
+    a filter of at least 256 MiB, one hash per block for inserts and two for
+    lookups) and the forced modes."""
+    f = sb.Filter(2**23)  # 256 MiB
+    assert f.partition_applies(2**23) and not f.partition_applies(2**23 - 1)
+    assert not f.partition_applies(2**23, lookup=True) and f.partition_applies(2**24, lookup=True)
+    assert not sb.Filter(2**23 - 1).partition_applies(2**26)
+    f.set_partitioning(sb.PARTITION_OFF)
+    assert not f.partition_applies(2**30) and not f.partition_applies(2**30, lookup=True)
+    f.set_partitioning(sb.PARTITION_ON)
+    assert f.partition_applies(1) and f.partition_applies(1, lookup=True)
+    assert not sb.Filter(4096, lanes=4).set_partitioning(sb.PARTITION_ON).partition_applies(2**30)
+
+
 def test_partitioned_find_many_sub_ranges():
     """A batch large enough that every scatter range spans several answer
     sub-ranges (2^18 positions each), members spread through it, a ragged
