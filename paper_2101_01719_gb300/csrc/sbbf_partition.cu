@@ -319,12 +319,13 @@ __host__ __device__ constexpr size_t scatter_smem_bytes(uint32_t tile, uint32_t 
   return 3ull * 8 * tile + 12ull * n_slices + (with_index ? 2ull * tile : 0);
 }
 
-// Keys into slice order.  CTA c streams its range in tiles of kT keys: the
-// tile is counted per slice, the counts are scanned in place into run starts
-// that then serve as rank cursors (one shared atomic places a key), and each
-// slice's run is written at the CTA's cursor for that slice (from the scan),
-// kept during the tile as cursor minus run start so that a key's output
-// position is one add.  Tile t+1 is bulk-copied into the other buffer while
+// Keys into slice order.  CTA c streams its range in tiles of kT keys: each
+// key claims its rank among the tile's keys of its slice with one shared
+// atomic (so the counters end as the slice counts), the counts are scanned
+// in place into run starts, a key goes to run start + rank in the sorted
+// tile, and each slice's run is written at the CTA's cursor for that slice
+// (from the scan), kept during the tile as cursor minus run start so that a
+// key's output position is one add.  Tile t+1 is bulk-copied into the other buffer while
 // tile t is processed.  The copies need a 16-byte aligned key array; with
 // any other alignment, or if a copy ever failed to complete in time, the
 // CTA reads the keys straight from global memory instead.  Lookups (kIndex)
@@ -338,6 +339,8 @@ __global__ void __launch_bounds__(kPartThreads, 1)
                    uint64_t* __restrict__ out, uint32_t* __restrict__ out_idx,
                    uint32_t* __restrict__ marks, uint32_t rows) {
   static_assert(kSubKeys % kT == 0, "a sub-range is a whole number of tiles");
+  static_assert(kT % kPartThreads == 0 && kT <= 8192, "whole keys per thread; 13-bit ranks");
+  constexpr uint32_t kPer = kT / kPartThreads;  // launched with kPartThreads threads
   extern __shared__ __align__(16) unsigned long long smem[];
   uint64_t* s_buf0 = reinterpret_cast<uint64_t*>(smem);
   uint64_t* s_buf1 = s_buf0 + kT;
@@ -401,23 +404,25 @@ __global__ void __launch_bounds__(kPartThreads, 1)
     auto key_at = [&](uint32_t j) -> uint64_t {
       return from_smem ? s_in[j] : load_key1(hashes + t0 + j, pol);
     };
-    for (uint32_t j0 = 0; j0 < m; j0 += blockDim.x) {
-      const uint32_t j = j0 + threadIdx.x;
+    // each key claims its rank among the tile's keys of its slice (the
+    // counters end as the slice counts); slice and rank stay in registers
+    uint32_t qr[kPer];  // slice << 13 | rank
+#pragma unroll
+    for (uint32_t i = 0; i < kPer; ++i) {
+      const uint32_t j = i * kPartThreads + threadIdx.x;
       const bool v = j < m;
-      count_warp<kFew>(s_cnt, n_slices, v, v ? slice_of(key_at(j), nb, shift) : 0u);
+      const uint32_t q = v ? slice_of(key_at(j), nb, shift) : 0u;
+      qr[i] = (q << 13) | rank_warp<kFew>(s_cnt, n_slices, v, q);
     }
     __syncthreads();
     cta_exclusive_scan(s_cnt, n_slices, warp_sums);  // counts -> run starts (ends with a barrier)
     for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x) s_cursor[i] -= s_cnt[i];
-    __syncthreads();  // run starts are read before the rank atomics move them
-    for (uint32_t j0 = 0; j0 < m; j0 += blockDim.x) {
-      const uint32_t j = j0 + threadIdx.x;
-      const bool v = j < m;
-      const uint64_t key = v ? key_at(j) : 0;
-      const uint32_t q = v ? slice_of(key, nb, shift) : 0u;
-      const unsigned at = rank_warp<kFew>(s_cnt, n_slices, v, q);  // run start + rank
-      if (v) {
-        s_sorted[at] = key;
+#pragma unroll
+    for (uint32_t i = 0; i < kPer; ++i) {
+      const uint32_t j = i * kPartThreads + threadIdx.x;
+      if (j < m) {
+        const unsigned at = s_cnt[qr[i] >> 13] + (qr[i] & 0x1FFFu);  // run start + rank
+        s_sorted[at] = key_at(j);
         if (kIndex) s_pos[at] = static_cast<uint16_t>(j);
       }
     }
@@ -431,10 +436,11 @@ __global__ void __launch_bounds__(kPartThreads, 1)
       }
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x) {
-      s_cursor[i] += s_cnt[i];  // s_cnt[i] is now the run's end: the cursor advances by its length
-      s_cnt[i] = 0;
-    }
+    // the cursor advances by the run's length: cursor - start + end
+    for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x)
+      s_cursor[i] += i + 1 < n_slices ? s_cnt[i + 1] : m;
+    __syncthreads();  // every run end is read before the counters are cleared
+    for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x) s_cnt[i] = 0;
     __syncthreads();
   }
   if (kIndex) {
