@@ -147,9 +147,9 @@ sbbf_status sbbf_insert_hashes(sbbf_t *f, const uint64_t *d_hashes, size_t n,
  * with each slice prefetched into L2, which turns random DRAM accesses into
  * L2 hits for filters larger than L2.  Results are identical either way
  * (inserts commute; a lookup's answer is set at its original position).  The
- * scratch -- 8 bytes per hash for inserts, 12.125 for lookups (at most 2^31
+ * scratch -- 8 bytes per hash for inserts, 10.125 for lookups (at most 2^31
  * hashes at a time), plus per slice 12 bytes per SM and, for lookups, 4
- * bytes per SM and per 2^18 hashes -- is allocated with cudaMalloc
+ * bytes per SM and per 2^16 hashes -- is allocated with cudaMalloc
  * (synchronous) when a batch needs more than the filter holds, kept by the
  * filter and freed by sbbf_destroy; partitioned calls on one filter must
  * therefore be ordered on one stream.

@@ -109,8 +109,9 @@ __host__ __device__ __forceinline__ uint64_t range_keys(uint64_t n, uint32_t cta
 // positions of a CTA's range (a multiple of every scatter tile).  The scatter
 // records its slice cursors at each sub-range start, so the keys of sub-range
 // u of CTA c that fall in slice q sit at sorted positions
-// [marks[c][u][q], marks[c][u + 1][q]).
-constexpr uint32_t kSubKeys = 1u << 18;
+// [marks[c][u][q], marks[c][u + 1][q]); a key's original position is then
+// stored as its 16-bit offset within its sub-range.
+constexpr uint32_t kSubKeys = 1u << 16;
 
 __host__ __device__ __forceinline__ uint32_t sub_ranges(uint64_t range) {
   return static_cast<uint32_t>((range + kSubKeys - 1) / kSubKeys);
@@ -336,7 +337,7 @@ template <bool kFew, bool kIndex, uint32_t kT>
 __global__ void __launch_bounds__(kPartThreads, 1)
     scatter_kernel(const uint64_t* __restrict__ hashes, uint64_t n, uint32_t nb, int shift,
                    uint32_t n_slices, uint64_t range, const unsigned long long* __restrict__ base,
-                   uint64_t* __restrict__ out, uint32_t* __restrict__ out_idx,
+                   uint64_t* __restrict__ out, uint16_t* __restrict__ out_idx,
                    uint32_t* __restrict__ marks, uint32_t rows) {
   static_assert(kSubKeys % kT == 0, "a sub-range is a whole number of tiles");
   static_assert(kT % kPartThreads == 0 && kT <= 8192, "whole keys per thread; 13-bit ranks");
@@ -386,7 +387,9 @@ __global__ void __launch_bounds__(kPartThreads, 1)
     const uint32_t m = static_cast<uint32_t>(b - t0 < kT ? b - t0 : kT);
     const int cur = static_cast<int>(t & 1);
     uint64_t* s_in = cur ? s_buf1 : s_buf0;
-    if (kIndex && t % (kSubKeys / kT) == 0) {  // cursors are true cursors between tiles
+    // offset of the tile's first key within its sub-range
+    const uint32_t sub_off = static_cast<uint32_t>((t % (kSubKeys / kT)) * kT);
+    if (kIndex && sub_off == 0) {  // cursors are true cursors between tiles
       uint32_t* row = my_marks + (t / (kSubKeys / kT)) * n_slices;
       for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x)
         row[i] = static_cast<uint32_t>(s_cursor[i]);
@@ -432,7 +435,7 @@ __global__ void __launch_bounds__(kPartThreads, 1)
       const unsigned long long pos = s_cursor[slice_of(key, nb, shift)] + j;
       if (pos < n) {  // in range unless the input changed between the passes
         out[pos] = key;
-        if (kIndex) out_idx[pos] = static_cast<uint32_t>(t0 + s_pos[j]);
+        if (kIndex) out_idx[pos] = static_cast<uint16_t>(sub_off + s_pos[j]);
       }
     }
     __syncthreads();
@@ -678,7 +681,7 @@ __host__ __device__ constexpr size_t unscatter_smem_bytes(uint32_t n_slices) {
 }
 
 __global__ void __launch_bounds__(kUnscatterThreads)
-    unscatter_kernel(const uint32_t* __restrict__ sorted_bits, const uint32_t* __restrict__ idx,
+    unscatter_kernel(const uint32_t* __restrict__ sorted_bits, const uint16_t* __restrict__ idx,
                      const uint32_t* __restrict__ marks, uint64_t n, uint64_t range, uint32_t rows,
                      uint32_t n_slices, uint32_t* __restrict__ out) {
   extern __shared__ __align__(16) uint32_t s_mem[];
@@ -695,7 +698,8 @@ __global__ void __launch_bounds__(kUnscatterThreads)
   const uint64_t lo = a + static_cast<uint64_t>(u) * kSubKeys;
   if (lo >= end) return;  // the whole CTA
   const uint64_t hi = lo + kSubKeys < end ? lo + kSubKeys : end;
-  const uint32_t n_words = static_cast<uint32_t>((hi - lo + 31) / 32);
+  const uint32_t span = static_cast<uint32_t>(hi - lo);
+  const uint32_t n_words = (span + 31) / 32;
   const uint32_t* m0 = marks + (static_cast<uint64_t>(c) * rows + u) * n_slices;
   const uint32_t* m1 = m0 + n_slices;
   for (uint32_t i = threadIdx.x; i < n_words; i += blockDim.x) s_out[i] = 0;
@@ -736,14 +740,11 @@ __global__ void __launch_bounds__(kUnscatterThreads)
         has[e] = bits != 0;
         const uint32_t p = base + (has[e] ? __ffs(bits) - 1 : 0u);
         bits &= bits - 1;
-        j[e] = has[e] ? __ldg(idx + p) : 0u;
+        j[e] = has[e] ? __ldg(idx + p) : 0u;  // offset within the sub-range
       }
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        if (has[e] && j[e] >= lo && j[e] < hi) {
-          const uint32_t o = static_cast<uint32_t>(j[e] - lo);
-          atomicOr(&s_out[o >> 5], 1u << (o & 31));
-        }
+        if (has[e] && j[e] < span) atomicOr(&s_out[j[e] >> 5], 1u << (j[e] & 31));
       }
     }
   }
@@ -860,7 +861,7 @@ uint64_t partition_scratch_bytes(uint32_t num_blocks, uint64_t n, bool with_inde
                    align256(8 * n);
   if (with_index) {
     const uint64_t rows = sub_ranges(range_keys(n, static_cast<uint32_t>(g))) + 1;
-    bytes += align256(4 * n) + align256(8 * ((n + 63) / 64)) + align256(4 * g * rows * s);
+    bytes += align256(2 * n) + align256(8 * ((n + 63) / 64)) + align256(4 * g * rows * s);
   }
   return bytes;
 }
@@ -876,7 +877,7 @@ struct PartScratch {
   unsigned long long* offsets;     // [n_slices + 1]
   unsigned long long* tiles;       // dynamic-schedule counter
   uint64_t* sorted;                // [n]
-  uint32_t* idx;                   // [n] original positions (lookups)
+  uint16_t* idx;                   // [n] offset of the original position in its sub-range
   uint32_t* sorted_bits;           // [2 * ceil(n / 64)] answers in sorted order (lookups)
   uint32_t* marks;                 // [ctas][rows][n_slices] sub-range cursors (lookups)
   uint32_t rows;
@@ -896,8 +897,8 @@ PartScratch carve(void* scratch, uint32_t ctas, uint32_t n_slices, uint64_t n) {
   p += 256;
   r.sorted = reinterpret_cast<uint64_t*>(p);
   p += align256(8 * n);
-  r.idx = reinterpret_cast<uint32_t*>(p);
-  p += align256(4 * n);
+  r.idx = reinterpret_cast<uint16_t*>(p);
+  p += align256(2 * n);
   r.sorted_bits = reinterpret_cast<uint32_t*>(p);
   p += align256(8 * ((n + 63) / 64));
   r.marks = reinterpret_cast<uint32_t*>(p);
