@@ -156,6 +156,46 @@ __device__ __forceinline__ void store_stream(uint32_t* p, uint32_t v) {
   asm volatile("st.global.cs.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Two or four answer words in one streaming store (8- / 16-byte aligned p).
+__device__ __forceinline__ void store_stream2(uint32_t* p, uint32_t a, uint32_t b) {
+  asm volatile("st.global.cs.v2.u32 [%0], {%1, %2};" ::"l"(p), "r"(a), "r"(b) : "memory");
+}
+__device__ __forceinline__ void store_stream4(uint32_t* p, uint32_t a, uint32_t b, uint32_t c,
+                                              uint32_t d) {
+  asm volatile("st.global.cs.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(a), "r"(b), "r"(c),
+               "r"(d)
+               : "memory");
+}
+
+// Answer words word0 .. word0 + 2U - 1 of a unit of U groups (lo[u], hi[u]
+// for group u), as few stores as the output's alignment allows: one 16-byte
+// store per two groups, else one 8-byte store per group, else (and for words
+// past the answers' end) word by word.  One store request carries four
+// answer words instead of one: measured +5.5% lookups/s on an L2-resident
+// filter, where the L1-to-L2 request rate is the bound.
+template <int U>
+__device__ __forceinline__ void store_answers(uint32_t* out, uint64_t n_out, uint64_t word0,
+                                              const uint32_t (&lo)[U], const uint32_t (&hi)[U],
+                                              unsigned lane, bool out16, bool out8) {
+  if (U % 2 == 0 && out16 && word0 + 2 * U <= n_out) {
+#pragma unroll
+    for (int p = 0; p < U / 2; ++p)
+      if (lane == static_cast<unsigned>(p))
+        store_stream4(out + word0 + 4 * p, lo[2 * p], hi[2 * p], lo[2 * p + 1], hi[2 * p + 1]);
+    return;
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const uint64_t w = word0 + 2 * u;
+    if (out8 && w + 2 <= n_out) {
+      if (lane == static_cast<unsigned>(u)) store_stream2(out + w, lo[u], hi[u]);
+    } else {
+      if (lane == 0 && w < n_out) store_stream(out + w, lo[u]);
+      if (lane == 1 && w + 1 < n_out) store_stream(out + w + 1, hi[u]);
+    }
+  }
+}
+
 __device__ __forceinline__ unsigned lane_id() {
   unsigned l;
   asm("mov.u32 %0, %%laneid;" : "=r"(l));

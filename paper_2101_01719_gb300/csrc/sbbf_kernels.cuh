@@ -286,6 +286,8 @@ __global__ void __launch_bounds__(kMaxThreads, find_min_blocks<R, S>(kLanes8, U)
   const uint64_t n_out = (n + 31) >> 5;
   const uint64_t pk = policy_evict_first();
   const uint64_t pf = policy_evict_last();
+  const bool out16 = (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+  const bool out8 = (reinterpret_cast<uintptr_t>(out) & 7) == 0;
 
   if (!kLanes8) {
     // a unit is U consecutive groups, all loads issued before any test
@@ -320,17 +322,16 @@ __global__ void __launch_bounds__(kMaxThreads, find_min_blocks<R, S>(kLanes8, U)
           }
         }
       }
+      uint32_t lo[U], hi[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const uint32_t r0 = block_has(w[u][0], static_cast<uint32_t>(h[u][0]));
         const uint32_t r1 = block_has(w[u][1], static_cast<uint32_t>(h[u][1]));
         const uint32_t v = (r0 | (r1 << 1)) << (2 * (lane & 15));
-        const uint32_t lo = __reduce_or_sync(0xFFFFFFFFu, lane < 16 ? v : 0u);
-        const uint32_t hi = __reduce_or_sync(0xFFFFFFFFu, lane >= 16 ? v : 0u);
-        const uint64_t word = 2 * (g0 + u);
-        if (lane == 0 && word < n_out) store_stream(out + word, lo);
-        if (lane == 1 && word + 1 < n_out) store_stream(out + word + 1, hi);
+        lo[u] = __reduce_or_sync(0xFFFFFFFFu, lane < 16 ? v : 0u);
+        hi[u] = __reduce_or_sync(0xFFFFFFFFu, lane >= 16 ? v : 0u);
       }
+      store_answers<U>(out, n_out, 2 * g0, lo, hi, lane, out16, out8);
     }
   } else {
     const uint32_t seed = lane_seed(lane & 7);
@@ -374,9 +375,8 @@ __global__ void __launch_bounds__(kMaxThreads, find_min_blocks<R, S>(kLanes8, U)
           hi |= (h_g2 << r) | (h_g3 << (16 + r));
         }
       }
-      const uint64_t word = 2 * g;
-      if (lane == 0 && word < n_out) store_stream(out + word, lo);
-      if (lane == 1 && word + 1 < n_out) store_stream(out + word + 1, hi);
+      const uint32_t lo1[1] = {lo}, hi1[1] = {hi};
+      store_answers<1>(out, n_out, 2 * g, lo1, hi1, lane, out16, out8);
     }
   }
   res.finish();

@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(256)
   const uint64_t pf = policy_evict_last();
   const uint64_t n_groups = (n + 63) >> 6;
   const uint64_t n_out = (n + 31) >> 5;
+  const bool out8 = (reinterpret_cast<uintptr_t>(out) & 7) == 0;
   uint64_t warp, n_warps;
   warp_span(warp, n_warps);
   for (uint64_t g = warp; g < n_groups; g += n_warps) {
@@ -119,8 +120,8 @@ __global__ void __launch_bounds__(256)
     const uint32_t v = (r0 | (r1 << 1)) << (2 * (lane & 15));
     const uint32_t lo = __reduce_or_sync(0xFFFFFFFFu, lane < 16 ? v : 0u);
     const uint32_t hi = __reduce_or_sync(0xFFFFFFFFu, lane >= 16 ? v : 0u);
-    if (lane == 0 && 2 * g < n_out) store_stream(out + 2 * g, lo);
-    if (lane == 1 && 2 * g + 1 < n_out) store_stream(out + 2 * g + 1, hi);
+    const uint32_t lo1[1] = {lo}, hi1[1] = {hi};
+    store_answers<1>(out, n_out, 2 * g, lo1, hi1, lane, false, out8);
   }
 }
 

@@ -130,8 +130,9 @@ __global__ void __launch_bounds__(256)
       const uint32_t hi = __reduce_or_sync(0xFFFFFFFFu, lane >= 16 ? v : 0u);
       const uint64_t word = (u - r_lo) * 2;
       const uint64_t n_out = (d.n + 31) >> 5;
-      if (lane == 0 && word < n_out) store_stream(d.out + word, lo);
-      if (lane == 1 && word + 1 < n_out) store_stream(d.out + word + 1, hi);
+      const uint32_t lo1[1] = {lo}, hi1[1] = {hi};
+      store_answers<1>(d.out, n_out, word, lo1, hi1, lane, false,
+                       (reinterpret_cast<uintptr_t>(d.out) & 7) == 0);
     }
   }
 }

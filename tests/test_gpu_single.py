@@ -438,6 +438,25 @@ def test_partitioned_find_equals_oracle(B, n):
     assert np.array_equal(bits_np(f.find(to_dev(q))), oracle.find(ref, B, q))
 
 
+@pytest.mark.parametrize("B,n", [(32768, 1_000_003), (3 * 2**20 - 1, 200_001), (7, 130)])
+@pytest.mark.parametrize("shift_words", [1, 2, 3])
+def test_find_into_offset_outputs(B, n, shift_words):
+    """Answers written 4, 8 or 12 bytes past a 16-byte boundary (the lookup
+    picks 16-, 8- or 4-byte stores by the output's alignment) equal the
+    oracle's, and the words on either side stay untouched."""
+    keys = inp.stream(170, 0, max(1, n // 4))
+    q = np.concatenate([inp.stream(170, 1, n - n // 8), keys[: n // 8]])
+    ref = _oracle_filter(B, keys)
+    f = sb.Filter(B)
+    f.insert(to_dev(keys))
+    w = sb.out_words(n)
+    buf = torch.full((w + shift_words + 4,), -1, dtype=torch.int32, device=dev())
+    f.find(to_dev(q), out=buf[shift_words: shift_words + w])
+    got = bits_np(buf)
+    assert np.array_equal(got[shift_words: shift_words + w], oracle.find(ref, B, q))
+    assert (got[:shift_words] == 0xFFFFFFFF).all() and (got[shift_words + w:] == 0xFFFFFFFF).all()
+
+
 def test_partition_applies_follows_the_rule():
     """sbbf_partition_applies reports the automatic rule (at least 4Mi hashes,
     a filter of at least 256 MiB, one hash per block for inserts and two for
