@@ -44,7 +44,10 @@ __global__ void __launch_bounds__(256) kA(const uint64_t* __restrict__ keys, uin
     uint32_t r[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) r[e] = test<F>(w[e], h[e]);
-    if (S == 0) { acc += r[0] + r[1] + r[2] + r[3]; continue; }
+    if constexpr (S == 0) {
+      acc += r[0] + r[1] + r[2] + r[3];
+      continue;
+    } else {
     uint32_t wd[4];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
@@ -60,6 +63,7 @@ __global__ void __launch_bounds__(256) kA(const uint64_t* __restrict__ keys, uin
       }
     } else {
       if (lane == 0) __stcs(reinterpret_cast<uint4*>(bits + 4 * c), make_uint4(wd[0], wd[1], wd[2], wd[3]));
+    }
     }
   }
   if (S == 0) { const uint32_t s = __reduce_add_sync(0xFFFFFFFFu, acc); if (lane == 0) atomicAdd(out, s); }
