@@ -604,9 +604,12 @@ __global__ void __launch_bounds__(256, 4)
   const uint64_t groups_per_tile = static_cast<uint64_t>(wpc) * rounds;
   const uint64_t keys_per_tile = groups_per_tile * 64;
   const uint64_t pk = policy_evict_first();
-  // blocks at normal priority: a slice is dropped from L2 once its keys are
-  // done, making room for the slices being prefetched
-  const uint64_t pf = policy_evict_normal();
+  // block loads at evict-last priority: the near die then keeps its copies of
+  // lines that live in the other die's memory, which halved the requests
+  // crossing the die-to-die fabric on a 2 GiB filter (50.2M against 100.8M
+  // for 128M keys) and cut the pass from 0.83 to 0.74 ms at the same DRAM
+  // reads (evict-normal loads measured 4-5% slower overall)
+  const uint64_t pf = policy_evict_last();
   uint64_t ahead = 0;
   if (wic == 0) {
     ahead = prefetch_ahead(offsets, n_slices, keys_per_tile * gridDim.x);
