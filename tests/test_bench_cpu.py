@@ -63,3 +63,25 @@ def test_bench_uses_no_undefined_names():
             if used - scope:
                 missing[node.name] = sorted(used - scope)
     assert not missing, missing
+
+
+def test_step_kernel_counts():
+    """gpu_launches: a step launches the clear, one kernel per unpartitioned
+    batch, four per partitioned insert batch and five per 2^31-key piece of a
+    partitioned lookup, plus one hashing kernel per partitioned batch of raw
+    keys."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class FakeFilter:
+        def __init__(self, ins, look):
+            self.ins, self.look = ins, look
+
+        def partition_applies(self, n, lookup=False):
+            return self.look if lookup else self.ins
+
+    assert bench.step_kernels(FakeFilter(False, False), [(0, 10)], 100, False) == 3
+    assert bench.step_kernels(FakeFilter(False, False), [(0, 10), (10, 5)], 100, True) == 4
+    assert bench.step_kernels(FakeFilter(True, True), [(0, 10), (10, 5)], 100, False) == 1 + 8 + 5
+    assert bench.step_kernels(FakeFilter(True, False), [(0, 10)], 100, True) == 1 + 5 + 1
+    assert bench.step_kernels(FakeFilter(False, True), [(0, 10)], 2**31 + 1, True) == 1 + 1 + 10 + 1
