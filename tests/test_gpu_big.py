@@ -16,7 +16,7 @@ import oracle
 import paper_2101_01719_gb300 as sb
 from paper_2101_01719_gb300 import workloads as wl
 import sbbf_inputs as inp
-from gpu_util import bit_at, bits_np, dev, to_dev
+from gpu_util import bit_at, bits_np, dev, to_dev, u64_np
 
 pytestmark = pytest.mark.gpu
 
@@ -119,4 +119,35 @@ def test_partitioned_paths_with_small_scatter_tiles(slices):
     tail = np.unpackbits(part.view(np.uint8), bitorder="little")[n: n + n // 4]
     assert tail.all()
     del f
+    torch.cuda.empty_cache()
+
+
+def test_partitioned_lookup_over_two_billion_keys():
+    """A partitioned lookup of 2^31 + 4103 hashes runs in two pieces (the
+    scatter's positions are 32-bit): every answer equals the unpartitioned
+    lookup's, and the answers on both sides of the piece boundary and at
+    sampled positions equal the oracle's."""
+    B, n = 2**23 + 5, 2**31 + 4103
+    keys = inp.stream(180, 0, 4_000_000)
+    ref = oracle.new_filter(B)
+    oracle.insert_mt(ref, B, keys, oracle.num_cores())
+    f = sb.Filter(B)
+    f.words.copy_(torch.from_numpy(ref.view(np.int32)).to(dev()))
+    q = sb.fill_splitmix64(torch.empty(n, dtype=torch.int64, device=dev()),
+                           inp.stream_seed(180, 1))
+    dk = to_dev(keys)
+    q[: 509 * keys.size: 509] = dk                # members spread over the first piece
+    q[2**31 - 2000: 2**31 + 2000] = dk[:4000]     # and across the boundary
+    f.set_partitioning(sb.PARTITION_ON)
+    part = f.find(q)
+    f.set_partitioning(sb.PARTITION_OFF)
+    assert torch.equal(part, f.find(q))
+    pos = np.concatenate([np.arange(2**31 - 3000, 2**31 + 3000),
+                          np.random.default_rng(180).integers(0, n, 20000), [n - 1]])
+    hq = u64_np(q[torch.from_numpy(pos).to(dev())])
+    exp = oracle.find(ref, B, hq)
+    got = bit_at(bits_np(part), pos)
+    assert np.array_equal(got, bit_at(exp, np.arange(pos.size)))
+    assert got[1000:5000].all()                   # the members across the boundary
+    del q, part
     torch.cuda.empty_cache()
