@@ -142,10 +142,11 @@ sbbf_status sbbf_insert_hashes(sbbf_t *f, const uint64_t *d_hashes, size_t n,
                                sbbf_stream_t stream);
 
 /* How sbbf_insert_hashes and sbbf_find_hashes process a batch.
- * Partitioned: the hashes are first grouped by filter slice (2^20
- * consecutive blocks) into a scratch buffer, then processed slice by slice
- * with each slice prefetched into L2, which turns random DRAM accesses into
- * L2 hits for filters larger than L2.  Results are identical either way
+ * Partitioned: the hashes are first grouped by filter slice (2^17 to 2^20
+ * consecutive blocks, 4 to 32 MiB) into a scratch buffer, then processed
+ * slice by slice with each slice prefetched into L2, which turns random DRAM
+ * accesses into L2 hits for filters larger than L2; a lookup's answers are
+ * then moved back to the hashes' order.  Results are identical either way
  * (inserts commute; a lookup's answer is set at its original position).  The
  * scratch -- 8 bytes per hash for inserts, 10.125 for lookups (at most 2^31
  * hashes at a time), plus per slice 12 bytes per SM and, for lookups, 4
