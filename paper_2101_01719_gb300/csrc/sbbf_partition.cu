@@ -330,9 +330,9 @@ __host__ __device__ constexpr size_t scatter_smem_bytes(uint32_t tile, uint32_t 
 // tile t is processed.  The copies need a 16-byte aligned key array; with
 // any other alignment, or if a copy ever failed to complete in time, the
 // CTA reads the keys straight from global memory instead.  Lookups (kIndex)
-// also write each key's original position, and the cursors at every
-// sub-range start (and after the last tile) to marks[c][u][q], `rows` rows
-// per CTA.
+// also write each key's original position, as its 16-bit offset within its
+// sub-range, and the cursors at every sub-range start (and after the last
+// tile) to marks[c][u][q], `rows` rows per CTA.
 template <bool kFew, bool kIndex, uint32_t kT>
 __global__ void __launch_bounds__(kPartThreads, 1)
     scatter_kernel(const uint64_t* __restrict__ hashes, uint64_t n, uint32_t nb, int shift,
@@ -670,8 +670,8 @@ __global__ void __launch_bounds__(256, 4)
 // [marks[c][u][q], marks[c][u + 1][q]).  The CTA lists the answer words that
 // overlap these runs (shared memory holds each run's bounds and the list
 // offset of its first word); a lane takes one word, masks it to its run, and
-// for each found key -- each set bit -- loads the key's original position
-// and sets its bit in a shared-memory copy of the sub-range's result words,
+// for each found key -- each set bit -- loads the key's offset within the
+// sub-range and sets its bit in a shared-memory copy of the sub-range's result words,
 // four bits per round so that their loads overlap.  The words are then
 // stored whole: every result word belongs to exactly one CTA, so there are
 // no global atomics and no zeroing pass.  Positions and runs are clamped to
@@ -809,8 +809,8 @@ constexpr double kLiveBytes = 48.0 * 1024 * 1024;
 // Slice shift, grid and tile rounds of a partitioned lookup of n keys.  A
 // slice's blocks stay in L2 from its prefetch until its last key is
 // processed, so a slice plus the keys in flight (and those prefetched ahead)
-// must fit there, while the scatter of 4-byte positions pays for every extra
-// slice: lookups take the largest slice (at most 32 MiB, no smaller than
+// must fit there, while the scatter of positions pays for every extra slice
+// (shorter runs): lookups take the largest slice (at most 32 MiB, no smaller than
 // lookup_min_shift) within the live-set budget.  When even that slice leaves
 // too little room -- sparse batches, many filter bytes per key -- the grid
 // shrinks (to one CTA per SM at least) until the window fits beside it.
@@ -869,7 +869,8 @@ uint64_t partition_scratch_bytes(uint32_t num_blocks, uint64_t n, bool with_inde
   return bytes;
 }
 
-// Largest batch a partitioned lookup handles in one pass (32-bit positions).
+// Largest batch a partitioned lookup handles in one pass (32-bit sorted
+// positions in the scatter's cursors and marks).
 constexpr uint64_t kMaxIndexedKeys = 1ull << 31;
 
 namespace {
