@@ -536,6 +536,18 @@ sbbf_status wait_ticket(sbbf_server_t* s, std::unique_lock<std::mutex>& lk, uint
 
 }  // namespace
 
+namespace {
+
+// Makes room for one more element ahead of the push_back, so that the push
+// cannot throw after other state changed; the capacity grows geometrically
+// (a bare reserve(size() + 1) reallocates and copies on every call).
+template <class V>
+void reserve_one_more(V& v) {
+  if (v.size() == v.capacity()) v.reserve(v.capacity() ? 2 * v.capacity() : 64);
+}
+
+}  // namespace
+
 extern "C" {
 
 sbbf_status sbbf_server_create(const sbbf_server_config_t* cfg, sbbf_server_t** out) {
@@ -597,8 +609,8 @@ sbbf_status sbbf_server_add_filter(sbbf_server_t* s, uint32_t num_blocks, uint32
     std::lock_guard<std::mutex> lk(s->mu);
     FilterState f;
     f.num_blocks = num_blocks;
-    s->filters.reserve(s->filters.size() + 1);
-    s->queues.reserve(s->queues.size() + 1);
+    reserve_one_more(s->filters);
+    reserve_one_more(s->queues);
     s->filters.push_back(f);
     s->queues.emplace_back();
     *id = static_cast<uint32_t>(s->filters.size() - 1);
@@ -627,8 +639,8 @@ sbbf_status sbbf_server_submit(sbbf_server_t* s, const sbbf_request_t* r, uint64
       if (s->filters[r->filter].bytes() + p.dev_bytes > s->cfg.budget_bytes) return SBBF_EBUSY;
       p.ticket = s->done_ns.size();
       // every step that can throw comes before the first change of state
-      s->done_ns.reserve(p.ticket + 1);
-      s->status.reserve(p.ticket + 1);
+      reserve_one_more(s->done_ns);
+      reserve_one_more(s->status);
       if (r->n > 0) {
         std::deque<Pending>& q = s->queues[r->filter];
         const bool was_empty = q.empty();

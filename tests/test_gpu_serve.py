@@ -199,3 +199,23 @@ class _View:
 
     def numel(self):
         return self._n
+
+
+def test_submits_take_amortised_constant_time():
+    """400,000 requests through one server (empty ones, done at submission,
+    no GPU work) replay in well under a second: the per-ticket tables grow
+    geometrically.  Growing them by one element per request copies the whole
+    table every time, which took minutes here and, in the full serving
+    workload, made throughput fall with every request served."""
+    import time
+    srv = sb.Server(1 << 20)
+    f = srv.add_filter(64)
+    n = 400_000
+    rec = np.zeros(n, dtype=sb.REQUEST_DTYPE)
+    rec["op"], rec["filter"], rec["n"] = sb.OP_INSERT, f, 0
+    t0 = time.perf_counter()
+    lat = srv.replay(rec, np.zeros(n, np.uint64))
+    elapsed = time.perf_counter() - t0
+    srv.close()
+    assert lat.size == n
+    assert elapsed < 5.0, elapsed
