@@ -214,7 +214,12 @@ sbbf_status sbbf_multi_create(const uint32_t* h_num_blocks, uint32_t n_filters, 
     m->device = current_device();
     m->tune_find_seg = m->tune_find_tag = kDefaultFind;
     m->tune_insert_seg = m->tune_insert_tag = kDefaultInsert;
-    m->h_dir.resize(n_filters);
+    try {
+      m->h_dir.resize(n_filters);
+    } catch (...) {
+      delete m;  // nothing on the device yet
+      throw;
+    }
     uint64_t base = 0;
     for (uint32_t t = 0; t < n_filters; ++t) {
       m->h_dir[t] = FilterRef{base, h_num_blocks[t], 0};
