@@ -103,7 +103,7 @@ sbbf_status launch_find_partitioned(const uint32_t* words, uint32_t num_blocks,
                                     void* scratch, cudaStream_t s);
 // True when a batch of n keys should take the partitioned path (the filter's
 // mode, its size, and at least min_keys_per_block keys per block).
-bool want_partition(const sbbf_filter* f, uint64_t n, uint64_t min_keys_per_block);
+bool want_partition(const sbbf_filter* f, uint64_t n);
 // Grows the filter's scratch (cudaMalloc, synchronous) to at least `bytes`.
 sbbf_status ensure_scratch(sbbf_filter* f, size_t bytes);
 

@@ -1025,6 +1025,7 @@ sbbf_status launch_find_partitioned(const uint32_t* words, uint32_t num_blocks,
 
 sbbf_status sbbf_partition_applies(const sbbf_t* f, size_t n, int lookup, int* applies) {
   if (!f || !applies) return SBBF_EINVAL;
-  *applies = sbbf::want_partition(f, n, lookup ? 2 : 1) ? 1 : 0;
+  (void)lookup;  // the same rule for inserts and lookups
+  *applies = sbbf::want_partition(f, n) ? 1 : 0;
   return SBBF_OK;
 }

@@ -100,17 +100,18 @@ sbbf_status launch_find_filter(const sbbf_t* f, const uint64_t* d_hashes, uint64
 constexpr uint64_t kPartitionMinKeys = 4ull << 20;
 constexpr uint64_t kPartitionMinBytes = 256ull << 20;
 
-// Automatic mode also wants enough keys per block: a partitioned pass reads
-// every block of the filter once (the slice prefetch), so it pays only when
-// the batch touches each block about once (inserts: >= 1 key per block; a
-// 3e9-key batch into 2^30 blocks runs 2.3x faster) or more (lookups: >= 2;
-// 1e9 lookups into 128.9M blocks run 1.8x faster, into 2^30 blocks 9% slower).
-bool want_partition(const sbbf_t* f, uint64_t n, uint64_t min_keys_per_block) {
+// Automatic mode also wants at least one key per block: a partitioned pass
+// reads every block of the filter once (the slice prefetch), so it pays only
+// when the batch touches each block about once or more.  Measured: 3e9
+// inserts into 2^30 blocks run 2.3x faster partitioned; lookups 2.1x faster
+// at 2 keys per block (2^26 blocks), 2.4x at 7.8 (128.9M blocks) and still
+// 1.12x at 0.93 (1e9 into 2^30 blocks).
+bool want_partition(const sbbf_t* f, uint64_t n) {
   if (f->lanes != 8 || f->partition_mode == SBBF_PARTITION_OFF) return false;
   if (f->partition_mode == SBBF_PARTITION_ON) return true;
   return n >= kPartitionMinKeys &&
          static_cast<uint64_t>(f->num_blocks) * 32 >= kPartitionMinBytes &&
-         n >= min_keys_per_block * f->num_blocks;
+         n >= f->num_blocks;
 }
 
 // Grows the filter's scratch (cudaMalloc, synchronous) to hold `bytes`.
@@ -242,7 +243,7 @@ sbbf_status sbbf_insert_hashes(sbbf_t* f, const uint64_t* d_hashes, size_t n,
   if (!f || !on_device(f)) return SBBF_EINVAL;
   if (n == 0) return SBBF_OK;
   if (!d_hashes || (reinterpret_cast<uintptr_t>(d_hashes) & 7)) return SBBF_EINVAL;
-  if (want_partition(f, n, 1)) {
+  if (want_partition(f, n)) {
     const sbbf_status st = ensure_scratch(f, partition_scratch_bytes(f->num_blocks, n, false));
     if (st == SBBF_OK)
       return launch_insert_partitioned(f->words, f->num_blocks, d_hashes, n, f->scratch, stream);
@@ -268,7 +269,7 @@ sbbf_status sbbf_find_hashes(const sbbf_t* f, const uint64_t* d_hashes, size_t n
   if (!d_hashes || !d_out_bits || (reinterpret_cast<uintptr_t>(d_hashes) & 7) ||
       (reinterpret_cast<uintptr_t>(d_out_bits) & 3))
     return SBBF_EINVAL;
-  if (want_partition(f, n, 2)) {
+  if (want_partition(f, n)) {
     const uint64_t piece = n < (1ull << 31) ? n : (1ull << 31);
     const sbbf_status st =
         ensure_scratch(const_cast<sbbf_t*>(f), partition_scratch_bytes(f->num_blocks, piece, true));

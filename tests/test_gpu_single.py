@@ -459,11 +459,11 @@ def test_find_into_offset_outputs(B, n, shift_words):
 
 def test_partition_applies_follows_the_rule():
     """sbbf_partition_applies reports the automatic rule (at least 4Mi hashes,
-    a filter of at least 256 MiB, one hash per block for inserts and two for
-    lookups) and the forced modes."""
+    a filter of at least 256 MiB, one hash per block) and the forced modes."""
     f = sb.Filter(2**23)  # 256 MiB
     assert f.partition_applies(2**23) and not f.partition_applies(2**23 - 1)
-    assert not f.partition_applies(2**23, lookup=True) and f.partition_applies(2**24, lookup=True)
+    assert f.partition_applies(2**23, lookup=True)
+    assert not f.partition_applies(2**23 - 1, lookup=True)
     assert not sb.Filter(2**23 - 1).partition_applies(2**26)
     f.set_partitioning(sb.PARTITION_OFF)
     assert not f.partition_applies(2**30) and not f.partition_applies(2**30, lookup=True)
