@@ -671,9 +671,9 @@ __global__ void __launch_bounds__(256, 4)
 // overlap these runs (shared memory holds each run's bounds and the list
 // offset of its first word); a lane takes one word, masks it to its run, and
 // for each found key -- each set bit -- loads the key's offset within the
-// sub-range and sets its bit in a shared-memory copy of the sub-range's result words,
-// four bits per round so that their loads overlap.  The words are then
-// stored whole: every result word belongs to exactly one CTA, so there are
+// sub-range and sets its bit in a shared-memory copy of the sub-range's
+// result words, four bits per round so that their loads overlap.  The words
+// are then stored whole: every result word belongs to exactly one CTA, so there are
 // no global atomics and no zeroing pass.  Positions and runs are clamped to
 // their buffers, so keys that changed between the passes give wrong answers,
 // never an access out of bounds.
