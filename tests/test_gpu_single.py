@@ -457,6 +457,30 @@ def test_find_into_offset_outputs(B, n, shift_words):
     assert (got[:shift_words] == 0xFFFFFFFF).all() and (got[shift_words + w:] == 0xFFFFFFFF).all()
 
 
+@pytest.mark.parametrize("bits_per_key", [5, 8, 10.5, 12.8])
+def test_bits_per_key_sweep(bits_per_key):
+    """The sweep of the L2-resident configuration: 1M hashes at 5, 8, 10.5
+    and 12.8 bits per key (19,532 / 31,250 / 41,016 / 50,000 blocks).  The
+    filter words and the answers for 2M fresh hashes equal the oracle's, and
+    the false-positive count lies in the binomial interval of the paper's
+    Poisson sum."""
+    n, q = 1_000_000, 2_000_000
+    B = int(np.ceil(n * bits_per_key / 256))
+    keys = inp.stream(190, 0, n)
+    fresh = inp.stream(190, 1, q)
+    f = sb.Filter(B)
+    f.insert(to_dev(keys))
+    ref = oracle.new_filter(B)
+    oracle.insert_mt(ref, B, keys, oracle.num_cores())
+    assert np.array_equal(f.to_numpy(), ref)
+    got = bits_np(f.find(to_dev(fresh)))
+    exp, _ = oracle.find_mt(ref, B, fresh, oracle.num_cores())
+    assert np.array_equal(got, exp)
+    fp = int(np.unpackbits(got.view(np.uint8)).sum())
+    p = oracle.fpr_poisson(n / B)
+    assert abs(fp / q - p) <= 5 * np.sqrt(p * (1 - p) / q) + 0.02 * p, (fp / q, p)
+
+
 def test_partition_applies_follows_the_rule():
     """sbbf_partition_applies reports the automatic rule (at least 4Mi hashes,
     a filter of at least 256 MiB, one hash per block) and the forced modes."""
