@@ -36,8 +36,8 @@ DOMINANT_KERNEL = "find_kernel"
 # hash read once plus its 1/8-byte share of the packed result.
 LOOKUP_HBM_BYTES_L2_RESIDENT = 8.0 + 1.0 / 8.0
 # Measured ceilings of random 32-byte block reads on GB300 (the random-sector
-# microbenchmark, paper_2101_01719_gb300/microbench/random_sector.cu and
-# tma_gather.cu): blocks resident in L2, and blocks in HBM (where every
+# microbenchmark, paper_2101_01719_gb300/microbench/random_sector.cu):
+# blocks resident in L2, and blocks in HBM (where every
 # random block costs about 128 bytes of DRAM traffic).
 RANDOM_BLOCK_CEILING_L2 = 293.0   # G blocks/s
 RANDOM_BLOCK_CEILING_HBM = 40.8   # G blocks/s

@@ -22,6 +22,7 @@
 #include "sbbf.h"
 #include "sbbf_host.cuh"
 #include "sbbf_kernels.cuh"
+#include "sbbf_launch.cuh"
 
 namespace sbbf {
 namespace {
@@ -162,14 +163,7 @@ extern "C" sbbf_status sbbf_multi_find_noalloc(const uint32_t* d_arena,
   if (st != SBBF_OK) return st;
   if (n > 0) {
     auto kernel = find_kernel<TaggedDeviceDir, false, 2, false>;
-    static const int occ = [] {
-      int v = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, find_kernel<TaggedDeviceDir, false, 2, false>,
-                                                        256, 0) != cudaSuccess ||
-          v < 1)
-        v = 1;
-      return v;
-    }();
+    const int occ = cached_occupancy(reinterpret_cast<const void*>(kernel), 256);
     const uint64_t groups = (n + 63) / 64;
     const TaggedDeviceDir res{d_ids, dir, n_filters, counter, 0};
     kernel<<<grid_for(groups, (256 / 32) * 2, occ), 256, 0, stream>>>(d_arena, res, d_hashes, n,

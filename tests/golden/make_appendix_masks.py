@@ -18,7 +18,7 @@ import subprocess
 import sys
 import tempfile
 
-PAPER = os.environ.get("SBBF_PAPER_TEX", "/root/reference/PAPER.md")
+PAPER = os.environ.get("SBBF_PAPER_TEX")  # path of the paper's source text; no default
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 # Driver written for this harness: reads "B n_ins n_q" then n_ins + n_q
@@ -55,6 +55,8 @@ int main(void) {
 
 def available() -> str | None:
     """None when the cross-check can run here, else the reason it cannot."""
+    if not PAPER:
+        return "paper source not configured (set SBBF_PAPER_TEX)"
     if not os.path.exists(PAPER):
         return "paper source not present"
     try:
