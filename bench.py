@@ -3,11 +3,14 @@
 One step = one pass of the hot path over one batch of the workload: clear the
 filter, insert the batch of hashes (appendix add_hash for each), look up the
 batch of queries (appendix find_hash for each, packed bitmask out).  The
-default workload is 1M hashes into a 32768-block (1 MiB) filter and 256M
-lookups, half of them members (the paper's 1M-element size with a lookup
-batch far larger than L2).  Inputs are seeded splitmix64 streams generated on
-the device before the timed region; the lookup stream (2 GiB) is larger than
-L2, so no flush is needed between steps.
+default workload is the paper's largest size: 100M hashes into a
+4,194,304-block (134,217,728 B, HBM-resident) filter in 16M batches, then 1e9
+lookups with 10% members.  Inputs are seeded splitmix64 streams generated on
+the device before the timed region; the lookup stream (8 GB) is far larger
+than L2, so no flush is needed between steps.  The line's ``rows`` add the
+other single-filter sizes, each timed the same way: 3e9 hashes at 11
+bits/key (4.1 GB) and into 2^30 blocks (32 GiB), each with 1e9 lookups, and
+the L2-resident 1 MiB filter with 256M lookups.
 
 Prints one JSON line.  ``--impl reference`` times the CPU oracle instead (a
 bounded sample of the same workload on the host cores).
@@ -32,6 +35,7 @@ METRIC = "SBBF insert/lookup Gkeys/s"
 UNIT = "Gkeys/s"
 FALLBACK_HBM_GBS = 6800.0
 DOMINANT_KERNEL = "find_kernel"
+DEFAULT_WORKLOAD = "sbbf_4194304blk_100M_ins_1G_lookup"
 # Algorithmic HBM bytes per lookup with an L2-resident filter: the 8-byte
 # hash read once plus its 1/8-byte share of the packed result.
 LOOKUP_HBM_BYTES_L2_RESIDENT = 8.0 + 1.0 / 8.0
@@ -52,10 +56,14 @@ INSERT_HBM_BYTES_HBM_RESIDENT = 8.0 + 32.0 + 32.0
 def parse_args(argv=None):
     p = argparse.ArgumentParser(description=__doc__)
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=600)
+    p.add_argument("--steps", type=int, default=300)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", default="sbbf_32768blk_1M_ins_256M_lookup")
+    p.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    p.add_argument("--rows", choices=["auto", "none"], default="auto",
+                   help="auto: with the default workload, also time the 11 bits/key, 32 GiB "
+                        "and 1 MiB filters as rows of the line")
+    p.add_argument("--row-steps", type=int, default=5)
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="approximate CPU work for the oracle baseline")
@@ -237,6 +245,106 @@ def profiled_traffic(workload: str):
     return None
 
 
+# ---- the workload's config dict (identical in both arms) ----------------------
+
+ROW_WORKLOADS = ("sbbf_128906250blk_3G_ins_1G_lookup", "sbbf_2^30blk_3G_ins_1G_lookup",
+                 "sbbf_32768blk_1M_ins_256M_lookup")
+
+
+def workload_config(w, world: int, lanes: int = 8, keys: str = "hashes") -> dict:
+    """What the line measures: the workload, its sizes and the layout of the
+    run -- the same dict from our arm and the oracle's, so that the two lines
+    compare like for like."""
+    return {"workload": w.name, "num_blocks": w.num_blocks * 8 // lanes, "lanes": lanes,
+            "keys": ("64-bit hashes" if keys == "hashes"
+                     else "%s keys, XXH64 in the kernels" % keys),
+            "filter_bytes": w.filter_bytes, "n_insert": w.n_insert,
+            "insert_batch": w.insert_batch, "n_lookup": w.n_lookup,
+            "member_frac": w.member_frac,
+            "l2": "inputs larger than L2 (%.1f GiB lookup stream per step)"
+                  % (8 * w.n_lookup / 2**30),
+            "parallelism": "independent replicas, lookups sharded by rank"
+                           if world > 1 else "single GPU"}
+
+
+def bytes_per_lookup(w, l2_bytes: int) -> float:
+    """Algorithmic HBM bytes per lookup: the hash and its result bit, plus the
+    32-byte block when the filter does not stay in L2."""
+    l2_resident = w.filter_bytes < l2_bytes / 2
+    return LOOKUP_HBM_BYTES_L2_RESIDENT if l2_resident else LOOKUP_HBM_BYTES_HBM_RESIDENT
+
+
+def bytes_per_insert(w, l2_bytes: int) -> float:
+    l2_resident = w.filter_bytes < l2_bytes / 2
+    return INSERT_HBM_BYTES_L2_RESIDENT if l2_resident else INSERT_HBM_BYTES_HBM_RESIDENT
+
+
+def measure_row(name: str, dev, stream, peak: float, l2_bytes: int, steps: int,
+                partition_lookups=("auto",)) -> dict:
+    """One single-filter workload timed on its own: build the inputs on the
+    device, warm up, then time `steps` repetitions of all its insert batches
+    (after a clear) and of its lookup batch with CUDA events on the launching
+    stream; the lookup is timed once per partitioning mode listed.  Members
+    must hit (checked on the last answers)."""
+    import torch
+
+    import paper_2101_01719_gb300 as sb
+    from paper_2101_01719_gb300 import workloads as wl
+
+    w = wl.WORKLOADS[name]
+    f = sb.Filter(w.num_blocks, device=dev)
+    ins = wl.gen_inserts(w, 0, w.n_insert, device=dev)
+    qry = wl.gen_queries(w, 0, w.n_lookup, device=dev)
+    out = torch.empty(sb.out_words(w.n_lookup), dtype=torch.int32, device=dev)
+    batches = [(s0, min(w.insert_batch, w.n_insert - s0))
+               for s0 in range(0, w.n_insert, w.insert_batch)]
+
+    def insert_all():
+        f.clear()
+        for s0, cnt in batches:
+            f.insert(ins[s0:s0 + cnt])
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / steps
+
+    insert_ms = timed(insert_all)
+    row = {"filter_bytes": w.filter_bytes, "n_insert": w.n_insert, "n_lookup": w.n_lookup,
+           "insert_partitioned": f.partition_applies(batches[0][1]),
+           "insert_gkeys_s": round(w.n_insert / (insert_ms / 1e3) / 1e9, 3),
+           "insert_ms": round(insert_ms, 4)}
+    ib = bytes_per_insert(w, l2_bytes)
+    row["insert_roofline"] = {"bytes_per_key": ib,
+                              "frac": round(ib * w.n_insert / (insert_ms / 1e3) / 1e9 / peak, 4)}
+    lb = bytes_per_lookup(w, l2_bytes)
+    row["lookup"] = {}
+    modes = {"auto": sb.PARTITION_AUTO, "on": sb.PARTITION_ON, "off": sb.PARTITION_OFF}
+    for mode in partition_lookups:
+        f.set_partitioning(modes[mode])
+        find_ms = timed(lambda: f.find(qry, out=out))
+        hits = int(sb.count_bits(out, w.n_lookup).item())
+        row["lookup"][mode] = {
+            "partitioned": f.partition_applies(w.n_lookup, lookup=True),
+            "gkeys_s": round(w.n_lookup / (find_ms / 1e3) / 1e9, 3),
+            "ms": round(find_ms, 4), "bytes_per_key": lb,
+            "roofline_frac": round(lb * w.n_lookup / (find_ms / 1e3) / 1e9 / peak, 4),
+            "hit_frac": round(hits / w.n_lookup, 5)}
+    f.set_partitioning(sb.PARTITION_AUTO)
+    del f, ins, qry, out
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return row
+
+
 # ---- our arm ----------------------------------------------------------------
 
 def run_ours(args):
@@ -405,36 +513,43 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     l2_bytes = props.L2_cache_size if hasattr(props, "L2_cache_size") else 126 * 2**20
     l2_resident = w.filter_bytes < l2_bytes / 2
-    per_key = LOOKUP_HBM_BYTES_L2_RESIDENT if l2_resident else LOOKUP_HBM_BYTES_HBM_RESIDENT
+    per_key = bytes_per_lookup(w, l2_bytes)
     key_bytes_less = 4 if args.keys == "u32" else 0  # 4-byte keys instead of 8-byte hashes
     per_key -= key_bytes_less
     achieved = per_key * w.n_lookup / (find_ms / 1e3) / 1e9
-    ins_per_key = INSERT_HBM_BYTES_L2_RESIDENT if l2_resident else INSERT_HBM_BYTES_HBM_RESIDENT
+    ins_per_key = bytes_per_insert(w, l2_bytes)
     ins_per_key -= key_bytes_less
     ins_achieved = ins_per_key * w.n_insert / (insert_ms / 1e3) / 1e9
     traffic = None if variant else profiled_traffic(w.name)
     clocks = sampler.summary()
+    partitioned = {"insert": f.partition_applies(batches[0][1]),
+                   "lookup": f.partition_applies(w.n_lookup, lookup=True)}
+    step_kernels_n = step_kernels(f, batches, w.n_lookup, args.keys != "hashes")
 
+    rows_extra = {}
+    if args.rows == "auto" and not variant and args.workload == DEFAULT_WORKLOAD:
+        # free the main workload's device memory (graphs, filter, inputs) first
+        graphs.clear()
+        do_insert = do_find = None
+        del f, ins, qry, out
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        for name in ROW_WORKLOADS:
+            big = wl.WORKLOADS[name].filter_bytes > (1 << 31)
+            rows_extra[name] = measure_row(name, dev, stream, peak, l2_bytes, args.row_steps,
+                                           ("auto", "on") if big else ("auto",))
     if rank != 0:
         return None
+    config = workload_config(w, world, args.lanes, args.keys)
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": max(args.warmup, 3),
         "ms_per_step": round(slowest_ms / args.steps, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (seeded splitmix64 hashes generated on the device)",
-        "config": {"workload": w.name, "num_blocks": num_blocks, "lanes": args.lanes,
-                   "keys": ("64-bit hashes" if args.keys == "hashes"
-                            else "%s keys, XXH64 in the kernels" % args.keys),
-                   "filter_bytes": w.filter_bytes, "n_insert": w.n_insert,
-                   "partitioned": {"insert": f.partition_applies(batches[0][1]),
-                                   "lookup": f.partition_applies(w.n_lookup, lookup=True)},
-                   "launch": "eager" if args.eager else "CUDA graph of the step",
-                   "n_lookup": w.n_lookup, "member_frac": w.member_frac,
-                   "l2": "inputs larger than L2 (%.1f GiB lookup stream per step)"
-                         % (8 * w.n_lookup / 2**30),
-                   "parallelism": "independent replicas, lookups sharded by rank"
-                                  if world > 1 else "single GPU"},
+        "config": config,
+        "path": {"partitioned": partitioned,
+                 "launch": "eager" if args.eager else "CUDA graph of the step"},
         "roofline": {"bound": "hbm", "kernel": DOMINANT_KERNEL,
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
@@ -455,9 +570,10 @@ def run_ours(args):
         "rows": {"insert_gkeys_s": round(w.n_insert / (insert_ms / 1e3) / 1e9, 3),
                  "lookup_gkeys_s": round(w.n_lookup / (find_ms / 1e3) / 1e9, 3),
                  "insert_ms": round(insert_ms, 5), "lookup_ms": round(find_ms, 5),
-                 "lookup_hits": hits, "lookup_hit_frac": round(hits / w.n_lookup, 5)},
+                 "lookup_hits": hits, "lookup_hit_frac": round(hits / w.n_lookup, 5),
+                 **rows_extra},
         "e2e": e2e,
-        "gpu_launches": step_kernels(f, batches, w.n_lookup, args.keys != "hashes") * args.steps,
+        "gpu_launches": step_kernels_n * args.steps,
         "clocks": clocks,
     }
     if variant:
@@ -750,9 +866,7 @@ def run_reference(args):
             "ms_per_step": round(1e3 * elapsed / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic (seeded splitmix64 hashes)",
-            "config": {"workload": w.name, "num_blocks": w.num_blocks, "lanes": 8,
-                       "keys": "64-bit hashes", "n_insert": w.n_insert, "n_lookup": w.n_lookup,
-                       "member_frac": w.member_frac},
+            "config": workload_config(w, world),
             "cpu_baseline": {"value": cb["value"], "unit": UNIT, "cores": cb["cores"],
                              "kind": "oracle", "sample": cb["sample"]},
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,

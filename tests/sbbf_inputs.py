@@ -169,3 +169,93 @@ def segment_queries(cfg: int, ins_off: np.ndarray, q_off: np.ndarray, frac: floa
     out = fresh.copy()
     out[member] = _splitmix64_at(np.uint64(stream_seed(cfg, ROLE_INSERT)), idx[member])
     return out
+
+
+# ---- native, threaded generation for billions of hashes ------------------------
+#
+# sbbf_inputs_native.c produces the same streams (pinned against the numpy
+# functions above by tests/test_inputs_native.py); it is compiled with gcc on
+# first use into tests/libsbbf_inputs.so.
+
+import ctypes as _c
+import os as _os
+import subprocess as _sp
+import threading as _th
+
+_HERE = _os.path.dirname(_os.path.abspath(__file__))
+_NSRC = _os.path.join(_HERE, "sbbf_inputs_native.c")
+_NLIB = _os.path.join(_HERE, "libsbbf_inputs.so")
+_nlib = None
+_nlock = _th.Lock()
+
+
+def _native():
+    global _nlib
+    with _nlock:
+        if _nlib is None:
+            if (not _os.path.exists(_NLIB)
+                    or _os.path.getmtime(_NLIB) < _os.path.getmtime(_NSRC)):
+                tmp = _NLIB + ".tmp.%d" % _os.getpid()
+                _sp.run(["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-Wall", "-o", tmp,
+                         _NSRC, "-lpthread"], check=True)
+                _os.replace(tmp, _NLIB)
+            L = _c.CDLL(_NLIB)
+            u64, sz, i32, u32 = _c.c_uint64, _c.c_size_t, _c.c_int, _c.c_uint32
+            P64 = _c.POINTER(_c.c_uint64)
+            PI64 = _c.POINTER(_c.c_int64)
+            L.sin_fill.argtypes = [u64, u64, sz, P64, i32]
+            L.sin_fill.restype = i32
+            L.sin_workload_queries.argtypes = [u64, u64, u64, u64, u64, u64, u64, sz, P64, i32]
+            L.sin_workload_queries.restype = i32
+            L.sin_segment_queries.argtypes = [u64, u64, u64, u64, PI64, PI64, u32, u32, P64, i32]
+            L.sin_segment_queries.restype = i32
+            _nlib = L
+    return _nlib
+
+
+def _threads(threads):
+    return threads or (_os.cpu_count() or 1)
+
+
+def _p64(a):
+    return a.ctypes.data_as(_c.POINTER(_c.c_uint64))
+
+
+def fast_splitmix64(seed: int, start: int, n: int, threads: int = 0) -> np.ndarray:
+    """splitmix64(seed, start, n), generated natively on several threads."""
+    out = np.empty(n, np.uint64)
+    if n:
+        _native().sin_fill(seed, start, n, _p64(out), _threads(threads))
+    return out
+
+
+def fast_stream(cfg: int, role: int, n: int, start: int = 0, threads: int = 0) -> np.ndarray:
+    return fast_splitmix64(stream_seed(cfg, role), start, n, threads)
+
+
+def fast_workload_queries(cfg: int, n_inserted: int, frac: float, prefix: int, start: int,
+                          n: int, threads: int = 0) -> np.ndarray:
+    """workload_queries(...), generated natively on several threads."""
+    out = np.empty(n, np.uint64)
+    if n:
+        _native().sin_workload_queries(
+            stream_seed(cfg, ROLE_INSERT), stream_seed(cfg, ROLE_FRESH),
+            stream_seed(cfg, ROLE_MEMBER), member_threshold(frac), n_inserted, prefix, start, n,
+            _p64(out), _threads(threads))
+    return out
+
+
+def fast_segment_queries(cfg: int, ins_off: np.ndarray, q_off: np.ndarray, frac: float,
+                         t0: int, t1: int, threads: int = 0) -> np.ndarray:
+    """Lookups of filters t0..t1-1 (segment_queries of each, concatenated)."""
+    ins_off = np.ascontiguousarray(ins_off, np.int64)
+    q_off = np.ascontiguousarray(q_off, np.int64)
+    out = np.empty(int(q_off[t1] - q_off[t0]), np.uint64)
+    if out.size:
+        P = _c.POINTER(_c.c_int64)
+        _native().sin_segment_queries(
+            stream_seed(cfg, ROLE_INSERT), stream_seed(cfg, ROLE_FRESH),
+            stream_seed(cfg, ROLE_MEMBER), member_threshold(frac),
+            ins_off.ctypes.data_as(P), q_off.ctypes.data_as(P), t0, t1, _p64(out),
+            _threads(threads))
+    return out

@@ -23,7 +23,7 @@ def test_reference_arm_prints_the_contract_line():
                 "higher_is_better", "config", "cpu_baseline", "e2e"):
         assert key in line, key
     assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
-    assert line["config"]["workload"] == "sbbf_32768blk_1M_ins_256M_lookup"
+    assert line["config"]["workload"] == "sbbf_4194304blk_100M_ins_1G_lookup"
     assert line["e2e"]["h2d_bytes_per_step"] == 0
 
 
