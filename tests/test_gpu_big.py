@@ -1,13 +1,11 @@
 """Full-size parity for the HBM-resident filters with 3e9 inserted hashes:
 2^30 blocks (32 GiB) and 128,906,250 blocks (11 bits/key), 1e9 lookups with
-10% members, in the batches the benchmark uses.  Filters this size cannot be
-rebuilt on the host quickly, so the oracle rebuilds exactly the blocks that a
-sample of lookups land in (plus two contiguous block ranges) from all 3e9
-hashes, and every sampled lookup and every rebuilt block must match; the
-whole output is also checked statistically (members always hit; the false
-positive count of the non-members within a Poisson interval of the formula)."""
-import concurrent.futures
-
+10% members, in the batches the benchmark uses.  The oracle rebuilds each
+filter whole on the host (all cores, each thread owning a block range), and
+every word and every one of the 1e9 answers must match; the random and the
+slice-ordered lookup paths must give the same answers; the whole output is
+also checked statistically (members always hit; the false positive count of
+the non-members within a Poisson interval of the formula)."""
 import numpy as np
 import pytest
 import torch
@@ -16,70 +14,31 @@ import oracle
 import paper_2101_01719_gb300 as sb
 from paper_2101_01719_gb300 import workloads as wl
 import sbbf_inputs as inp
-from gpu_util import bit_at, bits_np, dev, to_dev, u64_np
+from gpu_util import (bit_at, bits_np, compare_all_lookups, compare_words, dev,
+                      oracle_filter_of_stream, to_dev, u64_np)
 
 pytestmark = pytest.mark.gpu
 
 
-def _oracle_blocks(w, lo, hi, chunk=1 << 25, threads=8):
-    """Blocks [lo[r], hi[r]) of w's filter after all its inserts, by the
-    oracle, scanning the insert stream in chunks on several threads."""
-    size = 8 * int((hi - lo).sum())
-    sd = wl.seed(w.cfg, wl.ROLE_INSERT)
-    starts = list(range(0, w.n_insert, chunk))
-
-    def part(s0):
-        keys = oracle.splitmix64_fill(sd, s0, min(chunk, w.n_insert - s0))
-        out = np.zeros(size, np.uint32)
-        return oracle.insert_block_ranges(out, w.num_blocks, keys, lo, hi)
-
-    total = np.zeros(size, np.uint32)
-    with concurrent.futures.ThreadPoolExecutor(threads) as ex:
-        for p in ex.map(part, starts):
-            total |= p
-    return total
-
-
 @pytest.mark.parametrize("w", [wl.C2_BIG, wl.C2_11BPK], ids=lambda w: w.name)
-def test_three_billion_inserts_sampled_parity(w):
+def test_three_billion_inserts_full_parity(w):
     f = sb.Filter(w.num_blocks)
     buf = torch.empty(w.insert_batch, dtype=torch.int64, device=dev())
     wl.build_filter(w, f, scratch=buf)
     del buf
     q = wl.gen_queries(w, 0, w.n_lookup)
     bits = f.find(q)
+    other = sb.PARTITION_OFF if f.partition_applies(w.n_lookup, lookup=True) else sb.PARTITION_ON
+    f.set_partitioning(other)
+    assert torch.equal(f.find(q), bits)  # the other lookup path, the same answers
+    f.set_partitioning(sb.PARTITION_AUTO)
     torch.cuda.synchronize()
+    torch.cuda.empty_cache()
 
-    rng = np.random.default_rng(w.cfg)
-    idx = np.sort(rng.choice(w.n_lookup, size=512, replace=False)).astype(np.uint64)
-    qs = inp.sampled_queries(w.cfg, w.n_insert, w.member_frac, 0, idx)
-    assert np.array_equal(q[torch.from_numpy(idx.astype(np.int64)).to(dev())].cpu().numpy()
-                          .view(np.uint64), qs)
-    qb = np.array([oracle.block_index(int(h), w.num_blocks) for h in qs], np.uint64)
-    blocks = np.unique(qb)
-    lo = np.concatenate([blocks, [0, w.num_blocks - 2048]]).astype(np.uint64)
-    hi = np.concatenate([blocks + 1, [2048, w.num_blocks]]).astype(np.uint64)
-    order = np.argsort(lo, kind="stable")
-    lo, hi = lo[order], hi[order]
-    keep = np.ones(lo.size, bool)  # drop single blocks inside the two ranges
-    for i in range(1, lo.size):
-        if lo[i] < hi[:i][keep[:i]].max(initial=0):
-            keep[i] = False
-    lo, hi = lo[keep], hi[keep]
-    expect = _oracle_blocks(w, lo, hi)
-
-    words = f.words.view(-1, 8)
-    got = torch.cat([words[int(a): int(b)] for a, b in zip(lo, hi)]).cpu().numpy()
-    assert np.array_equal(got.view(np.uint32).reshape(-1), expect)
-
-    # every sampled lookup against its rebuilt block
-    first = np.concatenate([[0], np.cumsum(hi - lo)[:-1]]).astype(np.uint64)
-    ans = bit_at(bits.cpu().numpy().view(np.uint32), idx.astype(np.int64))
-    for j, (h, b) in enumerate(zip(qs, qb)):
-        r = int(np.searchsorted(lo, b, side="right") - 1)
-        off = int(first[r] + (b - lo[r]))
-        blk = expect[8 * off: 8 * off + 8].copy()
-        assert bool(ans[j]) == oracle.find_one(blk, 1, int(h) & 0xFFFFFFFF), j
+    ref = oracle_filter_of_stream(w)
+    compare_words(f.words, ref)
+    compare_all_lookups(w, ref, q, bits)
+    del ref
 
     # statistics over all 1e9 answers
     r = torch.empty(w.n_lookup, dtype=torch.int64, device=dev())
@@ -91,6 +50,8 @@ def test_three_billion_inserts_sampled_parity(w):
     lam = p * (w.n_lookup - members)
     assert hits >= members
     assert abs((hits - members) - lam) <= 6 * np.sqrt(lam) + 0.02 * lam + 10
+    del f, q, bits
+    torch.cuda.empty_cache()
 
 
 @pytest.mark.parametrize("slices", [1600, 3000])

@@ -197,10 +197,12 @@ def test_graph_launch_equals_separate_launches():
     assert np.array_equal(bits_np(out), bits_np(ref_bits))
 
 
-def test_config_c3_full_size_sampled_filters():
+def test_config_c3_full_size_every_filter():
     """4096 filters (1k..4M keys), one graph launch of all inserts then all
-    4x lookups; 24 filters (the largest, the smallest and a spread) checked in
-    full against the oracle; batched == per-filter launches on every word."""
+    4x lookups; batched == per-filter launches on every word and answer; and
+    every filter's words and every one of the 8.17e9 answers equal the
+    oracle's, filter by filter, with the oracle's queries generated on the
+    host and equal to the device-generated ones."""
     w = wl.C3
     n_keys, blocks = w.sizes()
     h_ins_off, h_q_off = w.offsets()
@@ -216,24 +218,42 @@ def test_config_c3_full_size_sampled_filters():
     assert np.array_equal(each.to_numpy(), arena)
     out_each = each.find_each(q, h_q_off)
     assert torch.equal(out_each, out)
-    del each, out_each
-    order = np.argsort(n_keys)
-    picks = sorted(set(order[:4].tolist() + order[-4:].tolist()
-                       + order[:: max(1, w.n_filters // 16)].tolist()))
+    del each, out_each, ins
+    torch.cuda.empty_cache()
     bits = bits_np(out)
+    del out
 
-    def check(t):
-        keys = inp.stream(w.cfg, 0, int(n_keys[t]), int(h_ins_off[t]))
+    def check(t, qs):
+        keys = inp.fast_stream(w.cfg, 0, int(n_keys[t]), int(h_ins_off[t]), threads=1)
         f = oracle.new_filter(int(blocks[t]))
         oracle.insert(f, int(blocks[t]), keys)
         if not np.array_equal(m.filter_words(arena, t), f):
             return "words of filter %d" % t
-        qs = inp.segment_queries(w.cfg, h_ins_off, h_q_off, w.member_frac, t)
         if not np.array_equal(bits[h_q_off[t] // 32: h_q_off[t + 1] // 32],
                               oracle.find(f, int(blocks[t]), qs)):
             return "lookups of filter %d" % t
         return None
 
-    with concurrent.futures.ThreadPoolExecutor(8) as ex:
-        errors = [e for e in ex.map(check, picks) if e]
-    assert not errors, errors
+    # groups of filters with about 2^26 lookups each; per group the host
+    # generates the queries, checks them against the device's, and the
+    # oracle checks each filter on its own thread
+    errors, pending = [], []
+    t0 = 0
+    threads = oracle.num_cores()
+    with concurrent.futures.ThreadPoolExecutor(threads) as ex:
+        while t0 < w.n_filters:
+            t1 = int(np.searchsorted(h_q_off, h_q_off[t0] + (1 << 26), side="right")) - 1
+            t1 = min(max(t1, t0 + 1), w.n_filters)
+            qh = inp.fast_segment_queries(w.cfg, h_ins_off, h_q_off, w.member_frac, t0, t1)
+            a, b = int(h_q_off[t0]), int(h_q_off[t1])
+            assert np.array_equal(u64_np(q[a:b]), qh), "queries of filters %d..%d" % (t0, t1)
+            pending.append([ex.submit(check, t, qh[int(h_q_off[t]) - a: int(h_q_off[t + 1]) - a])
+                            for t in range(t0, t1)])
+            while len(pending) > 4:  # bounds the host memory held by queued groups
+                errors += [e for e in (fu.result() for fu in pending.pop(0)) if e]
+            t0 = t1
+        for group in pending:
+            errors += [e for e in (fu.result() for fu in group) if e]
+    assert not errors, errors[:10]
+    del q
+    torch.cuda.empty_cache()

@@ -16,7 +16,8 @@ import paper_2101_01719_gb300 as sb
 from paper_2101_01719_gb300 import sbbf as abi
 from paper_2101_01719_gb300 import workloads as wl
 import sbbf_inputs as inp
-from gpu_util import bit_at, bits_np, dev, to_dev, u64_np
+from gpu_util import (bit_at, bits_np, compare_all_lookups, compare_words, dev,
+                      oracle_filter_of_stream, to_dev, u64_np)
 
 pytestmark = pytest.mark.gpu
 
@@ -272,26 +273,10 @@ def test_config_c0_full():
     assert abs(fp / nq - p) <= 5 * np.sqrt(p * (1 - p) / nq) + 0.02 * p
 
 
-def _sampled_lookup_check(w, f, ref, q_dev, bits_dev, start, n, n_samples, seed):
-    """Compare n_samples random lookups of a chunk against the oracle, one by
-    one, regenerating each query on the host."""
-    rng = np.random.default_rng(seed)
-    idx = np.sort(rng.choice(n, size=min(n_samples, n), replace=False))
-    qs = inp.sampled_queries(w.cfg, w.n_insert, w.member_frac, w.member_prefix,
-                             (idx + start).astype(np.uint64))
-    got_q = u64_np(q_dev)[idx] if q_dev is not None else None
-    if got_q is not None:
-        assert np.array_equal(got_q, qs)
-    ref_bits = oracle.find(ref, w.num_blocks, qs)
-    exp = bit_at(ref_bits, np.arange(idx.size))
-    got = bit_at(bits_np(bits_dev), idx)
-    assert np.array_equal(got, exp)
-
-
 def test_config_c1_full_size():
     """1M hashes into 32768 blocks; 256M lookups in one launch (the benchmark's
-    launch); words bit-exact; the first 8M lookups compared in full and 1M
-    sampled ones across the whole batch; members always hit."""
+    launch): filter words and every one of the 268,435,456 answers equal the
+    oracle's; members always hit."""
     w = wl.C1
     f = sb.Filter(w.num_blocks)
     wl.build_filter(w, f)
@@ -300,21 +285,17 @@ def test_config_c1_full_size():
     assert np.array_equal(f.to_numpy(), ref)
     q = wl.gen_queries(w, 0, w.n_lookup)
     bits = f.find(q)
+    compare_all_lookups(w, ref, q, bits)
     head = 8 * 2**20
-    qh = u64_np(q[:head])
-    assert np.array_equal(qh, inp.workload_queries(w.cfg, w.n_insert, w.member_frac, 0, 0, head))
-    assert np.array_equal(bits_np(bits[: head // 32]), oracle.find(ref, w.num_blocks, qh))
-    _sampled_lookup_check(w, f, ref, None, bits, 0, w.n_lookup, 1 << 20, 5)
     member = inp.query_is_member(w.cfg, head, w.member_frac)
     hit = np.unpackbits(bits_np(bits[: head // 32]).view(np.uint8), bitorder="little").astype(bool)
     assert hit[member].all()
 
 
 def test_bench_step_as_cuda_graph():
-    """The benchmark's timed step as it runs there: clear, insert 1M, look up
-    256M, captured once as a CUDA graph and replayed; after two replays the
-    words are the oracle's, the first 8M answers equal the oracle's and 1M
-    sampled answers across the batch do too."""
+    """The 1 MiB filter's step as a CUDA graph: clear, insert 1M, look up
+    256M, captured once and replayed; after two replays the words and every
+    answer are the oracle's."""
     w = wl.C1
     f = sb.Filter(w.num_blocks)
     ins = wl.gen_inserts(w, 0, w.n_insert, device=dev())
@@ -339,29 +320,41 @@ def test_bench_step_as_cuda_graph():
     keys = inp.stream(w.cfg, 0, w.n_insert)
     ref = _oracle_filter(w.num_blocks, keys)
     assert np.array_equal(f.to_numpy(), ref)
-    head = 8 * 2**20
-    assert np.array_equal(bits_np(out[: head // 32]),
-                          oracle.find(ref, w.num_blocks, u64_np(q[:head])))
-    _sampled_lookup_check(w, f, ref, None, out, 0, w.n_lookup, 1 << 20, 7)
+    compare_all_lookups(w, ref, q, out)
 
 
 def test_config_c2_full_size():
-    """100M hashes into 4,194,304 blocks in 16M batches: words bit-exact; 1B
-    lookups: first 4M in full and 1M sampled."""
+    """The default benchmark workload as the benchmark runs it: 100M hashes
+    into 4,194,304 blocks in 16M batches, then 1e9 lookups, captured as one
+    CUDA graph and replayed twice: words bit-exact and every one of the 1e9
+    answers equal to the oracle's."""
     w = wl.C2
     f = sb.Filter(w.num_blocks)
-    wl.build_filter(w, f)
-    keys = inp.stream(w.cfg, 0, w.n_insert)
-    ref = oracle.new_filter(w.num_blocks)
-    oracle.insert_mt(ref, w.num_blocks, keys, 8)
-    del keys
-    assert np.array_equal(f.to_numpy(), ref)
+    ins = wl.gen_inserts(w, 0, w.n_insert, device=dev())
     q = wl.gen_queries(w, 0, w.n_lookup)
-    bits = f.find(q)
-    head = 4 * 2**20
-    qh = u64_np(q[:head])
-    assert np.array_equal(bits_np(bits[: head // 32]), oracle.find(ref, w.num_blocks, qh))
-    _sampled_lookup_check(w, f, ref, None, bits, 0, w.n_lookup, 1 << 20, 6)
+    out = torch.empty(sb.out_words(w.n_lookup), dtype=torch.int32, device=dev())
+
+    def step():
+        f.clear()
+        for s0 in range(0, w.n_insert, w.insert_batch):
+            f.insert(ins[s0:s0 + w.insert_batch])
+        f.find(q, out=out)
+
+    step()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    out.fill_(-1)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    del ins
+    ref = oracle_filter_of_stream(w)
+    compare_words(f.words, ref)
+    compare_all_lookups(w, ref, q, out)
+    del q, out, g
+    torch.cuda.empty_cache()
 
 
 PARTITION_CASES = [(2**20, 0), (2**20, 1), (2**20 + 5, 16385), (3 * 2**20 - 1, 1_000_003),
