@@ -129,9 +129,9 @@ def step_kernels(f, batches, n_lookup, raw_keys):
     hashing = 1 if raw_keys else 0
     n = 1
     for _, cnt in batches:
-        n += (4 + hashing) if f.partition_applies(cnt) else 1
+        n += (3 * ((cnt + 2**34 - 1) // 2**34) + hashing) if f.partition_applies(cnt) else 1
     if f.partition_applies(n_lookup, lookup=True):
-        n += 5 * ((n_lookup + 2**31 - 1) // 2**31) + hashing
+        n += 4 * ((n_lookup + 2**31 - 1) // 2**31) + hashing
     else:
         n += 1
     return n

@@ -147,13 +147,15 @@ sbbf_status sbbf_insert_hashes(sbbf_t *f, const uint64_t *d_hashes, size_t n,
  * slice by slice with each slice prefetched into L2, which turns random DRAM
  * accesses into L2 hits for filters larger than L2; a lookup's answers are
  * then moved back to the hashes' order.  Results are identical either way
- * (inserts commute; a lookup's answer is set at its original position).  The
- * scratch -- 8 bytes per hash for inserts, 10.125 for lookups (at most 2^31
- * hashes at a time), plus per slice 12 bytes per SM and, for lookups, 4
- * bytes per SM and per 2^16 hashes -- is allocated with cudaMalloc
- * (synchronous) when a batch needs more than the filter holds, kept by the
- * filter and freed by sbbf_destroy; partitioned calls on one filter must
- * therefore be ordered on one stream.
+ * (inserts commute; a lookup's answer is set at its original position), for
+ * any input: hashes that crowd one slice far beyond its share are redone by
+ * the unpartitioned path.  The scratch -- about 8.6 bytes per hash for
+ * inserts and 11 for lookups (processed in pieces of at most 2^34 and 2^31
+ * hashes), plus per slice 4 bytes per SM and, for lookups, 4 bytes per SM
+ * and per 2^16 hashes -- is allocated with cudaMalloc (synchronous) when a
+ * batch needs more than the filter holds, kept by the filter and freed by
+ * sbbf_destroy; partitioned calls on one filter must therefore be ordered on
+ * one stream.
  *   SBBF_PARTITION_AUTO (default): partition batches of at least 4Mi hashes
  *     into filters of at least 256 MiB when the batch has at least one hash
  *     per block; if the scratch cannot be allocated, run unpartitioned;
@@ -169,12 +171,32 @@ sbbf_status sbbf_set_partitioning(sbbf_t *f, int mode);
  * follow the same rule today).  The answer is the
  * decision before any scratch allocation (in automatic mode a failed
  * allocation still falls back to the unpartitioned path).  A partitioned
- * insert runs four kernels (count, scan, scatter, slice-ordered insert), a
- * partitioned lookup five per piece of at most 2^31 hashes (count, scan,
- * scatter, slice-ordered lookup, answers back to key order); raw keys add
- * one hashing kernel.  *applies is set to 1 or 0.
+ * insert runs three kernels per piece of at most 2^34 hashes (scatter,
+ * slice-ordered insert, crowded ranges), a partitioned lookup four per piece
+ * of at most 2^31 hashes (scatter, slice-ordered lookup, answers back to key
+ * order, crowded ranges); raw keys add one hashing kernel.  *applies is set to 1 or 0.
  * Errors: SBBF_EINVAL (NULL filter or applies). */
 sbbf_status sbbf_partition_applies(const sbbf_t *f, size_t n, int lookup, int *applies);
+
+/* Outcome of the device-side waits of the partitioned calls on f since the
+ * last query.  The partitioned passes stream each CTA's hashes through
+ * shared memory with asynchronous bulk copies and wait for each copy on an
+ * mbarrier with a time limit (2 s; a copy takes microseconds).  If a wait
+ * runs out, the CTA records bit 1 in the filter's device status word and
+ * reads its remaining hashes with plain loads -- the call's results stay
+ * exact; before the CTA exits it waits, with the same limit, for every copy
+ * still outstanding, and records bit 2 if one never completed (the results
+ * of that call are then not guaranteed).  This call synchronises `stream`
+ * (order it after the calls to check), reads the word and clears it.
+ * Returns SBBF_OK when no wait ran out, SBBF_ETIMEOUT when one did.
+ * Errors: SBBF_EINVAL (NULL filter), SBBF_ECUDA. */
+sbbf_status sbbf_device_status(sbbf_t *f, sbbf_stream_t stream);
+
+/* Sets `bits` in f's device status word on `stream`, as a timed-out device
+ * wait does; for testing the reporting of sbbf_device_status without making
+ * a device wait run out.  Errors: SBBF_EINVAL (NULL filter or one not on
+ * the current device), SBBF_ENOMEM / SBBF_ECUDA (allocating the word). */
+sbbf_status sbbf_record_device_status(sbbf_t *f, uint32_t bits, sbbf_stream_t stream);
 
 /* Look up d_hashes[0..n) (appendix find_hash for each) into the packed
  * bitmask d_out_bits of (n + 31) / 32 words (caller-owned, 4-byte aligned).

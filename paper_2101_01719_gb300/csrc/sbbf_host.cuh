@@ -89,6 +89,8 @@ struct sbbf_filter {
   int partition_mode;   // SBBF_PARTITION_*
   void *scratch;        // partitioned-insert scratch (library-owned), or NULL
   size_t scratch_bytes;
+  unsigned *status;     // device status word of the partitioned passes (allocated with
+                        // the first scratch; read and cleared by sbbf_device_status)
 };
 
 namespace sbbf {
@@ -97,14 +99,16 @@ namespace sbbf {
 // single-filter policy that selects it (sbbf_single.cu).
 uint64_t partition_scratch_bytes(uint32_t num_blocks, uint64_t n, bool with_index);
 sbbf_status launch_insert_partitioned(uint32_t* words, uint32_t num_blocks, const uint64_t* hashes,
-                                      uint64_t n, void* scratch, cudaStream_t s);
+                                      uint64_t n, void* scratch, unsigned* status,
+                                      cudaStream_t s);
 sbbf_status launch_find_partitioned(const uint32_t* words, uint32_t num_blocks,
                                     const uint64_t* hashes, uint64_t n, uint32_t* d_out,
-                                    void* scratch, cudaStream_t s);
+                                    void* scratch, unsigned* status, cudaStream_t s);
 // True when a batch of n keys should take the partitioned path (the filter's
 // mode, its size, and at least min_keys_per_block keys per block).
 bool want_partition(const sbbf_filter* f, uint64_t n);
-// Grows the filter's scratch (cudaMalloc, synchronous) to at least `bytes`.
+// Grows the filter's scratch (cudaMalloc, synchronous) to at least `bytes`;
+// the first call also allocates the filter's zeroed device status word.
 sbbf_status ensure_scratch(sbbf_filter* f, size_t bytes);
 
 // Words and bytes of a filter's bit array.

@@ -62,7 +62,7 @@ sbbf_status insert_src(sbbf_t* f, S src, uint64_t n, cudaStream_t s) {
       const sbbf_status hs = launch_hash(src, n, hashes, s);
       if (hs != SBBF_OK) return hs;
       return launch_insert_partitioned(f->words, f->num_blocks, hashes, n,
-                                       static_cast<char*>(f->scratch) + hb, s);
+                                       static_cast<char*>(f->scratch) + hb, f->status, s);
     }
     if (st != SBBF_ENOMEM || f->partition_mode == SBBF_PARTITION_ON) return st;
   }
@@ -75,17 +75,15 @@ template <class S>
 sbbf_status find_src(const sbbf_t* f, S src, uint64_t n, uint32_t* out, cudaStream_t s) {
   if (n == 0) return SBBF_OK;
   if (want_partition(f, n)) {
-    const uint64_t piece = n < (1ull << 31) ? n : (1ull << 31);
     const size_t hb = round256(n * 8);
     sbbf_t* fm = const_cast<sbbf_t*>(f);
-    const sbbf_status st =
-        ensure_scratch(fm, hb + partition_scratch_bytes(f->num_blocks, piece, true));
+    const sbbf_status st = ensure_scratch(fm, hb + partition_scratch_bytes(f->num_blocks, n, true));
     if (st == SBBF_OK) {
       uint64_t* hashes = static_cast<uint64_t*>(fm->scratch);
       const sbbf_status hs = launch_hash(src, n, hashes, s);
       if (hs != SBBF_OK) return hs;
       return launch_find_partitioned(f->words, f->num_blocks, hashes, n, out,
-                                     static_cast<char*>(fm->scratch) + hb, s);
+                                     static_cast<char*>(fm->scratch) + hb, fm->status, s);
     }
     if (st != SBBF_ENOMEM || f->partition_mode == SBBF_PARTITION_ON) return st;
   }

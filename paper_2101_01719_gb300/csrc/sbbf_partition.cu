@@ -4,31 +4,40 @@
 // of at least 64 bytes, and DRAM serves only ~40 G random accesses per
 // second, whereas the same block in L2 costs one L1/L2 request.  So for a
 // large batch the keys are first grouped by filter slice -- 2^shift
-// consecutive blocks, 4 to 32 MiB (see slice_shift) -- and then processed
-// slice by slice, in order:
-//   1. count: the keys are split into one contiguous range per CTA; each CTA
-//      histograms its range by slice in shared memory and stores its row;
-//   2. scan (one CTA): slice totals, slice start offsets, and for every
-//      (CTA, slice) the output position where that CTA's keys of the slice
-//      begin -- so the scatter needs no global atomics and its output order
-//      is the same on every run;
-//   3. scatter: each CTA streams its range in tiles through shared memory
-//      (double-buffered bulk copies, cp.async.bulk with an mbarrier, the next
-//      tile arriving while the current one is processed), counting-sorts the
-//      tile by slice there and writes each slice's run at its own cursor, so
-//      consecutive threads write consecutive addresses;
-//   4. insert or look up the slice-ordered keys with the in-order dynamic
-//      tile schedule; every claimed tile bulk-prefetches into L2 the filter
-//      bytes of the keys a slice ahead, so the filter is read from DRAM
-//      sequentially and hit in L2 when the keys arrive;
-//   5. lookups only: the answers, written in slice order, go back to key
-//      order one sub-range of positions at a time, each in shared memory.
+// consecutive blocks, 4 to 32 MiB (see insert_shift, find_plan) -- and then
+// processed slice by slice, in order:
+//   1. scatter: the keys are split into one contiguous range per CTA (one
+//      CTA per SM); each CTA streams its range through shared memory in
+//      8192-key tiles (double-buffered bulk copies, cp.async.bulk with an
+//      mbarrier, the next tile arriving while the current one is
+//      processed), counting-sorts each tile by slice there and appends each
+//      slice's run to its bucket for that slice, so consecutive threads write
+//      consecutive addresses.  Bucket (q, c) of slice q and CTA c holds
+//      positions [(q C + c) cap, (q C + c + 1) cap) of the slice-ordered
+//      array (C CTAs), where cap is the expected number of keys of one
+//      (slice, CTA) pair plus six standard deviations, so the buckets are
+//      placed by formula and no counting pass over the keys precedes the
+//      scatter.  Each CTA records how full its buckets are; a CTA whose keys
+//      overflow one of its buckets drops the overflow and is marked spilled.
+//   2. insert or look up the slice-ordered keys with the in-order dynamic
+//      tile schedule, skipping the unfilled end of each bucket; every
+//      claimed tile bulk-prefetches into L2 the filter bytes of the keys a
+//      slice ahead, so the filter is read from DRAM sequentially and hit in
+//      L2 when the keys arrive;
+//   3. lookups only: the answers, written in slice order, go back to key
+//      order one sub-range of positions at a time, each in shared memory;
+//   4. spilled CTAs (an input that crowds one slice far beyond its share;
+//      uniformly distributed hashes essentially never do) have their whole
+//      key range redone by the random-access path: inserts again (OR is
+//      idempotent), lookups rewrite that range's result words.  So every
+//      input gives the exact result, and a crowded one only costs time.
 // Inserts commute (OR), so the order within a slice does not matter and the
 // filter equals the unpartitioned insert bit for bit; lookups keep each key's
 // original position (written by the scatter) and answer exactly as the
 // unpartitioned lookup.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 
 #include "sbbf.h"
@@ -37,7 +46,6 @@
 #include "sbbf_kernels.cuh"
 
 namespace sbbf {
-sbbf_status launch_clear(uint32_t* dst, uint64_t n_words, cudaStream_t s);
 
 namespace {
 
@@ -45,8 +53,10 @@ constexpr int kMinSliceShift = 17;       // 2^17 blocks (4 MiB) per slice
 constexpr int kMaxSliceShift = 20;       // 2^20 blocks (32 MiB) per slice
 constexpr uint32_t kTargetSlices = 512;
 constexpr uint32_t kMaxSlices = 4096;    // num_blocks < 2^32 at the largest slice
-constexpr uint32_t kFewSlices = 32;      // ballot counting up to this many slices
+constexpr uint32_t kFewSlices = 32;      // ballot ranking up to this many slices
 constexpr int kPartThreads = 1024;
+constexpr uint32_t kTile = 8192;         // keys per scatter tile
+constexpr uint32_t kPer = kTile / kPartThreads;
 
 __device__ __forceinline__ uint32_t slice_of(uint64_t h, uint32_t nb, int shift) {
   return block_of(h, nb) >> shift;
@@ -58,25 +68,9 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
-constexpr int kCountThreads = 1024;
-
-// Adds 1 to bins[p] for every valid lane's p.  With few bins (kFew) a warp
-// counts each bin with one ballot; with many, lanes rarely collide and add
-// directly.
-template <bool kFew>
-__device__ __forceinline__ void count_warp(unsigned* bins, uint32_t n_slices, bool v, uint32_t p) {
-  if (kFew) {
-    for (uint32_t b = 0; b < n_slices; ++b) {
-      const unsigned m = __ballot_sync(0xFFFFFFFFu, v && p == b);
-      if (m && lane_id() == static_cast<unsigned>(__ffs(m) - 1)) atomicAdd(&bins[b], __popc(m));
-    }
-  } else if (v) {
-    atomicAdd(&bins[p], 1u);
-  }
-}
-
 // Rank of this lane's key among the keys of the same bin (claims ranks from
-// the shared counter ranks[p]).
+// the shared counter ranks[p]).  With few bins (kFew) a warp ranks each bin
+// with one ballot; with many, lanes rarely collide and count directly.
 template <bool kFew>
 __device__ __forceinline__ unsigned rank_warp(unsigned* ranks, uint32_t n_slices, bool v,
                                               uint32_t p) {
@@ -96,26 +90,45 @@ __device__ __forceinline__ unsigned rank_warp(unsigned* ranks, uint32_t n_slices
   return v ? atomicAdd(&ranks[p], 1u) : 0u;
 }
 
-// Keys [c * R, min(n, (c + 1) * R)) belong to CTA c of the count and scatter
-// passes.  R is a multiple of 32: a range starts 16-byte aligned whenever the
-// array does, and a lookup's result words split between ranges without
-// sharing a word.
+// Keys [c * R, min(n, (c + 1) * R)) belong to CTA c of the scatter.  R is a
+// multiple of 32: a range starts 16-byte aligned whenever the array does,
+// and a lookup's result words split between ranges without sharing a word.
 __host__ __device__ __forceinline__ uint64_t range_keys(uint64_t n, uint32_t ctas) {
   const uint64_t r = (n + ctas - 1) / ctas;
   return (r + 31) & ~31ull;
 }
 
 // Lookups map answers back to key order by sub-range: kSubKeys consecutive
-// positions of a CTA's range (a multiple of every scatter tile).  The scatter
-// records its slice cursors at each sub-range start, so the keys of sub-range
-// u of CTA c that fall in slice q sit at sorted positions
+// positions of a CTA's range (a whole number of scatter tiles).  The scatter
+// records its bucket cursors at each sub-range start, so the keys of
+// sub-range u of CTA c that fall in slice q sit at sorted positions
 // [marks[c][u][q], marks[c][u + 1][q]); a key's original position is then
 // stored as its 16-bit offset within its sub-range.
 constexpr uint32_t kSubKeys = 1u << 16;
+static_assert(kSubKeys % kTile == 0, "a sub-range is a whole number of tiles");
+static_assert(kTile % kPartThreads == 0 && kTile <= 8192, "whole keys per thread; 13-bit ranks");
 
 __host__ __device__ __forceinline__ uint32_t sub_ranges(uint64_t range) {
   return static_cast<uint32_t>((range + kSubKeys - 1) / kSubKeys);
 }
+
+// Where the slice-ordered keys go: bucket (q, c) -- slice q, scatter CTA c --
+// holds positions [base(q, c), base(q, c) + cap); slice q's buckets are
+// consecutive, so slice q spans positions [q * slice_positions(), ...).
+struct Buckets {
+  uint32_t ctas;
+  uint32_t n_slices;
+  uint64_t cap;  // a multiple of 64, below 2^31
+  __host__ __device__ __forceinline__ uint64_t base(uint32_t q, uint32_t c) const {
+    return (static_cast<uint64_t>(q) * ctas + c) * cap;
+  }
+  __host__ __device__ __forceinline__ uint64_t slice_positions() const {
+    return static_cast<uint64_t>(ctas) * cap;
+  }
+  __host__ __device__ __forceinline__ uint64_t positions() const {
+    return slice_positions() * n_slices;
+  }
+};
 
 // ---- bulk copies into shared memory ------------------------------------------
 
@@ -165,116 +178,33 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
       : "memory");
 }
 
-// hist[c * n_slices + p] = keys of CTA c's range that fall in slice p.  The
-// range streams through shared memory in tiles of kCountTile keys,
-// double-buffered bulk copies like the scatter's (plain loads when the key
-// array is not 16-byte aligned or a copy did not complete in time), so the
-// histogram atomics of one tile overlap the copy of the next.
-constexpr uint32_t kCountTile = 8192;
+// Bits of the device status word the partitioned passes report through
+// (sbbf_device_status turns any of them into SBBF_ETIMEOUT).
+constexpr unsigned kStatusWaitTimedOut = 1u;  // a bulk-copy wait ran out; plain loads took over
+constexpr unsigned kStatusCopyPending = 2u;   // a copy had not landed when the CTA gave up on it
 
-template <bool kFew>
-__global__ void __launch_bounds__(kCountThreads, 1)
-    count_kernel(const uint64_t* __restrict__ hashes, uint64_t n, uint32_t nb, int shift,
-                 uint32_t n_slices, uint64_t range, unsigned* __restrict__ hist) {
-  extern __shared__ __align__(16) unsigned long long smem[];
-  uint64_t* s_buf0 = reinterpret_cast<uint64_t*>(smem);
-  uint64_t* s_buf1 = s_buf0 + kCountTile;
-  unsigned* s_cnt = reinterpret_cast<unsigned*>(s_buf1 + kCountTile);
-  __shared__ __align__(8) unsigned long long s_bar[2];
-  for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x) s_cnt[i] = 0;
-  const uint64_t pol = policy_evict_first();
-  const uint64_t a = static_cast<uint64_t>(blockIdx.x) * range;
-  const uint64_t b = a + range < n ? a + range : n;
-  const uint64_t n_tiles = a < b ? (b - a + kCountTile - 1) / kCountTile : 0;
-  bool bulk = (reinterpret_cast<uintptr_t>(hashes) & 15) == 0 && n_tiles > 0;
-  const uint32_t bar0 = smem_u32(&s_bar[0]), bar1 = smem_u32(&s_bar[1]);
-  if (threadIdx.x == 0 && bulk) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+// Thread 0's record of the bulk copies it issued into a CTA's two key
+// buffers: which buffer has a copy whose completion no wait has observed
+// yet, and the mbarrier phase parity that completion will show.  After a
+// timed-out wait the CTA stops using the buffers (plain loads instead), so a
+// late copy can only land in a buffer nothing reads; before the CTA exits,
+// drain() waits -- again with the time limit -- for every copy still
+// outstanding, so that its shared memory is not handed to another CTA while
+// a copy may still write it.
+struct CopyTrack {
+  uint32_t pending = 0, parity = 0;
+  __device__ void issued(int buf, uint32_t expected_parity) {
+    pending |= 1u << buf;
+    parity = (parity & ~(1u << buf)) | (expected_parity << buf);
   }
-  __syncthreads();
-  auto issue = [&](uint64_t t) {
-    const uint64_t t0 = a + t * kCountTile;
-    const uint64_t m = b - t0 < kCountTile ? b - t0 : kCountTile;
-    bulk_load((t & 1) ? s_buf1 : s_buf0, hashes + t0, static_cast<uint32_t>((m & ~1ull) * 8),
-              (t & 1) ? bar1 : bar0);
-  };
-  if (threadIdx.x == 0 && bulk) issue(0);
-  uint32_t parity = 0;
-  for (uint64_t t = 0; t < n_tiles; ++t) {
-    const uint64_t t0 = a + t * kCountTile;
-    const uint32_t m = static_cast<uint32_t>(b - t0 < kCountTile ? b - t0 : kCountTile);
-    const int cur = static_cast<int>(t & 1);
-    uint64_t* s_in = cur ? s_buf1 : s_buf0;
-    if (bulk) {
-      if (threadIdx.x == 0 && t + 1 < n_tiles) issue(t + 1);
-      const bool ok = wait_phase(cur ? bar1 : bar0, (parity >> cur) & 1);
-      parity ^= 1u << cur;
-      bulk = __syncthreads_and(ok);
-      if (bulk && (m & 1) && threadIdx.x == 0) s_in[m - 1] = load_key1(hashes + t0 + m - 1, pol);
-      __syncthreads();
-    }
-    for (uint32_t j0 = 0; j0 < m; j0 += blockDim.x) {
-      const uint32_t j = j0 + threadIdx.x;
-      const bool v = j < m;
-      const uint64_t key = !v ? 0 : bulk ? s_in[j] : load_key1(hashes + t0 + j, pol);
-      count_warp<kFew>(s_cnt, n_slices, v, v ? slice_of(key, nb, shift) : 0u);
-    }
-    __syncthreads();  // this buffer's readers are done before it is refilled
+  __device__ void observed(int buf) { pending &= ~(1u << buf); }
+  __device__ void drain(uint32_t bar0, uint32_t bar1, unsigned* status) {
+    for (int b = 0; b < 2; ++b)
+      if (((pending >> b) & 1) && !wait_phase(b ? bar1 : bar0, (parity >> b) & 1))
+        atomicOr(status, kStatusCopyPending);
+    pending = 0;
   }
-  for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x)
-    hist[static_cast<uint64_t>(blockIdx.x) * n_slices + i] = s_cnt[i];
-}
-
-// From the per-CTA histograms of `ctas` CTAs: offsets[0..n_slices] (slice
-// starts in the sorted array, exclusive scan of the slice totals) and
-// base[c * n_slices + p] = offsets[p] + keys of slice p in the ranges of CTAs
-// before c.  One CTA.
-__global__ void __launch_bounds__(1024)
-    scan_kernel(const unsigned* __restrict__ hist, uint32_t ctas, uint32_t n_slices,
-                unsigned long long* __restrict__ offsets, unsigned long long* __restrict__ base) {
-  __shared__ unsigned long long warp_total[32];
-  __shared__ unsigned long long carry;
-  const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (uint32_t start = 0; start < n_slices; start += blockDim.x) {
-    const uint32_t t = start + threadIdx.x;
-    unsigned long long v = 0;
-    if (t < n_slices)
-      for (uint32_t c = 0; c < ctas; ++c) v += hist[static_cast<uint64_t>(c) * n_slices + t];
-    unsigned long long x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-      if (lane >= static_cast<unsigned>(o)) x += y;
-    }
-    if (lane == 31) warp_total[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-      unsigned long long s = warp_total[lane];
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, s, o);
-        if (lane >= static_cast<unsigned>(o)) s += y;
-      }
-      warp_total[lane] = s;
-    }
-    __syncthreads();
-    const unsigned long long before = carry + (warp > 0 ? warp_total[warp - 1] : 0ull) + x - v;
-    if (t < n_slices) {
-      offsets[t] = before;
-      unsigned long long run = before;
-      for (uint32_t c = 0; c < ctas; ++c) {
-        base[static_cast<uint64_t>(c) * n_slices + t] = run;
-        run += hist[static_cast<uint64_t>(c) * n_slices + t];
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) carry += warp_total[31];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) offsets[n_slices] = carry;
-}
+};
 
 // Exclusive scan of vals[0..n) in place over the CTA (n <= 8 * blockDim);
 // each thread scans up to 8 consecutive entries, then the per-thread sums
@@ -312,55 +242,63 @@ __device__ __forceinline__ void cta_exclusive_scan(unsigned* vals, uint32_t n, u
   __syncthreads();
 }
 
-// Shared memory of the scatter: two input tiles, the sorted tile, the
-// per-slice output cursors (u64) and counts / run starts / rank cursors
-// (u32), and the tile positions of the sorted keys (u16, lookups only).
-__host__ __device__ constexpr size_t scatter_smem_bytes(uint32_t tile, uint32_t n_slices,
-                                                        bool with_index) {
-  return 3ull * 8 * tile + 12ull * n_slices + (with_index ? 2ull * tile : 0);
+// ---- 1. scatter -----------------------------------------------------------------
+
+// Shared memory of the scatter: two input tiles, the per-slice bucket
+// cursors (i32) and counts / run starts (u32), and the sorted tile as the
+// input positions of its keys (u16).
+__host__ __device__ constexpr size_t scatter_smem_bytes(uint32_t n_slices) {
+  return 2ull * 8 * kTile + 8ull * n_slices + 2ull * kTile;
 }
 
-// Keys into slice order.  CTA c streams its range in tiles of kT keys: each
-// key claims its rank among the tile's keys of its slice with one shared
-// atomic (so the counters end as the slice counts), the counts are scanned
-// in place into run starts, a key goes to run start + rank in the sorted
-// tile, and each slice's run is written at the CTA's cursor for that slice
-// (from the scan), kept during the tile as cursor minus run start so that a
-// key's output position is one add.  Tile t+1 is bulk-copied into the other buffer while
-// tile t is processed.  The copies need a 16-byte aligned key array; with
-// any other alignment, or if a copy ever failed to complete in time, the
-// CTA reads the keys straight from global memory instead.  Lookups (kIndex)
-// also write each key's original position, as its 16-bit offset within its
-// sub-range, and the cursors at every sub-range start (and after the last
-// tile) to marks[c][u][q], `rows` rows per CTA.
-template <bool kFew, bool kIndex, uint32_t kT>
+// Keys into slice order.  CTA c streams its range in tiles: each key, read
+// once from the input buffer, claims its rank among the tile's keys of its
+// slice with one shared atomic (so the counters end as the slice counts),
+// the counts are scanned in place into run starts, and the tile's sort is
+// recorded as the input position of the key at each sorted slot (16 bits).
+// The write pass then walks the sorted slots in order, gathers each key from
+// the input buffer and stores it at its bucket's cursor (kept during the tile
+// as cursor minus run start, so that a key's slot is one add), consecutive
+// threads writing consecutive addresses within each run.  A key past its
+// bucket's capacity is dropped and the CTA marked spilled.  Tile t+1 is
+// bulk-copied into the other buffer while tile t is processed; the copies
+// need a 16-byte aligned key array, and with any other alignment, or if a
+// copy ever failed to complete in time, the CTA reads the keys straight from
+// global memory instead.  At the end the CTA records each bucket's fill and
+// its spill flag.  Lookups (kIndex) also write each key's original position,
+// as its 16-bit offset within its sub-range, and the bucket cursors at every
+// sub-range start (and after the last tile) to marks[c][u][q], `rows` rows
+// per CTA.  CTA 0 also resets the slice pass's tile counter.
+template <bool kFew, bool kIndex>
 __global__ void __launch_bounds__(kPartThreads, 1)
     scatter_kernel(const uint64_t* __restrict__ hashes, uint64_t n, uint32_t nb, int shift,
-                   uint32_t n_slices, uint64_t range, const unsigned long long* __restrict__ base,
-                   uint64_t* __restrict__ out, uint16_t* __restrict__ out_idx,
-                   uint32_t* __restrict__ marks, uint32_t rows) {
-  static_assert(kSubKeys % kT == 0, "a sub-range is a whole number of tiles");
-  static_assert(kT % kPartThreads == 0 && kT <= 8192, "whole keys per thread; 13-bit ranks");
-  constexpr uint32_t kPer = kT / kPartThreads;  // launched with kPartThreads threads
+                   Buckets bk, uint64_t range, uint64_t* __restrict__ out,
+                   uint16_t* __restrict__ out_idx, uint32_t* __restrict__ marks, uint32_t rows,
+                   uint32_t* __restrict__ fill, uint32_t* __restrict__ spill,
+                   unsigned long long* __restrict__ tiles, unsigned* __restrict__ status) {
   extern __shared__ __align__(16) unsigned long long smem[];
+  const uint32_t S = bk.n_slices;
   uint64_t* s_buf0 = reinterpret_cast<uint64_t*>(smem);
-  uint64_t* s_buf1 = s_buf0 + kT;
-  uint64_t* s_sorted = s_buf1 + kT;
-  unsigned long long* s_cursor = reinterpret_cast<unsigned long long*>(s_sorted + kT);
-  unsigned* s_cnt = reinterpret_cast<unsigned*>(s_cursor + n_slices);
-  uint16_t* s_pos = reinterpret_cast<uint16_t*>(s_cnt + n_slices);  // kIndex
+  uint64_t* s_buf1 = s_buf0 + kTile;
+  int* s_rel = reinterpret_cast<int*>(s_buf1 + kTile);              // [S] keys in bucket (q, c)
+  unsigned* s_cnt = reinterpret_cast<unsigned*>(s_rel + S);         // [S]
+  uint16_t* s_perm = reinterpret_cast<uint16_t*>(s_cnt + S);        // [kTile]
   __shared__ unsigned warp_sums[32];
   __shared__ __align__(8) unsigned long long s_bar[2];
+  __shared__ unsigned s_spill;
 
-  const uint64_t a = static_cast<uint64_t>(blockIdx.x) * range;
-  if (a >= n) return;  // the whole CTA: nothing of the key array is ours
-  const uint64_t b = a + range < n ? a + range : n;
-  const uint64_t n_tiles = (b - a + kT - 1) / kT;
-  for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x) {
-    s_cursor[i] = base[static_cast<uint64_t>(blockIdx.x) * n_slices + i];
+  const uint32_t c = blockIdx.x;
+  const int cap = static_cast<int>(bk.cap);
+  if (c == 0 && threadIdx.x == 0) *tiles = 0;
+  const uint64_t a = static_cast<uint64_t>(c) * range;
+  const uint64_t b = a < n ? (a + range < n ? a + range : n) : a;
+  const uint64_t n_tiles = (b - a + kTile - 1) / kTile;  // 0 past the keys
+  for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
+    s_rel[i] = 0;
     s_cnt[i] = 0;
   }
-  bool bulk = (reinterpret_cast<uintptr_t>(hashes) & 15) == 0;  // uniform over the CTA
+  if (threadIdx.x == 0) s_spill = 0;
+  bool bulk = (reinterpret_cast<uintptr_t>(hashes) & 15) == 0 && n_tiles > 0;  // CTA-uniform
   const uint32_t bar0 = smem_u32(&s_bar[0]), bar1 = smem_u32(&s_bar[1]);
   if (threadIdx.x == 0 && bulk) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
@@ -368,31 +306,33 @@ __global__ void __launch_bounds__(kPartThreads, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  uint32_t parity = 0;  // bit i: phase parity expected next on buffer i
+  CopyTrack track;      // thread 0's outstanding copies
   // thread 0 starts the copy of tile t (its even-length head; an odd last
   // key is loaded after the wait)
   auto issue = [&](uint64_t t) {
-    const uint64_t t0 = a + t * kT;
-    const uint64_t m = b - t0 < kT ? b - t0 : kT;
-    bulk_load((t & 1) ? s_buf1 : s_buf0, hashes + t0, static_cast<uint32_t>((m & ~1ull) * 8),
-              (t & 1) ? bar1 : bar0);
+    const uint64_t t0 = a + t * kTile;
+    const uint64_t m = b - t0 < kTile ? b - t0 : kTile;
+    const int buf = static_cast<int>(t & 1);
+    track.issued(buf, (parity >> buf) & 1);
+    bulk_load(buf ? s_buf1 : s_buf0, hashes + t0, static_cast<uint32_t>((m & ~1ull) * 8),
+              buf ? bar1 : bar0);
   };
   if (threadIdx.x == 0 && bulk) issue(0);
-  uint32_t parity = 0;  // bit i: phase parity expected next on buffer i
   const uint64_t pol = policy_evict_first();
 
-  uint32_t* my_marks = kIndex ? marks + static_cast<uint64_t>(blockIdx.x) * rows * n_slices
-                              : nullptr;
+  uint32_t* my_marks = kIndex ? marks + static_cast<uint64_t>(c) * rows * S : nullptr;
   for (uint64_t t = 0; t < n_tiles; ++t) {
-    const uint64_t t0 = a + t * kT;
-    const uint32_t m = static_cast<uint32_t>(b - t0 < kT ? b - t0 : kT);
+    const uint64_t t0 = a + t * kTile;
+    const uint32_t m = static_cast<uint32_t>(b - t0 < kTile ? b - t0 : kTile);
     const int cur = static_cast<int>(t & 1);
     uint64_t* s_in = cur ? s_buf1 : s_buf0;
     // offset of the tile's first key within its sub-range
-    const uint32_t sub_off = static_cast<uint32_t>((t % (kSubKeys / kT)) * kT);
-    if (kIndex && sub_off == 0) {  // cursors are true cursors between tiles
-      uint32_t* row = my_marks + (t / (kSubKeys / kT)) * n_slices;
-      for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x)
-        row[i] = static_cast<uint32_t>(s_cursor[i]);
+    const uint32_t sub_off = static_cast<uint32_t>((t % (kSubKeys / kTile)) * kTile);
+    if (kIndex && sub_off == 0) {  // bucket cursors are true cursors between tiles
+      uint32_t* row = my_marks + (t / (kSubKeys / kTile)) * S;
+      for (uint32_t q = threadIdx.x; q < S; q += blockDim.x)
+        row[q] = static_cast<uint32_t>(bk.base(q, c) + (s_rel[q] < cap ? s_rel[q] : cap));
     }
     if (bulk) {
       // the other buffer's last reader finished at the previous tile's end
@@ -400,13 +340,12 @@ __global__ void __launch_bounds__(kPartThreads, 1)
       // an odd last key lies past the copied span: stored before the barrier
       if ((m & 1) && threadIdx.x == 0) s_in[m - 1] = load_key1(hashes + t0 + m - 1, pol);
       const bool ok = wait_phase(cur ? bar1 : bar0, (parity >> cur) & 1);
+      if (ok && threadIdx.x == 0) track.observed(cur);
       parity ^= 1u << cur;
       bulk = __syncthreads_and(ok);  // all threads agree; on failure never use the buffers again
+      if (!bulk && threadIdx.x == 0) atomicOr(status, kStatusWaitTimedOut);
     }
     const bool from_smem = bulk;
-    auto key_at = [&](uint32_t j) -> uint64_t {
-      return from_smem ? s_in[j] : load_key1(hashes + t0 + j, pol);
-    };
     // each key claims its rank among the tile's keys of its slice (the
     // counters end as the slice counts); slice and rank stay in registers
     uint32_t qr[kPer];  // slice << 13 | rank
@@ -414,43 +353,68 @@ __global__ void __launch_bounds__(kPartThreads, 1)
     for (uint32_t i = 0; i < kPer; ++i) {
       const uint32_t j = i * kPartThreads + threadIdx.x;
       const bool v = j < m;
-      const uint32_t q = v ? slice_of(key_at(j), nb, shift) : 0u;
-      qr[i] = (q << 13) | rank_warp<kFew>(s_cnt, n_slices, v, q);
+      const uint64_t key = !v ? 0 : from_smem ? s_in[j] : load_key1(hashes + t0 + j, pol);
+      const uint32_t q = v ? slice_of(key, nb, shift) : 0u;
+      qr[i] = (q << 13) | rank_warp<kFew>(s_cnt, S, v, q);
     }
     __syncthreads();
-    cta_exclusive_scan(s_cnt, n_slices, warp_sums);  // counts -> run starts (ends with a barrier)
-    for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x) s_cursor[i] -= s_cnt[i];
+    cta_exclusive_scan(s_cnt, S, warp_sums);  // counts -> run starts (ends with a barrier)
+    for (uint32_t q = threadIdx.x; q < S; q += blockDim.x) s_rel[q] -= static_cast<int>(s_cnt[q]);
 #pragma unroll
     for (uint32_t i = 0; i < kPer; ++i) {
       const uint32_t j = i * kPartThreads + threadIdx.x;
-      if (j < m) {
-        const unsigned at = s_cnt[qr[i] >> 13] + (qr[i] & 0x1FFFu);  // run start + rank
-        s_sorted[at] = key_at(j);
-        if (kIndex) s_pos[at] = static_cast<uint16_t>(j);
-      }
+      if (j < m) s_perm[s_cnt[qr[i] >> 13] + (qr[i] & 0x1FFFu)] = static_cast<uint16_t>(j);
     }
     __syncthreads();
-    for (uint32_t j = threadIdx.x; j < m; j += blockDim.x) {
-      const uint64_t key = s_sorted[j];
-      const unsigned long long pos = s_cursor[slice_of(key, nb, shift)] + j;
-      if (pos < n) {  // in range unless the input changed between the passes
+    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
+      const uint32_t src = s_perm[i];
+      const uint64_t key = from_smem ? s_in[src] : load_key1(hashes + t0 + src, pol);
+      const uint32_t q = slice_of(key, nb, shift);
+      const int rel = s_rel[q] + static_cast<int>(i);  // this key's slot in bucket (q, c)
+      if (rel < cap) {
+        const uint64_t pos = bk.base(q, c) + static_cast<uint64_t>(rel);
         out[pos] = key;
-        if (kIndex) out_idx[pos] = static_cast<uint16_t>(sub_off + s_pos[j]);
+        if (kIndex) out_idx[pos] = static_cast<uint16_t>(sub_off + src);
+      } else {
+        s_spill = 1;
       }
     }
     __syncthreads();
     // the cursor advances by the run's length: cursor - start + end
-    for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x)
-      s_cursor[i] += i + 1 < n_slices ? s_cnt[i + 1] : m;
+    for (uint32_t q = threadIdx.x; q < S; q += blockDim.x)
+      s_rel[q] += static_cast<int>(q + 1 < S ? s_cnt[q + 1] : m);
     __syncthreads();  // every run end is read before the counters are cleared
-    for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x) s_cnt[i] = 0;
+    for (uint32_t q = threadIdx.x; q < S; q += blockDim.x) s_cnt[q] = 0;
     __syncthreads();
   }
   if (kIndex) {
-    uint32_t* row = my_marks + static_cast<uint64_t>(sub_ranges(b - a)) * n_slices;
-    for (uint32_t i = threadIdx.x; i < n_slices; i += blockDim.x)
-      row[i] = static_cast<uint32_t>(s_cursor[i]);
+    uint32_t* row = my_marks + static_cast<uint64_t>(sub_ranges(b - a)) * S;
+    for (uint32_t q = threadIdx.x; q < S; q += blockDim.x)
+      row[q] = static_cast<uint32_t>(bk.base(q, c) + (s_rel[q] < cap ? s_rel[q] : cap));
   }
+  for (uint32_t q = threadIdx.x; q < S; q += blockDim.x)
+    fill[static_cast<uint64_t>(c) * S + q] = static_cast<uint32_t>(s_rel[q] < cap ? s_rel[q] : cap);
+  if (threadIdx.x == 0) {
+    spill[c] = s_spill;
+    track.drain(bar0, bar1, status);
+  }
+}
+
+// ---- 2. the slice-ordered passes ---------------------------------------------------
+
+// One past the last key of the 64-position group g: a group lies within one
+// bucket (cap is a multiple of 64), whose first fill[c][q] positions hold
+// keys.
+__device__ __forceinline__ uint64_t group_end(const Buckets& bk, const uint32_t* __restrict__ fill,
+                                              uint64_t g) {
+  const uint64_t per = bk.cap >> 6;            // groups per bucket
+  const uint64_t bucket = g / per;             // q * ctas + c
+  const uint64_t o = (g - bucket * per) << 6;  // the group's offset in its bucket
+  const uint32_t q = static_cast<uint32_t>(bucket / bk.ctas);
+  const uint32_t c = static_cast<uint32_t>(bucket - static_cast<uint64_t>(q) * bk.ctas);
+  const uint64_t f = fill[static_cast<uint64_t>(c) * bk.n_slices + q];
+  const uint64_t valid = f > o ? (f - o < 64 ? f - o : 64) : 0;
+  return (g << 6) + valid;
 }
 
 // Prefetches bytes [lo, hi) of the filter words into L2 (16-byte multiples);
@@ -467,71 +431,52 @@ __device__ __forceinline__ void prefetch_bytes(const uint32_t* words, uint64_t l
   }
 }
 
-// Streaming prefetch by key position.  Slice q holds sorted positions
-// [offsets[q], offsets[q+1]) and filter blocks [q << shift, ...); the
-// position p of slice q is mapped to byte
-//   slice_lo + floor((p - first) * slice_bytes / keys / 32) * 32
+// Streaming prefetch by position.  Slice q holds positions [q P, (q + 1) P)
+// (P = bk.slice_positions()) and filter blocks [q << shift, ...); position p
+// of slice q is mapped to byte
+//   slice_lo + floor((p - q P) * slice_blocks / P) * 32
 // so consecutive position ranges map to consecutive, disjoint byte ranges and
-// every byte of every slice that holds keys is covered exactly once.  A warp
-// prefetches the bytes of positions [p0, p1) (any number of slices).
-__device__ __forceinline__ uint64_t position_byte(uint32_t nb, int shift, uint32_t q,
-                                                  uint64_t first, uint64_t keys, uint64_t p) {
+// every byte of every slice is covered exactly once.  A warp prefetches the
+// bytes of positions [p0, p1) (any number of slices).
+__device__ __forceinline__ uint64_t position_byte(uint32_t nb, int shift, uint32_t q, uint64_t P,
+                                                  uint64_t p) {
   const uint64_t b0 = static_cast<uint64_t>(q) << shift;
   const uint64_t b1 = b0 + (1ull << shift) < nb ? b0 + (1ull << shift) : nb;
   const uint64_t blocks = b1 - b0;
-  // (p - first) * blocks / keys without overflow: both factors < 2^32 here
-  // unless keys is large, so split the quotient
-  const uint64_t d = p - first;
-  const uint64_t blk = (d / keys) * blocks + ((d % keys) * blocks) / keys;
+  // (p - qP) * blocks / P without overflow: split the quotient
+  const uint64_t d = p - static_cast<uint64_t>(q) * P;
+  const uint64_t blk = (d / P) * blocks + ((d % P) * blocks) / P;
   return 32 * (b0 + blk);
 }
 
 __device__ __forceinline__ void prefetch_positions(const uint32_t* words, uint32_t nb, int shift,
-                                                   const unsigned long long* __restrict__ offsets,
-                                                   uint32_t n_slices, uint64_t p0, uint64_t p1) {
-  const uint64_t n = offsets[n_slices];
+                                                   const Buckets& bk, uint64_t p0, uint64_t p1) {
+  const uint64_t P = bk.slice_positions(), n = bk.positions();
   if (p0 >= n) return;
   if (p1 > n) p1 = n;
-  uint32_t lo = 0, hi = n_slices;  // last q with offsets[q] <= p0
-  while (hi - lo > 1) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (offsets[mid] <= p0) lo = mid; else hi = mid;
-  }
-  for (uint32_t q = lo; q < n_slices && offsets[q] < p1; ++q) {
-    const uint64_t first = offsets[q], last = offsets[q + 1];
-    if (last == first) continue;
-    const uint64_t a = p0 > first ? p0 : first, b = p1 < last ? p1 : last;
+  for (uint64_t q = p0 / P; q < bk.n_slices && q * P < p1; ++q) {
+    const uint64_t lo = q * P, hi = lo + P;
+    const uint64_t a = p0 > lo ? p0 : lo, b = p1 < hi ? p1 : hi;
     if (a >= b) continue;
-    prefetch_bytes(words, position_byte(nb, shift, q, first, last - first, a),
-                   position_byte(nb, shift, q, first, last - first, b));
+    prefetch_bytes(words, position_byte(nb, shift, static_cast<uint32_t>(q), P, a),
+                   position_byte(nb, shift, static_cast<uint32_t>(q), P, b));
   }
 }
 
-// Distance, in sorted positions, that the streaming prefetch runs ahead of
-// the newest claimed tile: one whole slice of keys (the largest), so a
-// slice's blocks are all in L2 before its first key is processed, plus half
-// the window of keys in flight, for the prefetches to land.  The L2
-// footprint is then about one slice plus 1.5 windows of filter bytes.  One
-// warp computes it (all lanes return the same value).
-__device__ __forceinline__ uint64_t prefetch_ahead(const unsigned long long* __restrict__ offsets,
-                                                   uint32_t n_slices, uint64_t window) {
-  unsigned long long k_max = 0;
-  for (uint32_t q = lane_id(); q < n_slices; q += 32) {
-    const unsigned long long k = offsets[q + 1] - offsets[q];
-    k_max = k > k_max ? k : k_max;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long v = __shfl_xor_sync(0xFFFFFFFFu, k_max, o);
-    k_max = v > k_max ? v : k_max;
-  }
-  return k_max + window / 2;
+// Distance, in positions, that the streaming prefetch runs ahead of the
+// newest claimed tile: one whole slice, so a slice's blocks are all in L2
+// before its first key is processed, plus half the window of positions in
+// flight, for the prefetches to land.  The L2 footprint is then about one
+// slice plus 1.5 windows of filter bytes.
+__device__ __forceinline__ uint64_t prefetch_ahead(const Buckets& bk, uint64_t window) {
+  return bk.slice_positions() + window / 2;
 }
 
-// Rounds of 64-key groups per warp per tile (a launch argument, 1..8; even
-// for lookups).  The host picks it from the filter bytes per key: the window
-// of keys in flight (CTAs x tile) times that is held near 24 MiB, so window
-// and prefetch fit in L2 with a slice; dense batches get long tiles (fewer
-// claims of the shared tile counter), sparse ones short tiles.
+// Rounds of 64-position groups per warp per tile (a launch argument, 1..8;
+// even for lookups).  The host picks it from the filter bytes per key: the
+// window of keys in flight (CTAs x tile) times that is held near 24 MiB, so
+// window and prefetch fit in L2 with a slice; dense batches get long tiles
+// (fewer claims of the shared tile counter), sparse ones short tiles.
 constexpr int kMaxSlicedRounds = 8;
 
 // Slice-ordered insert with the in-order dynamic tile schedule.  Every tile
@@ -541,22 +486,21 @@ constexpr int kMaxSlicedRounds = 8;
 // prefetch of positions [0, ahead).
 __global__ void __launch_bounds__(256)
     sliced_insert_kernel(uint32_t* __restrict__ words, uint32_t nb, int shift,
-                         const uint64_t* __restrict__ keys, uint64_t n,
-                         const unsigned long long* __restrict__ offsets, uint32_t n_slices,
-                         unsigned long long* __restrict__ tiles, int rounds) {
+                         const uint64_t* __restrict__ keys, Buckets bk,
+                         const uint32_t* __restrict__ fill, unsigned long long* __restrict__ tiles,
+                         int rounds) {
   __shared__ unsigned long long s_tile;
   const unsigned wpc = blockDim.x >> 5, wic = threadIdx.x >> 5;
-  const uint64_t n_groups = (n + 63) >> 6;
+  const uint64_t n_groups = bk.positions() >> 6;
   const uint64_t groups_per_tile = static_cast<uint64_t>(wpc) * rounds;
   const uint64_t keys_per_tile = groups_per_tile * 64;
   const uint64_t pol = policy_evict_first();
   OneFilter res{nb};
   uint64_t ahead = 0;
   if (wic == 0) {
-    ahead = prefetch_ahead(offsets, n_slices, keys_per_tile * gridDim.x);
+    ahead = prefetch_ahead(bk, keys_per_tile * gridDim.x);
     const uint64_t share = (ahead + gridDim.x - 1) / gridDim.x;
-    prefetch_positions(words, nb, shift, offsets, n_slices, blockIdx.x * share,
-                       (blockIdx.x + 1) * share);
+    prefetch_positions(words, nb, shift, bk, blockIdx.x * share, (blockIdx.x + 1) * share);
   }
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(tiles, 1ull);
@@ -565,11 +509,10 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     if (g0 >= n_groups) break;
     if (wic == 0)
-      prefetch_positions(words, nb, shift, offsets, n_slices, g0 * 64 + ahead,
-                         g0 * 64 + ahead + keys_per_tile);
+      prefetch_positions(words, nb, shift, bk, g0 * 64 + ahead, g0 * 64 + ahead + keys_per_tile);
     for (int r = 0; r < rounds; ++r) {
       const uint64_t g = g0 + static_cast<uint64_t>(r) * wpc + wic;
-      if (g < n_groups) insert_group8(words, res, HashInput(keys), n, pol, g);
+      if (g < n_groups) insert_group8(words, res, HashInput(keys), group_end(bk, fill, g), pol, g);
     }
   }
 }
@@ -587,20 +530,20 @@ __device__ __forceinline__ uint32_t interleave16(uint32_t x, uint32_t y) {
   return spread16(x) | (spread16(y) << 1);
 }
 
-// Slice-ordered lookups of keys[0..n), with the same schedule and streaming
-// prefetch as the sliced insert.  The answers are written in sorted order,
-// packed like the unpartitioned lookup's (bit k of the pair of words 2g, 2g+1
-// answers sorted position 64g + k); unscatter_kernel moves them to the keys'
+// Slice-ordered lookups of the keys at positions [0, bk.positions()), with
+// the same schedule and streaming prefetch as the sliced insert; positions
+// past a bucket's fill answer 0.  The answers are written in sorted order,
+// packed like the unpartitioned lookup's (bit k of the pair of words 2g,
+// 2g+1 answers position 64g + k); unscatter_kernel moves them to the keys'
 // original positions.
 __global__ void __launch_bounds__(256, 4)
     sliced_find_kernel(const uint32_t* __restrict__ words, uint32_t nb, int shift,
-                       const uint64_t* __restrict__ keys, uint64_t n,
-                       const unsigned long long* __restrict__ offsets, uint32_t n_slices,
-                       unsigned long long* __restrict__ tiles, uint32_t* __restrict__ sorted_bits,
-                       int rounds) {
+                       const uint64_t* __restrict__ keys, Buckets bk,
+                       const uint32_t* __restrict__ fill, unsigned long long* __restrict__ tiles,
+                       uint32_t* __restrict__ sorted_bits, int rounds) {
   __shared__ unsigned long long s_tile;
   const unsigned wpc = blockDim.x >> 5, wic = threadIdx.x >> 5, lane = lane_id();
-  const uint64_t n_groups = (n + 63) >> 6;
+  const uint64_t n_groups = bk.positions() >> 6;
   const uint64_t groups_per_tile = static_cast<uint64_t>(wpc) * rounds;
   const uint64_t keys_per_tile = groups_per_tile * 64;
   const uint64_t pk = policy_evict_first();
@@ -612,10 +555,9 @@ __global__ void __launch_bounds__(256, 4)
   const uint64_t pf = policy_evict_last();
   uint64_t ahead = 0;
   if (wic == 0) {
-    ahead = prefetch_ahead(offsets, n_slices, keys_per_tile * gridDim.x);
+    ahead = prefetch_ahead(bk, keys_per_tile * gridDim.x);
     const uint64_t share = (ahead + gridDim.x - 1) / gridDim.x;
-    prefetch_positions(words, nb, shift, offsets, n_slices, blockIdx.x * share,
-                       (blockIdx.x + 1) * share);
+    prefetch_positions(words, nb, shift, bk, blockIdx.x * share, (blockIdx.x + 1) * share);
   }
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(tiles, 1ull);
@@ -624,23 +566,23 @@ __global__ void __launch_bounds__(256, 4)
     __syncthreads();
     if (g0 >= n_groups) break;
     if (wic == 0)
-      prefetch_positions(words, nb, shift, offsets, n_slices, g0 * 64 + ahead,
-                         g0 * 64 + ahead + keys_per_tile);
+      prefetch_positions(words, nb, shift, bk, g0 * 64 + ahead, g0 * 64 + ahead + keys_per_tile);
     // two rounds per step: four block loads per lane in flight before any test
     for (int r = 0; r < rounds; r += 2) {
-      uint64_t k[2], h[2][2];
+      uint64_t k[2], lim[2], h[2][2];
       uint32_t w[2][2][8];
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const uint64_t g = g0 + static_cast<uint64_t>(r + u) * wpc + wic;
-        k[u] = g * 64 + 2 * lane;  // >= n past the last group
-        HashInput(keys).pair(k[u], n, pk, h[u][0], h[u][1]);
+        k[u] = g * 64 + 2 * lane;
+        lim[u] = g < n_groups ? group_end(bk, fill, g) : 0;  // keys [64 g, lim) are valid
+        HashInput(keys).pair(k[u], lim[u], pk, h[u][0], h[u][1]);
       }
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-          if (k[u] + e < n) {
+          if (k[u] + e < lim[u]) {
             load_block_na(words + 8ull * block_of(h[u][e], nb), pf, w[u][e]);
           } else {
 #pragma unroll
@@ -652,9 +594,10 @@ __global__ void __launch_bounds__(256, 4)
       for (int u = 0; u < 2; ++u) {
         // bit l of b0 / b1: key 2l / 2l + 1 of the group
         const uint32_t b0 = __ballot_sync(
-            0xFFFFFFFFu, k[u] < n && block_has(w[u][0], static_cast<uint32_t>(h[u][0])));
+            0xFFFFFFFFu, k[u] < lim[u] && block_has(w[u][0], static_cast<uint32_t>(h[u][0])));
         const uint32_t b1 = __ballot_sync(
-            0xFFFFFFFFu, k[u] + 1 < n && block_has(w[u][1], static_cast<uint32_t>(h[u][1])));
+            0xFFFFFFFFu,
+            k[u] + 1 < lim[u] && block_has(w[u][1], static_cast<uint32_t>(h[u][1])));
         const uint64_t g = g0 + static_cast<uint64_t>(r + u) * wpc + wic;
         if (lane == 0 && g < n_groups)
           *reinterpret_cast<uint2*>(sorted_bits + 2 * g) =
@@ -664,19 +607,21 @@ __global__ void __launch_bounds__(256, 4)
   }
 }
 
-// Answers back into key order.  CTA (c, u) owns the original positions
-// [lo, hi): sub-range u of scatter CTA c's key range.  The scatter put the
-// keys of that sub-range that fall in slice q at sorted positions
-// [marks[c][u][q], marks[c][u + 1][q]).  The CTA lists the answer words that
-// overlap these runs (shared memory holds each run's bounds and the list
-// offset of its first word); a lane takes one word, masks it to its run, and
-// for each found key -- each set bit -- loads the key's offset within the
-// sub-range and sets its bit in a shared-memory copy of the sub-range's
-// result words, four bits per round so that their loads overlap.  The words
-// are then stored whole: every result word belongs to exactly one CTA, so there are
-// no global atomics and no zeroing pass.  Positions and runs are clamped to
-// their buffers, so keys that changed between the passes give wrong answers,
-// never an access out of bounds.
+// ---- 3. answers back to key order ---------------------------------------------------
+
+// CTA (c, u) owns the original positions [lo, hi): sub-range u of scatter
+// CTA c's key range.  The scatter put the keys of that sub-range that fall in
+// slice q at sorted positions [marks[c][u][q], marks[c][u + 1][q]).  The CTA
+// lists the answer words that overlap these runs (shared memory holds each
+// run's bounds and the list offset of its first word); a lane takes one
+// word, masks it to its run, and for each found key -- each set bit -- loads
+// the key's offset within the sub-range and sets its bit in a shared-memory
+// copy of the sub-range's result words, four bits per round so that their
+// loads overlap.  The words are then stored whole: every result word belongs
+// to exactly one CTA, so there are no global atomics and no zeroing pass.
+// Positions and runs are clamped to their buffers (n_pos positions), so keys
+// that changed between the passes give wrong answers, never an access out of
+// bounds.
 constexpr int kUnscatterThreads = 512;
 
 __host__ __device__ constexpr size_t unscatter_smem_bytes(uint32_t n_slices) {
@@ -685,8 +630,8 @@ __host__ __device__ constexpr size_t unscatter_smem_bytes(uint32_t n_slices) {
 
 __global__ void __launch_bounds__(kUnscatterThreads)
     unscatter_kernel(const uint32_t* __restrict__ sorted_bits, const uint16_t* __restrict__ idx,
-                     const uint32_t* __restrict__ marks, uint64_t n, uint64_t range, uint32_t rows,
-                     uint32_t n_slices, uint32_t* __restrict__ out) {
+                     const uint32_t* __restrict__ marks, uint64_t n, uint64_t n_pos,
+                     uint64_t range, uint32_t rows, uint32_t n_slices, uint32_t* __restrict__ out) {
   extern __shared__ __align__(16) uint32_t s_mem[];
   uint32_t* s_out = s_mem;                           // result words of the sub-range
   uint32_t* s_lo = s_out + kSubKeys / 32;            // run q: sorted positions [s_lo, s_hi)
@@ -707,7 +652,7 @@ __global__ void __launch_bounds__(kUnscatterThreads)
   const uint32_t* m1 = m0 + n_slices;
   for (uint32_t i = threadIdx.x; i < n_words; i += blockDim.x) s_out[i] = 0;
   for (uint32_t q = threadIdx.x; q < n_slices; q += blockDim.x) {
-    const uint32_t p1 = static_cast<uint32_t>(m1[q] < n ? m1[q] : n);
+    const uint32_t p1 = static_cast<uint32_t>(m1[q] < n_pos ? m1[q] : n_pos);
     const uint32_t p0 = m0[q] < p1 ? m0[q] : p1;
     s_lo[q] = p0;
     s_hi[q] = p1;
@@ -756,6 +701,57 @@ __global__ void __launch_bounds__(kUnscatterThreads)
   for (uint32_t i = threadIdx.x; i < n_words; i += blockDim.x) dst[i] = s_out[i];
 }
 
+// ---- 4. spilled CTAs by the random-access path ----------------------------------
+
+constexpr int kFixupThreads = 256;
+
+// CTA c of the scatter spilled: insert its whole key range [c R, (c+1) R)
+// again, one warp per 64 keys (a repeated insert changes nothing).
+__global__ void __launch_bounds__(kFixupThreads)
+    fixup_insert_kernel(uint32_t* __restrict__ words, uint32_t nb,
+                        const uint64_t* __restrict__ hashes, uint64_t n, uint64_t range,
+                        const uint32_t* __restrict__ spill) {
+  const uint32_t c = blockIdx.x;
+  if (spill[c] == 0) return;
+  const uint64_t a = static_cast<uint64_t>(c) * range;
+  if (a >= n) return;
+  const uint64_t m = a + range < n ? range : n - a;
+  const uint64_t pol = policy_evict_first();
+  OneFilter res{nb};
+  const unsigned wpc = blockDim.x >> 5, wic = threadIdx.x >> 5;
+  for (uint64_t g = wic; g < (m + 63) / 64; g += wpc)
+    insert_group8(words, res, HashInput(hashes + a), m, pol, g);
+}
+
+// CTA c of the scatter spilled: answer its whole key range again and rewrite
+// the range's result words (a range is a whole number of words).
+__global__ void __launch_bounds__(kFixupThreads)
+    fixup_find_kernel(const uint32_t* __restrict__ words, uint32_t nb,
+                      const uint64_t* __restrict__ hashes, uint64_t n, uint64_t range,
+                      const uint32_t* __restrict__ spill, uint32_t* __restrict__ out) {
+  const uint32_t c = blockIdx.x;
+  if (spill[c] == 0) return;
+  const uint64_t a = static_cast<uint64_t>(c) * range;
+  if (a >= n) return;
+  const uint64_t b = a + range < n ? a + range : n;
+  const uint64_t pk = policy_evict_first(), pf = policy_evict_normal();
+  const unsigned lane = lane_id(), wpc = blockDim.x >> 5, wic = threadIdx.x >> 5;
+  for (uint64_t k0 = a + 32ull * wic; k0 < b; k0 += 32ull * wpc) {
+    const uint64_t k = k0 + lane;
+    bool hit = false;
+    if (k < b) {
+      const uint64_t h = load_key1(hashes + k, pk);
+      uint32_t w[8];
+      load_block_na(words + 8ull * block_of(h, nb), pf, w);
+      hit = block_has(w, static_cast<uint32_t>(h));
+    }
+    const uint32_t bits = __ballot_sync(0xFFFFFFFFu, hit);
+    if (lane == 0) out[k0 / 32] = bits;
+  }
+}
+
+// ---- host side ------------------------------------------------------------------------
+
 inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
 
 // Tile rounds for a sliced launch of `grid` CTAs of 8 warps over n keys into
@@ -773,15 +769,9 @@ int sliced_rounds(unsigned grid, uint64_t n, uint64_t filter_bytes, int min_roun
 // Dynamic shared memory a CTA may use on this architecture (227 KB), less a
 // margin for the kernel's static shared memory.
 constexpr size_t kSmemBudget = 227 * 1024 - 512;
+static_assert(scatter_smem_bytes(kMaxSlices) <= kSmemBudget, "scatter tables fit");
 
-// Scatter tile size: 8192 keys while three tiles, the index and the slice
-// tables fit, else 4096.
-uint32_t scatter_tile(uint32_t n_slices, bool with_index) {
-  return scatter_smem_bytes(8192, n_slices, with_index) <= kSmemBudget ? 8192u : 4096u;
-}
-
-// CTAs of the count and scatter passes (one per SM; both use the same key
-// ranges).
+// CTAs of the scatter (one per SM).
 uint32_t partition_ctas() { return static_cast<uint32_t>(sm_count()); }
 
 uint32_t slices_at(uint32_t num_blocks, int shift) {
@@ -789,7 +779,7 @@ uint32_t slices_at(uint32_t num_blocks, int shift) {
 }
 
 // Smallest slice shift lookups may take: 4 MiB, or larger until at most 1024
-// slices (the scatter's shared-memory tables).
+// slices (the answer pass's per-sub-range runs).
 int lookup_min_shift(uint32_t num_blocks) {
   int shift = kMinSliceShift;
   while (shift < kMaxSliceShift && slices_at(num_blocks, shift) > 1024) ++shift;
@@ -809,8 +799,8 @@ constexpr double kLiveBytes = 48.0 * 1024 * 1024;
 // Slice shift, grid and tile rounds of a partitioned lookup of n keys.  A
 // slice's blocks stay in L2 from its prefetch until its last key is
 // processed, so a slice plus the keys in flight (and those prefetched ahead)
-// must fit there, while the scatter of positions pays for every extra slice
-// (shorter runs): lookups take the largest slice (at most 32 MiB, no smaller than
+// must fit there, while the scatter pays for every extra slice (shorter
+// runs): lookups take the largest slice (at most 32 MiB, no smaller than
 // lookup_min_shift) within the live-set budget.  When even that slice leaves
 // too little room -- sparse batches, many filter bytes per key -- the grid
 // shrinks (to one CTA per SM at least) until the window fits beside it.
@@ -844,178 +834,204 @@ FindPlan find_plan(uint32_t num_blocks, uint64_t n) {
 // partition's fan-out stays near kTargetSlices (the scatter's runs per tile
 // shrink with more slices), between 4 and 32 MiB: measured 67.6 against
 // 60.3 G inserts/s on a 2 GiB filter.  Lookups: find_plan.
-int slice_shift(uint32_t num_blocks, uint64_t n, bool lookup) {
-  if (lookup) return find_plan(num_blocks, n).shift;
+int insert_shift(uint32_t num_blocks) {
   int shift = kMinSliceShift;
   while (shift < kMaxSliceShift && slices_at(num_blocks, shift) > kTargetSlices) ++shift;
   return shift;
 }
 
+// Capacity of one bucket: the keys a (slice, CTA) pair expects -- its range
+// times the slice's share of the blocks -- plus six standard deviations of
+// that binomial count and 64, rounded up to a multiple of 64.  Uniform hashes
+// overflow a bucket with probability ~1e-9, and an overflow only sends that
+// CTA's range down the random-access path.
+uint64_t bucket_cap(uint64_t range, uint32_t num_blocks, int shift) {
+  const double share =
+      std::fmin(1.0, static_cast<double>(1ull << shift) / static_cast<double>(num_blocks));
+  const double e = static_cast<double>(range) * share;
+  const uint64_t cap = static_cast<uint64_t>(std::ceil(e + 6.0 * std::sqrt(e) + 64.0));
+  return (cap + 63) & ~63ull;
+}
+
+// Largest batch a partitioned lookup handles in one piece (32-bit sorted
+// positions in the scatter's marks; the padded positions of a piece stay
+// below 2^32), and a partitioned insert (32-bit bucket cursors: ranges below
+// 2^31 keys).
+constexpr uint64_t kMaxIndexedKeys = 1ull << 31;
+constexpr uint64_t kMaxInsertKeys = 1ull << 34;
+
+// The geometry of one piece of n keys.
+struct Piece {
+  int shift;
+  uint32_t n_slices;
+  uint64_t range;
+  Buckets bk;
+  uint32_t rows;   // lookups: mark rows per CTA (sub-ranges + 1)
+  FindPlan plan;   // lookups
+};
+
+Piece piece_of(uint32_t num_blocks, uint64_t n, bool lookup) {
+  Piece p{};
+  const uint32_t ctas = partition_ctas();
+  if (lookup) {
+    p.plan = find_plan(num_blocks, n);
+    p.shift = p.plan.shift;
+  } else {
+    p.shift = insert_shift(num_blocks);
+  }
+  p.n_slices = slices_at(num_blocks, p.shift);
+  p.range = range_keys(n, ctas);
+  p.bk = Buckets{ctas, p.n_slices, bucket_cap(p.range, num_blocks, p.shift)};
+  p.rows = sub_ranges(p.range) + 1;
+  return p;
+}
+
+uint64_t piece_scratch_bytes(const Piece& p, bool with_index) {
+  const uint64_t cells = static_cast<uint64_t>(p.bk.ctas) * p.n_slices;
+  const uint64_t pos = p.bk.positions();
+  uint64_t bytes = 256 + align256(4 * cells) + align256(4ull * p.bk.ctas) + align256(8 * pos);
+  if (with_index)
+    bytes += align256(2 * pos) + align256(pos / 8) + align256(4 * cells * p.rows);
+  return bytes;
+}
+
+struct PartScratch {
+  unsigned long long* tiles;  // dynamic-schedule counter of the slice pass
+  uint32_t* fill;             // [ctas][n_slices] keys in bucket (q, c)
+  uint32_t* spill;            // [ctas] 1: the CTA's range overflowed a bucket
+  uint64_t* sorted;           // [positions] slice-ordered keys
+  uint16_t* idx;              // [positions] offset of the original position in its sub-range
+  uint32_t* sorted_bits;      // [positions / 32] answers in sorted order (lookups)
+  uint32_t* marks;            // [ctas][rows][n_slices] sub-range cursors (lookups)
+};
+
+PartScratch carve(void* scratch, const Piece& p) {
+  PartScratch r;
+  char* c = static_cast<char*>(scratch);
+  const uint64_t cells = static_cast<uint64_t>(p.bk.ctas) * p.n_slices;
+  const uint64_t pos = p.bk.positions();
+  r.tiles = reinterpret_cast<unsigned long long*>(c);
+  c += 256;
+  r.fill = reinterpret_cast<uint32_t*>(c);
+  c += align256(4 * cells);
+  r.spill = reinterpret_cast<uint32_t*>(c);
+  c += align256(4ull * p.bk.ctas);
+  r.sorted = reinterpret_cast<uint64_t*>(c);
+  c += align256(8 * pos);
+  r.idx = reinterpret_cast<uint16_t*>(c);
+  c += align256(2 * pos);
+  r.sorted_bits = reinterpret_cast<uint32_t*>(c);
+  c += align256(pos / 8);
+  r.marks = reinterpret_cast<uint32_t*>(c);
+  return r;
+}
+
+template <bool kFew, bool kIndex>
+sbbf_status launch_scatter(const uint64_t* hashes, uint64_t n, uint32_t nb, const Piece& p,
+                           const PartScratch& ps, unsigned* status, cudaStream_t s) {
+  const size_t smem = scatter_smem_bytes(p.n_slices);
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      scatter_kernel<kFew, kIndex>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      static_cast<int>(kSmemBudget));
+  if (attr != cudaSuccess) return record_cuda(attr);
+  scatter_kernel<kFew, kIndex><<<p.bk.ctas, kPartThreads, smem, s>>>(
+      hashes, n, nb, p.shift, p.bk, p.range, ps.sorted, kIndex ? ps.idx : nullptr,
+      kIndex ? ps.marks : nullptr, p.rows, ps.fill, ps.spill, ps.tiles, status);
+  return launch_status();
+}
+
+// Step 1: the slice-ordered keys (and positions), bucket fills and spills.
+sbbf_status scatter(const uint64_t* hashes, uint64_t n, uint32_t num_blocks, const Piece& p,
+                    const PartScratch& ps, bool with_index, unsigned* status, cudaStream_t s) {
+  const bool few = p.n_slices <= kFewSlices;
+  if (with_index)
+    return few ? launch_scatter<true, true>(hashes, n, num_blocks, p, ps, status, s)
+               : launch_scatter<false, true>(hashes, n, num_blocks, p, ps, status, s);
+  return few ? launch_scatter<true, false>(hashes, n, num_blocks, p, ps, status, s)
+             : launch_scatter<false, false>(hashes, n, num_blocks, p, ps, status, s);
+}
+
+bool piece_fits(const Piece& p, bool lookup) {
+  if (p.n_slices == 0 || p.n_slices > kMaxSlices || p.bk.cap >= (1ull << 31)) return false;
+  return !lookup || p.bk.positions() < (1ull << 32);
+}
+
 }  // namespace
 
 // Scratch bytes for a partitioned insert (or, with_index, lookup) of n keys
-// into num_blocks blocks.
+// into num_blocks blocks, processed in pieces: enough for the largest piece
+// (a full piece and the last one can have different geometries).
 uint64_t partition_scratch_bytes(uint32_t num_blocks, uint64_t n, bool with_index) {
-  // lookups: the most slices their rule can pick, so any piece fits
-  const uint64_t s = with_index ? slices_at(num_blocks, lookup_min_shift(num_blocks))
-                                : slices_at(num_blocks, slice_shift(num_blocks, n, false));
-  const uint64_t g = partition_ctas();
-  uint64_t bytes = align256(4 * g * s) + align256(8 * g * s) + align256(8 * (s + 1)) + 256 +
-                   align256(8 * n);
-  if (with_index) {
-    const uint64_t rows = sub_ranges(range_keys(n, static_cast<uint32_t>(g))) + 1;
-    bytes += align256(2 * n) + align256(8 * ((n + 63) / 64)) + align256(4 * g * rows * s);
+  const uint64_t max_piece = with_index ? kMaxIndexedKeys : kMaxInsertKeys;
+  if (n == 0) return 256;
+  const uint64_t full = n < max_piece ? n : max_piece;
+  uint64_t bytes = piece_scratch_bytes(piece_of(num_blocks, full, with_index), with_index);
+  const uint64_t last = n % max_piece;
+  if (n > max_piece && last > 0) {
+    const uint64_t b = piece_scratch_bytes(piece_of(num_blocks, last, with_index), with_index);
+    if (b > bytes) bytes = b;
   }
   return bytes;
 }
 
-// Largest batch a partitioned lookup handles in one pass (32-bit sorted
-// positions in the scatter's cursors and marks).
-constexpr uint64_t kMaxIndexedKeys = 1ull << 31;
-
-namespace {
-
-struct PartScratch {
-  unsigned* hist;                  // [ctas][n_slices]
-  unsigned long long* base;        // [ctas][n_slices]
-  unsigned long long* offsets;     // [n_slices + 1]
-  unsigned long long* tiles;       // dynamic-schedule counter
-  uint64_t* sorted;                // [n]
-  uint16_t* idx;                   // [n] offset of the original position in its sub-range
-  uint32_t* sorted_bits;           // [2 * ceil(n / 64)] answers in sorted order (lookups)
-  uint32_t* marks;                 // [ctas][rows][n_slices] sub-range cursors (lookups)
-  uint32_t rows;
-};
-
-PartScratch carve(void* scratch, uint32_t ctas, uint32_t n_slices, uint64_t n) {
-  PartScratch r;
-  char* p = static_cast<char*>(scratch);
-  const uint64_t cells = static_cast<uint64_t>(ctas) * n_slices;
-  r.hist = reinterpret_cast<unsigned*>(p);
-  p += align256(4 * cells);
-  r.base = reinterpret_cast<unsigned long long*>(p);
-  p += align256(8 * cells);
-  r.offsets = reinterpret_cast<unsigned long long*>(p);
-  p += align256(8 * (n_slices + 1));
-  r.tiles = reinterpret_cast<unsigned long long*>(p);
-  p += 256;
-  r.sorted = reinterpret_cast<uint64_t*>(p);
-  p += align256(8 * n);
-  r.idx = reinterpret_cast<uint16_t*>(p);
-  p += align256(2 * n);
-  r.sorted_bits = reinterpret_cast<uint32_t*>(p);
-  p += align256(8 * ((n + 63) / 64));
-  r.marks = reinterpret_cast<uint32_t*>(p);
-  r.rows = sub_ranges(range_keys(n, ctas)) + 1;
-  return r;
-}
-
-template <bool kFew, bool kIndex, uint32_t kT>
-sbbf_status launch_scatter(const uint64_t* hashes, uint64_t n, uint32_t nb, int shift,
-                           uint32_t n_slices, uint64_t range, uint32_t ctas, const PartScratch& ps,
-                           cudaStream_t s) {
-  const size_t smem = scatter_smem_bytes(kT, n_slices, kIndex);
-  static const cudaError_t attr = cudaFuncSetAttribute(
-      scatter_kernel<kFew, kIndex, kT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-      static_cast<int>(kSmemBudget));
-  if (attr != cudaSuccess) return record_cuda(attr);
-  scatter_kernel<kFew, kIndex, kT><<<ctas, kPartThreads, smem, s>>>(
-      hashes, n, nb, shift, n_slices, range, ps.base, ps.sorted, kIndex ? ps.idx : nullptr,
-      kIndex ? ps.marks : nullptr, ps.rows);
-  return launch_status();
-}
-
-// Steps 1-3: per-CTA counts, offsets and bases, and the slice-ordered keys
-// (and positions).
-sbbf_status partition(const uint64_t* hashes, uint64_t n, uint32_t num_blocks, int shift,
-                      uint32_t n_slices, const PartScratch& ps, bool with_index, cudaStream_t s) {
-  const bool few = n_slices <= kFewSlices;
-  const uint32_t ctas = partition_ctas();
-  const uint64_t range = range_keys(n, ctas);
-  const size_t count_smem = 16ull * kCountTile + 4ull * n_slices;
-  static const bool count_attr = [] {
-    cudaFuncSetAttribute(count_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(kSmemBudget));
-    cudaFuncSetAttribute(count_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(kSmemBudget));
-    return true;
-  }();
-  (void)count_attr;
-  if (few)
-    count_kernel<true><<<ctas, kCountThreads, count_smem, s>>>(hashes, n, num_blocks, shift,
-                                                              n_slices, range, ps.hist);
-  else
-    count_kernel<false><<<ctas, kCountThreads, count_smem, s>>>(hashes, n, num_blocks, shift,
-                                                               n_slices, range, ps.hist);
-  sbbf_status st = launch_status();
-  if (st != SBBF_OK) return st;
-  scan_kernel<<<1, 1024, 0, s>>>(ps.hist, ctas, n_slices, ps.offsets, ps.base);
-  if ((st = launch_status()) != SBBF_OK) return st;
-  const bool big = scatter_tile(n_slices, with_index) == 8192;
-  const auto args = [&](auto launch) {
-    return launch(hashes, n, num_blocks, shift, n_slices, range, ctas, ps, s);
-  };
-  if (few)
-    return with_index ? args(launch_scatter<true, true, 8192>)
-                      : args(launch_scatter<true, false, 8192>);
-  if (with_index)
-    return big ? args(launch_scatter<false, true, 8192>) : args(launch_scatter<false, true, 4096>);
-  return big ? args(launch_scatter<false, false, 8192>) : args(launch_scatter<false, false, 4096>);
-}
-
-}  // namespace
-
-// Partitioned insert (see the file comment).  `scratch` holds at least
-// partition_scratch_bytes(num_blocks, n, false) bytes of device memory.
+// Partitioned insert (see the file comment): scatter, slice-ordered insert
+// and the spilled ranges, per piece of at most kMaxInsertKeys keys.
+// `scratch` holds at least partition_scratch_bytes(num_blocks, n, false)
+// bytes of device memory.
 sbbf_status launch_insert_partitioned(uint32_t* words, uint32_t num_blocks, const uint64_t* hashes,
-                                      uint64_t n, void* scratch, cudaStream_t s) {
+                                      uint64_t n, void* scratch, unsigned* status,
+                                      cudaStream_t s) {
   SBBF_TRACE_NAMED("sbbf_partitioned_insert");
-  if (n == 0) return SBBF_OK;
-  const int shift = slice_shift(num_blocks, n, false);
-  const uint32_t n_slices = slices_at(num_blocks, shift);
-  if (n_slices == 0 || n_slices > kMaxSlices) return SBBF_EINVAL;
-  const PartScratch ps = carve(scratch, partition_ctas(), n_slices, n);
-  sbbf_status st = partition(hashes, n, num_blocks, shift, n_slices, ps, false, s);
-  if (st != SBBF_OK) return st;
-  SBBF_CUDA(cudaMemsetAsync(ps.tiles, 0, 8, s));
-  static int occ_ins = occupancy(sliced_insert_kernel, 256);
-  const unsigned grid = grid_for((n + 63) / 64, 8, occ_ins);
-  const int rounds = sliced_rounds(grid, n, 32ull * num_blocks, 1);
-  sliced_insert_kernel<<<grid, 256, 0, s>>>(words, num_blocks, shift, ps.sorted, n, ps.offsets,
-                                            n_slices, ps.tiles, rounds);
-  return launch_status();
+  static const int occ_ins = occupancy(sliced_insert_kernel, 256);
+  for (uint64_t off = 0; off < n; off += kMaxInsertKeys) {
+    const uint64_t m = n - off < kMaxInsertKeys ? n - off : kMaxInsertKeys;
+    const Piece p = piece_of(num_blocks, m, false);
+    if (!piece_fits(p, false)) return SBBF_EINVAL;
+    const PartScratch ps = carve(scratch, p);
+    sbbf_status st = scatter(hashes + off, m, num_blocks, p, ps, false, status, s);
+    if (st != SBBF_OK) return st;
+    const unsigned grid = grid_for(p.bk.positions() / 64, 8, occ_ins);
+    const int rounds = sliced_rounds(grid, m, 32ull * num_blocks, 1);
+    sliced_insert_kernel<<<grid, 256, 0, s>>>(words, num_blocks, p.shift, ps.sorted, p.bk, ps.fill,
+                                              ps.tiles, rounds);
+    if ((st = launch_status()) != SBBF_OK) return st;
+    fixup_insert_kernel<<<p.bk.ctas, kFixupThreads, 0, s>>>(words, num_blocks, hashes + off, m,
+                                                            p.range, ps.spill);
+    if ((st = launch_status()) != SBBF_OK) return st;
+  }
+  return SBBF_OK;
 }
 
 // Partitioned lookup of d_hashes[0..n) into the packed bitmask d_out (the
 // same bits as the unpartitioned lookup; every word of the answer is
-// written).  `scratch` holds at least partition_scratch_bytes(num_blocks,
-// min(n, 2^31), true) bytes; batches larger than 2^31 keys run in pieces of
-// 2^31 (a multiple of 32).
+// written): scatter, slice-ordered lookup, answers back to key order and the
+// spilled ranges, per piece of at most 2^31 keys (a multiple of 32).
+// `scratch` holds at least partition_scratch_bytes(num_blocks, n, true) bytes.
 sbbf_status launch_find_partitioned(const uint32_t* words, uint32_t num_blocks,
                                     const uint64_t* hashes, uint64_t n, uint32_t* d_out,
-                                    void* scratch, cudaStream_t s) {
+                                    void* scratch, unsigned* status, cudaStream_t s) {
   SBBF_TRACE_NAMED("sbbf_partitioned_find");
-  if (n == 0) return SBBF_OK;
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      unscatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmemBudget));
+  if (attr != cudaSuccess) return record_cuda(attr);
   for (uint64_t off = 0; off < n; off += kMaxIndexedKeys) {
     const uint64_t m = n - off < kMaxIndexedKeys ? n - off : kMaxIndexedKeys;
-    const FindPlan plan = find_plan(num_blocks, m);
-    const uint32_t n_slices = slices_at(num_blocks, plan.shift);
-    if (n_slices == 0 || n_slices > kMaxSlices) return SBBF_EINVAL;
-    const uint32_t ctas = partition_ctas();
-    const PartScratch ps = carve(scratch, ctas, n_slices, m);
-    sbbf_status st = partition(hashes + off, m, num_blocks, plan.shift, n_slices, ps, true, s);
+    const Piece p = piece_of(num_blocks, m, true);
+    if (!piece_fits(p, true)) return SBBF_EINVAL;
+    const PartScratch ps = carve(scratch, p);
+    sbbf_status st = scatter(hashes + off, m, num_blocks, p, ps, true, status, s);
     if (st != SBBF_OK) return st;
-    SBBF_CUDA(cudaMemsetAsync(ps.tiles, 0, 8, s));
-    static const cudaError_t attr = cudaFuncSetAttribute(
-        unscatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmemBudget));
-    if (attr != cudaSuccess) return record_cuda(attr);
-    sliced_find_kernel<<<plan.grid, 256, 0, s>>>(words, num_blocks, plan.shift, ps.sorted, m,
-                                                 ps.offsets, n_slices, ps.tiles, ps.sorted_bits,
-                                                 plan.rounds);
+    sliced_find_kernel<<<p.plan.grid, 256, 0, s>>>(words, num_blocks, p.shift, ps.sorted, p.bk,
+                                                   ps.fill, ps.tiles, ps.sorted_bits,
+                                                   p.plan.rounds);
     if ((st = launch_status()) != SBBF_OK) return st;
-    unscatter_kernel<<<ctas * (ps.rows - 1), kUnscatterThreads, unscatter_smem_bytes(n_slices),
-                       s>>>(ps.sorted_bits, ps.idx, ps.marks, m, range_keys(m, ctas), ps.rows,
-                            n_slices, d_out + off / 32);
+    unscatter_kernel<<<p.bk.ctas * (p.rows - 1), kUnscatterThreads,
+                       unscatter_smem_bytes(p.n_slices), s>>>(
+        ps.sorted_bits, ps.idx, ps.marks, m, p.bk.positions(), p.range, p.rows, p.n_slices,
+        d_out + off / 32);
+    if ((st = launch_status()) != SBBF_OK) return st;
+    fixup_find_kernel<<<p.bk.ctas, kFixupThreads, 0, s>>>(words, num_blocks, hashes + off, m,
+                                                          p.range, ps.spill, d_out + off / 32);
     if ((st = launch_status()) != SBBF_OK) return st;
   }
   return SBBF_OK;

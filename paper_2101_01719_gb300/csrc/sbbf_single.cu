@@ -116,6 +116,16 @@ bool want_partition(const sbbf_t* f, uint64_t n) {
 
 // Grows the filter's scratch (cudaMalloc, synchronous) to hold `bytes`.
 sbbf_status ensure_scratch(sbbf_t* f, size_t bytes) {
+  if (!f->status) {
+    unsigned* w = nullptr;
+    cudaError_t e = cudaMalloc(&w, 256);
+    if (e == cudaSuccess) e = cudaMemset(w, 0, 256);
+    if (e != cudaSuccess) {
+      if (w) cudaFree(w);
+      return record_cuda(e);
+    }
+    f->status = w;
+  }
   if (f->scratch_bytes >= bytes) return SBBF_OK;
   if (f->scratch) {
     cudaError_t e = cudaFree(f->scratch);
@@ -216,8 +226,36 @@ sbbf_status sbbf_destroy(sbbf_t* f) {
     cudaError_t e = cudaFree(f->scratch);
     if (e != cudaSuccess) st = record_cuda(e);
   }
+  if (f->status) {
+    cudaError_t e = cudaFree(f->status);
+    if (e != cudaSuccess) st = record_cuda(e);
+  }
   std::free(f);
   return st;
+}
+
+namespace {
+__global__ void or_status_kernel(unsigned* status, unsigned bits) { atomicOr(status, bits); }
+}  // namespace
+
+sbbf_status sbbf_device_status(sbbf_t* f, sbbf_stream_t stream) {
+  if (!f) return SBBF_EINVAL;
+  if (!f->status) return SBBF_OK;  // no partitioned pass has run on this filter
+  unsigned bits = 0;
+  SBBF_CUDA(cudaMemcpyAsync(&bits, f->status, sizeof bits, cudaMemcpyDeviceToHost, stream));
+  SBBF_CUDA(cudaStreamSynchronize(stream));
+  if (bits == 0) return SBBF_OK;
+  SBBF_CUDA(cudaMemsetAsync(f->status, 0, sizeof bits, stream));
+  return SBBF_ETIMEOUT;
+}
+
+sbbf_status sbbf_record_device_status(sbbf_t* f, uint32_t bits, sbbf_stream_t stream) {
+  if (!f || !on_device(f)) return SBBF_EINVAL;
+  const sbbf_status st = ensure_scratch(f, 0);  // allocates the word on first use
+  if (st != SBBF_OK) return st;
+  if (bits == 0) return SBBF_OK;
+  or_status_kernel<<<1, 1, 0, stream>>>(f->status, bits);
+  return launch_status();
 }
 
 uint32_t sbbf_num_blocks(const sbbf_t* f) { return f ? f->num_blocks : 0; }
@@ -246,7 +284,8 @@ sbbf_status sbbf_insert_hashes(sbbf_t* f, const uint64_t* d_hashes, size_t n,
   if (want_partition(f, n)) {
     const sbbf_status st = ensure_scratch(f, partition_scratch_bytes(f->num_blocks, n, false));
     if (st == SBBF_OK)
-      return launch_insert_partitioned(f->words, f->num_blocks, d_hashes, n, f->scratch, stream);
+      return launch_insert_partitioned(f->words, f->num_blocks, d_hashes, n, f->scratch, f->status,
+                                       stream);
     if (st != SBBF_ENOMEM || f->partition_mode == SBBF_PARTITION_ON) return st;
     // automatic mode without room for the scratch: insert unpartitioned
   }
@@ -270,12 +309,11 @@ sbbf_status sbbf_find_hashes(const sbbf_t* f, const uint64_t* d_hashes, size_t n
       (reinterpret_cast<uintptr_t>(d_out_bits) & 3))
     return SBBF_EINVAL;
   if (want_partition(f, n)) {
-    const uint64_t piece = n < (1ull << 31) ? n : (1ull << 31);
     const sbbf_status st =
-        ensure_scratch(const_cast<sbbf_t*>(f), partition_scratch_bytes(f->num_blocks, piece, true));
+        ensure_scratch(const_cast<sbbf_t*>(f), partition_scratch_bytes(f->num_blocks, n, true));
     if (st == SBBF_OK)
       return launch_find_partitioned(f->words, f->num_blocks, d_hashes, n, d_out_bits, f->scratch,
-                                     stream);
+                                     f->status, stream);
     if (st != SBBF_ENOMEM || f->partition_mode == SBBF_PARTITION_ON) return st;
   }
   return launch_find_filter(f, d_hashes, n, d_out_bits, stream);

@@ -56,6 +56,8 @@ SIGNATURES = {
     "sbbf_insert_hashes": (_int, [_P, _P, _sz, _P]),
     "sbbf_set_partitioning": (_int, [_P, _int]),
     "sbbf_partition_applies": (_int, [_P, _sz, _int, _P]),
+    "sbbf_device_status": (_int, [_P, _P]),
+    "sbbf_record_device_status": (_int, [_P, _u32, _P]),
     "sbbf_find_hashes": (_int, [_P, _P, _sz, _P, _P]),
     "sbbf_union": (_int, [_P, _P, _P]),
     "sbbf_copy_to_host": (_int, [_P, _P, _sz, _P]),
@@ -370,6 +372,23 @@ class Filter:
         check(lib().sbbf_partition_applies(self._h, n, 1 if lookup else 0, _c.byref(v)),
               "sbbf_partition_applies")
         return bool(v.value)
+
+    def device_status(self, stream=None) -> int:
+        """sbbf_device_status: OK, or ETIMEOUT when a device-side wait of a
+        partitioned call ran out since the last query (synchronises the
+        stream; reading clears the status)."""
+        with torch.cuda.device(self.device):
+            st = int(lib().sbbf_device_status(self._h, stream_handle(stream)))
+        if st not in (SBBF_OK, SBBF_ETIMEOUT):
+            check(st, "sbbf_device_status")
+        return st
+
+    def record_device_status(self, bits: int, stream=None):
+        """sbbf_record_device_status (testing the reporting path)."""
+        with torch.cuda.device(self.device):
+            check(lib().sbbf_record_device_status(self._h, bits, stream_handle(stream)),
+                  "sbbf_record_device_status")
+        return self
 
     def insert(self, hashes: torch.Tensor, stream=None):
         ptr = _hashes_ptr(hashes, self.device)

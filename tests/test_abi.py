@@ -69,6 +69,8 @@ def test_argument_checks_need_no_gpu(built):
     assert L.sbbf_partition_applies(None, 10, 0, ctypes.byref(flag)) == sbbf.SBBF_EINVAL
     assert flag.value == 7  # untouched on error
     assert L.sbbf_set_partitioning(None, 0) == sbbf.SBBF_EINVAL
+    assert L.sbbf_device_status(None, None) == sbbf.SBBF_EINVAL
+    assert L.sbbf_record_device_status(None, 1, None) == sbbf.SBBF_EINVAL
     assert L.sbbf_destroy(None) == sbbf.SBBF_OK
     assert L.sbbf_num_blocks(None) == 0
     assert L.sbbf_host_pipe_create(100, ctypes.byref(h)) == sbbf.SBBF_EINVAL  # not /64

@@ -67,9 +67,9 @@ def test_bench_uses_no_undefined_names():
 
 def test_step_kernel_counts():
     """gpu_launches: a step launches the clear, one kernel per unpartitioned
-    batch, four per partitioned insert batch and five per 2^31-key piece of a
-    partitioned lookup, plus one hashing kernel per partitioned batch of raw
-    keys."""
+    batch, three per 2^34-key piece of a partitioned insert batch and four per
+    2^31-key piece of a partitioned lookup, plus one hashing kernel per
+    partitioned batch of raw keys."""
     sys.path.insert(0, ROOT)
     import bench
 
@@ -82,6 +82,7 @@ def test_step_kernel_counts():
 
     assert bench.step_kernels(FakeFilter(False, False), [(0, 10)], 100, False) == 3
     assert bench.step_kernels(FakeFilter(False, False), [(0, 10), (10, 5)], 100, True) == 4
-    assert bench.step_kernels(FakeFilter(True, True), [(0, 10), (10, 5)], 100, False) == 1 + 8 + 5
-    assert bench.step_kernels(FakeFilter(True, False), [(0, 10)], 100, True) == 1 + 5 + 1
-    assert bench.step_kernels(FakeFilter(False, True), [(0, 10)], 2**31 + 1, True) == 1 + 1 + 10 + 1
+    assert bench.step_kernels(FakeFilter(True, True), [(0, 10), (10, 5)], 100, False) == 1 + 6 + 4
+    assert bench.step_kernels(FakeFilter(True, False), [(0, 10)], 100, True) == 1 + 4 + 1
+    assert bench.step_kernels(FakeFilter(False, True), [(0, 10)], 2**31 + 1, True) == 1 + 1 + 8 + 1
+    assert bench.step_kernels(FakeFilter(True, False), [(0, 2**34 + 1)], 1, False) == 1 + 6 + 1

@@ -509,3 +509,49 @@ def test_partitioned_find_many_sub_ranges():
     exp, _ = oracle.find_mt(ref, B, q, oracle.num_cores())
     assert np.array_equal(got[: sb.out_words(n)], exp)
     assert got[-1] == 0xFFFFFFFF
+
+
+def test_device_status_of_partitioned_calls():
+    """The bulk-copy waits of the partitioned passes report through the
+    filter's device status word: after ordinary partitioned calls no wait
+    ran out (SBBF_OK); a recorded timeout bit (set on the host side, as a
+    timed-out wait would) comes back once as SBBF_ETIMEOUT, then the word is
+    clear again.  No device wait is made to run out."""
+    B, n = 2**23 + 5, 5_000_001
+    keys = inp.stream(190, 0, n)
+    f = sb.Filter(B).set_partitioning(sb.PARTITION_ON)
+    assert f.device_status() == abi.SBBF_OK  # nothing ran yet
+    dk = to_dev(keys)
+    f.insert(dk)
+    bits = f.find(dk)
+    assert f.device_status() == abi.SBBF_OK
+    assert np.unpackbits(bits_np(bits).view(np.uint8), bitorder="little")[:n].all()
+    for b in (1, 2, 3):
+        f.record_device_status(b)
+        assert f.device_status() == abi.SBBF_ETIMEOUT
+        assert f.device_status() == abi.SBBF_OK
+    f.record_device_status(0)
+    assert f.device_status() == abi.SBBF_OK
+
+
+@pytest.mark.parametrize("crowd_frac", [1.0, 0.3])
+def test_partitioned_crowded_slices_take_the_fixup_path(crowd_frac):
+    """Hashes that crowd one slice far beyond its share overflow their
+    scatter buckets; the ranges of the CTAs that spilled are redone by the
+    unpartitioned path, so inserts and lookups still equal the oracle's, when
+    every CTA spills (all hashes in the first 1/64 of the blocks) and when
+    only the CTAs holding the first 30% of the batch do."""
+    B, n = 2**23 + 5, 5_000_003
+    keys = inp.stream(191, 0, n)
+    k = int(n * crowd_frac)
+    keys[:k] = keys[:k] >> np.uint64(6)  # top bits below 2^58: blocks below B/64
+    ref = _oracle_filter(B, keys)
+    f = sb.Filter(B).set_partitioning(sb.PARTITION_ON)
+    dk = to_dev(keys)
+    f.insert(dk)
+    assert np.array_equal(f.to_numpy(), ref)
+    q = np.concatenate([inp.stream(191, 1, n), keys[::3]])
+    q[: n // 2] = q[: n // 2] >> np.uint64(6)
+    got = bits_np(f.find(to_dev(q)))
+    assert np.array_equal(got, oracle.find(ref, B, q))
+    assert f.device_status() == abi.SBBF_OK
