@@ -64,6 +64,9 @@ def parse_args(argv=None):
                    help="auto: with the default workload, also time the 11 bits/key, 32 GiB "
                         "and 1 MiB filters as rows of the line")
     p.add_argument("--row-steps", type=int, default=5)
+    p.add_argument("--parallelism", choices=["sharded", "replicas"], default="sharded",
+                   help="N > 1 ranks: one filter sharded by block range over the ranks "
+                        "(all-to-all of hashes and answers), or independent replicas")
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="approximate CPU work for the oracle baseline")
@@ -584,6 +587,123 @@ def run_ours(args):
     return line
 
 
+
+# ---- N ranks: one filter sharded by block range -----------------------------------
+
+def run_sharded(args):
+    """Weak scaling of one filter over N GPUs: the filter has N times the
+    workload's blocks, each rank owning one workload-sized block range; each
+    rank inserts its own n_insert hashes and looks up its own n_lookup
+    queries (members drawn from its own inserts), routed to the owners by
+    all-to-all exchanges (paper_2101_01719_gb300/sharded.py)."""
+    import numpy as np
+    import torch
+
+    import paper_2101_01719_gb300 as sb
+    from paper_2101_01719_gb300 import workloads as wl
+    from paper_2101_01719_gb300.sharded import DeviceOps, ShardedFilter, TorchComm
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = init_dist(world, "nccl")
+    w = wl.WORKLOADS[args.workload]
+    stream = torch.cuda.current_stream()
+    num_blocks = w.num_blocks * world
+    sf = ShardedFilter(num_blocks, comm=TorchComm(device=dev), ops=DeviceOps(dev))
+    ins = wl.gen_inserts(w, rank * w.n_insert, w.n_insert, device=dev)
+    qry = torch.empty(w.n_lookup, dtype=torch.int64, device=dev)
+    sb.fill_queries(qry, lookup_slice_start(rank, w.n_lookup), wl.seed(w.cfg, wl.ROLE_INSERT),
+                    rank * w.n_insert, w.n_insert, wl.seed(w.cfg, wl.ROLE_FRESH),
+                    wl.seed(w.cfg, wl.ROLE_MEMBER), wl.member_threshold(w.member_frac))
+    batches = [(s0, min(w.insert_batch, w.n_insert - s0))
+               for s0 in range(0, w.n_insert, w.insert_batch)]
+
+    def step(ev=None):
+        if sf.local is not None:
+            sf.local.clear()
+        for s0, cnt in batches:
+            sf.insert(ins[s0:s0 + cnt])
+        if ev is not None:
+            ev[0].record(stream)
+        out = sf.find(qry)
+        if ev is not None:
+            ev[1].record(stream)
+        return out
+
+    for _ in range(max(args.warmup, 3)):
+        out = step()
+    torch.cuda.synchronize()
+    hits = int(sb.count_bits(out, w.n_lookup).item())
+    props = torch.cuda.get_device_properties(dev)
+    uuid = str(getattr(props, "uuid", ""))
+    sampler = ClockSampler(uuid if uuid.startswith("GPU-") else "GPU-" + uuid).start()
+    time.sleep(0.3)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    barrier(dist)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(args.steps):
+        step(ev[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    sampler.stop()
+    slowest_ms = max_over_ranks(dist, t0.elapsed_time(t1), dev)
+    find_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+    keys_per_step = w.n_insert + w.n_lookup
+    value = aggregate([keys_per_step * args.steps] * world, slowest_ms / 1e3) / 1e9
+
+    # end to end: the step's inputs from pinned host memory, answers back
+    h_ins, h_q = ins.cpu().pin_memory(), qry.cpu().pin_memory()
+    h_out = torch.empty(sb.out_words(w.n_lookup), dtype=torch.int32).pin_memory()
+    barrier(dist)
+    torch.cuda.synchronize()
+    a = time.perf_counter()
+    e2e_steps = max(1, args.e2e_steps)
+    for _ in range(e2e_steps):
+        ins.copy_(h_ins, non_blocking=True)
+        qry.copy_(h_q, non_blocking=True)
+        h_out.copy_(step(), non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(dist, time.perf_counter() - a, dev)
+    peak, peak_kind = measured_peaks()
+    if rank != 0:
+        return None
+    config = workload_config(w, world)
+    config.update({"num_blocks": num_blocks, "filter_bytes": 32 * num_blocks,
+                   "n_insert": w.n_insert * world, "n_lookup": w.n_lookup * world,
+                   "parallelism": "one filter sharded by block range over %d GPUs "
+                                  "(all-to-all of hashes and answer words)" % world})
+    return {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3),
+        "ms_per_step": round(slowest_ms / args.steps, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (seeded splitmix64 hashes generated on the device)",
+        "config": config,
+        "roofline": {"bound": "hbm", "kernel": "sharded step (route, exchange, shard kernels)",
+                     "achieved": round(LOOKUP_HBM_BYTES_HBM_RESIDENT * w.n_lookup
+                                       / (find_ms / 1e3) / 1e9, 1),
+                     "peak": peak, "unit": "GB/s", "peak_kind": peak_kind,
+                     "frac": round(LOOKUP_HBM_BYTES_HBM_RESIDENT * w.n_lookup
+                                   / (find_ms / 1e3) / 1e9 / peak, 4),
+                     "bytes_per_key": LOOKUP_HBM_BYTES_HBM_RESIDENT, "traffic": None},
+        "rows": {"lookup_gkeys_s_per_gpu": round(w.n_lookup / (find_ms / 1e3) / 1e9, 3),
+                 "lookup_ms": round(find_ms, 4), "lookup_hit_frac": round(hits / w.n_lookup, 5)},
+        "e2e": {"value": round(keys_per_step * e2e_steps * world / e2e_s / 1e9, 3), "unit": UNIT,
+                "h2d_bytes_per_step": 8 * keys_per_step,
+                "d2h_bytes_per_step": 4 * sb.out_words(w.n_lookup)},
+        # per step: the clear; per insert batch the route (count, scan, scatter)
+        # and the shard insert; the lookup's route, shard lookup and answer
+        # reassembly (NCCL's own kernels not counted)
+        "gpu_launches": (1 + 4 * len(batches) + 5) * args.steps,
+        "clocks": sampler.summary(),
+    }
+
+
 # ---- many filters: one graph launch per batch vs one launch per filter ---------
 
 def run_multi(args):
@@ -882,6 +1002,8 @@ def main(argv=None):
         line = run_multi(args)
     elif args.workload in wl.SERVING_WORKLOADS:
         line = run_serving(args)
+    elif dist_env()[1] > 1 and args.parallelism == "sharded":
+        line = run_sharded(args)
     else:
         line = run_ours(args)
     if line is not None:

@@ -690,6 +690,79 @@ sbbf_status sbbf_multi_graph_launch(sbbf_multi_graph_t *g,
                                     const uint64_t *d_q_offsets, size_t n_q,
                                     uint32_t *d_out_bits, sbbf_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * One filter sharded by block range over several devices.
+ *
+ * The appendix's block_index sends every hash to exactly one block, so a
+ * filter of B blocks split into contiguous block ranges is the same filter:
+ * shard s of G owns global blocks [s P, min(B, (s + 1) P)), P = ceil(B / G),
+ * held as a filter of its own (sbbf_create with hi - lo blocks), and a hash
+ * belongs to the shard that owns its block.  A batch on one device is
+ * routed (sbbf_shard_route), exchanged with the other devices by the
+ * caller's collective library (an all-to-all of the routed hashes, with the
+ * per-shard counts), inserted or looked up on the local range
+ * (sbbf_shard_insert / sbbf_shard_find), and for lookups the answer words go
+ * back by the reverse all-to-all and are put in query order
+ * (sbbf_shard_unpermute).  The results equal those of the unsharded filter
+ * bit for bit.
+ * ---------------------------------------------------------------------- */
+
+/* The global block range [*lo, *hi) of shard `shard` of n_shards (empty when
+ * the filter has fewer blocks than shards need).  Pure arithmetic; no device
+ * is needed.  Errors: SBBF_EINVAL (num_blocks or n_shards 0, n_shards above
+ * 1024, shard >= n_shards, NULL out pointers). */
+sbbf_status sbbf_shard_range(uint32_t num_blocks, uint32_t n_shards, uint32_t shard,
+                             uint32_t *lo, uint32_t *hi);
+
+/* Entries sbbf_shard_route may write to d_routed / d_perm: n, plus 31 per
+ * shard when padding. */
+size_t sbbf_shard_routed_capacity(size_t n, uint32_t n_shards, int pad);
+
+/* Device scratch bytes sbbf_shard_route needs (per SM and shard). */
+size_t sbbf_shard_route_scratch_bytes(size_t n, uint32_t n_shards);
+
+/* Groups d_hashes[0..n) (device, 8-byte aligned, n < 2^32) by owner shard
+ * of a num_blocks-block filter split n_shards ways: owner 0's hashes first,
+ * then owner 1's, ...; d_routed[i] is a hash and d_perm[i] its index in
+ * d_hashes.  d_counts[s] (device, n_shards uint64) receives the number of
+ * entries of owner s's group.  With pad != 0 every group is padded to a
+ * multiple of 32 entries with a hash of the owner's first block and
+ * d_perm = 0xFFFFFFFF, so that a group's lookup answers are whole 32-bit
+ * words; padding is for lookups only (an insert of a padding hash would set
+ * bits).  The order within a group is not specified.  d_routed and d_perm
+ * hold sbbf_shard_routed_capacity(n, n_shards, pad) entries; d_scratch
+ * (device, 8-byte aligned) holds sbbf_shard_route_scratch_bytes bytes.
+ * Asynchronous on stream.  Errors: SBBF_EINVAL (sizes, NULL, alignment,
+ * n_shards above 1024), SBBF_ECUDA. */
+sbbf_status sbbf_shard_route(const uint64_t *d_hashes, size_t n, uint32_t num_blocks,
+                             uint32_t n_shards, int pad, uint64_t *d_routed, uint32_t *d_perm,
+                             uint64_t *d_counts, void *d_scratch, size_t scratch_bytes,
+                             sbbf_stream_t stream);
+
+/* Insert d_hashes[0..n) into f, the shard holding global blocks
+ * [lo, lo + sbbf_num_blocks(f)) of a num_blocks-block filter (appendix
+ * add_hash at block block_index(h, num_blocks) - lo); hashes whose block
+ * lies outside the range are skipped.  f has 8 lanes.  Errors: SBBF_EINVAL
+ * (NULL, other lane count, a range past num_blocks, misaligned), SBBF_ECUDA. */
+sbbf_status sbbf_shard_insert(sbbf_t *f, uint32_t num_blocks, uint32_t lo,
+                              const uint64_t *d_hashes, size_t n, sbbf_stream_t stream);
+
+/* Look up d_hashes[0..n) in shard f (as sbbf_shard_insert) into the packed
+ * bitmask d_out_bits ((n + 31) / 32 words); hashes outside the range answer
+ * 0.  Errors as sbbf_shard_insert; d_out_bits NULL or not 4-byte aligned is
+ * SBBF_EINVAL. */
+sbbf_status sbbf_shard_find(const sbbf_t *f, uint32_t num_blocks, uint32_t lo,
+                            const uint64_t *d_hashes, size_t n, uint32_t *d_out_bits,
+                            sbbf_stream_t stream);
+
+/* Answers back to query order: zeroes d_out_bits ((n + 31) / 32 words) and
+ * sets bit d_perm[i] for every set bit i of d_routed_bits (answers of the
+ * n_routed routed entries) whose d_perm is not padding.  Errors:
+ * SBBF_EINVAL (NULL with a nonzero size, misaligned), SBBF_ECUDA. */
+sbbf_status sbbf_shard_unpermute(const uint32_t *d_routed_bits, const uint32_t *d_perm,
+                                 size_t n_routed, size_t n, uint32_t *d_out_bits,
+                                 sbbf_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -206,17 +206,19 @@ struct UnitIter {
 // word j of the key's block.
 template <class R, class S>
 __device__ __forceinline__ void insert_group8(uint32_t* __restrict__ words, R& res, const S& src,
-                                              uint64_t n, uint64_t pol, uint64_t g) {
+                                              uint64_t n, uint64_t pol, uint64_t g,
+                                              uint64_t lim = ~0ull) {
   const unsigned lane = lane_id();
   const uint32_t seed = lane_seed(lane & 7);
   uint32_t* const word_j = words + (lane & 7);
   const int group_base = static_cast<int>(lane & ~7u);
   const uint64_t k = g * 64 + 2 * lane;
   uint64_t h0, h1;
-  src.pair(k, n, pol, h0, h1);
+  src.pair(k, n, pol, h0, h1);  // keys [0, n) are readable; [0, min(n, lim)) are inserted
   res.begin_chunk(g * 64);
-  const uint64_t b0 = k < n ? res.block(k, h0) : kNoBlock64;
-  const uint64_t b1 = k + 1 < n ? res.block(k + 1, h1) : kNoBlock64;
+  const uint64_t end = n < lim ? n : lim;
+  const uint64_t b0 = k < end ? res.block(k, h0) : kNoBlock64;
+  const uint64_t b1 = k + 1 < end ? res.block(k + 1, h1) : kNoBlock64;
   const uint32_t x0 = static_cast<uint32_t>(h0), x1 = static_cast<uint32_t>(h1);
 #pragma unroll
   for (int r = 0; r < 16; ++r) {

@@ -144,13 +144,15 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// Polls the mbarrier phase with the given parity; false after kWaitNs.
+// Waits for the mbarrier phase with the given parity; false after kWaitNs.
+// try_wait suspends the thread in hardware for a while when the phase is not
+// complete yet, so waiting threads do not take issue slots from the others.
 __device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity) {
   const uint64_t t0 = global_ns();
   for (;;) {
     uint32_t done;
     asm volatile(
-        "{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; "
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "
         "selp.u32 %0, 1, 0, p; }"
         : "=r"(done)
         : "r"(bar), "r"(parity)
@@ -404,16 +406,18 @@ __global__ void __launch_bounds__(kPartThreads, 1)
 
 // One past the last key of the 64-position group g: a group lies within one
 // bucket (cap is a multiple of 64), whose first fill[c][q] positions hold
-// keys.
+// keys.  Group indexes stay below 2^32 (positions below 2^38), so the
+// divisions are 32-bit.
 __device__ __forceinline__ uint64_t group_end(const Buckets& bk, const uint32_t* __restrict__ fill,
                                               uint64_t g) {
-  const uint64_t per = bk.cap >> 6;            // groups per bucket
-  const uint64_t bucket = g / per;             // q * ctas + c
-  const uint64_t o = (g - bucket * per) << 6;  // the group's offset in its bucket
-  const uint32_t q = static_cast<uint32_t>(bucket / bk.ctas);
-  const uint32_t c = static_cast<uint32_t>(bucket - static_cast<uint64_t>(q) * bk.ctas);
-  const uint64_t f = fill[static_cast<uint64_t>(c) * bk.n_slices + q];
-  const uint64_t valid = f > o ? (f - o < 64 ? f - o : 64) : 0;
+  const uint32_t g32 = static_cast<uint32_t>(g);
+  const uint32_t per = static_cast<uint32_t>(bk.cap >> 6);  // groups per bucket
+  const uint32_t bucket = g32 / per;                        // q * ctas + c
+  const uint32_t o = (g32 - bucket * per) << 6;             // the group's offset in its bucket
+  const uint32_t q = bucket / bk.ctas;
+  const uint32_t c = bucket - q * bk.ctas;
+  const uint32_t f = __ldg(fill + static_cast<uint64_t>(c) * bk.n_slices + q);
+  const uint32_t valid = f > o ? (f - o < 64 ? f - o : 64) : 0;
   return (g << 6) + valid;
 }
 
@@ -491,7 +495,7 @@ __global__ void __launch_bounds__(256)
                          int rounds) {
   __shared__ unsigned long long s_tile;
   const unsigned wpc = blockDim.x >> 5, wic = threadIdx.x >> 5;
-  const uint64_t n_groups = bk.positions() >> 6;
+  const uint64_t n_pos = bk.positions(), n_groups = n_pos >> 6;
   const uint64_t groups_per_tile = static_cast<uint64_t>(wpc) * rounds;
   const uint64_t keys_per_tile = groups_per_tile * 64;
   const uint64_t pol = policy_evict_first();
@@ -512,7 +516,9 @@ __global__ void __launch_bounds__(256)
       prefetch_positions(words, nb, shift, bk, g0 * 64 + ahead, g0 * 64 + ahead + keys_per_tile);
     for (int r = 0; r < rounds; ++r) {
       const uint64_t g = g0 + static_cast<uint64_t>(r) * wpc + wic;
-      if (g < n_groups) insert_group8(words, res, HashInput(keys), group_end(bk, fill, g), pol, g);
+      // the group's keys are loaded whole while its fill is looked up
+      if (g < n_groups)
+        insert_group8(words, res, HashInput(keys), n_pos, pol, g, group_end(bk, fill, g));
     }
   }
 }
@@ -543,7 +549,7 @@ __global__ void __launch_bounds__(256, 4)
                        uint32_t* __restrict__ sorted_bits, int rounds) {
   __shared__ unsigned long long s_tile;
   const unsigned wpc = blockDim.x >> 5, wic = threadIdx.x >> 5, lane = lane_id();
-  const uint64_t n_groups = bk.positions() >> 6;
+  const uint64_t n_pos = bk.positions(), n_groups = n_pos >> 6;
   const uint64_t groups_per_tile = static_cast<uint64_t>(wpc) * rounds;
   const uint64_t keys_per_tile = groups_per_tile * 64;
   const uint64_t pk = policy_evict_first();
@@ -575,8 +581,10 @@ __global__ void __launch_bounds__(256, 4)
       for (int u = 0; u < 2; ++u) {
         const uint64_t g = g0 + static_cast<uint64_t>(r + u) * wpc + wic;
         k[u] = g * 64 + 2 * lane;
-        lim[u] = g < n_groups ? group_end(bk, fill, g) : 0;  // keys [64 g, lim) are valid
-        HashInput(keys).pair(k[u], lim[u], pk, h[u][0], h[u][1]);
+        // the group's keys are loaded whole (every position is readable)
+        // while its fill is looked up; keys [64 g, lim) are valid
+        HashInput(keys).pair(k[u], n_pos, pk, h[u][0], h[u][1]);
+        lim[u] = g < n_groups ? group_end(bk, fill, g) : 0;
       }
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
@@ -953,6 +961,7 @@ sbbf_status scatter(const uint64_t* hashes, uint64_t n, uint32_t num_blocks, con
 
 bool piece_fits(const Piece& p, bool lookup) {
   if (p.n_slices == 0 || p.n_slices > kMaxSlices || p.bk.cap >= (1ull << 31)) return false;
+  if ((p.bk.positions() >> 6) >= (1ull << 32)) return false;  // 32-bit group indexes
   return !lookup || p.bk.positions() < (1ull << 32);
 }
 

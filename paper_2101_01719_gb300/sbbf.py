@@ -111,6 +111,13 @@ SIGNATURES = {
     "sbbf_server_stats": (_int, [_P, _P]),
     "sbbf_server_replay": (_int, [_P, _P, _P, _sz, _P]),
     "sbbf_server_replay_serial": (_int, [_P, _P, _P, _sz, _P]),
+    "sbbf_shard_range": (_int, [_u32, _u32, _u32, _c.POINTER(_u32), _c.POINTER(_u32)]),
+    "sbbf_shard_routed_capacity": (_sz, [_sz, _u32, _int]),
+    "sbbf_shard_route_scratch_bytes": (_sz, [_sz, _u32]),
+    "sbbf_shard_route": (_int, [_P, _sz, _u32, _u32, _int, _P, _P, _P, _P, _sz, _P]),
+    "sbbf_shard_insert": (_int, [_P, _u32, _u32, _P, _sz, _P]),
+    "sbbf_shard_find": (_int, [_P, _u32, _u32, _P, _sz, _P, _P]),
+    "sbbf_shard_unpermute": (_int, [_P, _P, _sz, _sz, _P, _P]),
 }
 
 OP_INSERT, OP_FIND = 0, 1
@@ -818,3 +825,66 @@ class Server:
             check(fn(self._h, reqs.ctypes.data, arr.ctypes.data, len(reqs), lat.ctypes.data),
                   "sbbf_server_replay_serial" if serial else "sbbf_server_replay")
         return lat
+
+
+# ---- one filter sharded by block range (see sbbf.h) ------------------------------
+
+def shard_range(num_blocks: int, n_shards: int, shard: int):
+    """(lo, hi): the global blocks shard `shard` of n_shards owns."""
+    lo, hi = _u32(), _u32()
+    check(lib().sbbf_shard_range(num_blocks, n_shards, shard, _c.byref(lo), _c.byref(hi)),
+          "sbbf_shard_range")
+    return int(lo.value), int(hi.value)
+
+
+def shard_route(hashes: torch.Tensor, num_blocks: int, n_shards: int, pad: bool, stream=None):
+    """sbbf_shard_route: (routed hashes, their query indexes, per-shard counts),
+    device tensors (int64, int32, int64); the counts stay on the device."""
+    n = hashes.numel()
+    dev = hashes.device
+    cap = int(lib().sbbf_shard_routed_capacity(n, n_shards, 1 if pad else 0))
+    routed = torch.empty(cap, dtype=torch.int64, device=dev)
+    perm = torch.empty(cap, dtype=torch.int32, device=dev)
+    counts = torch.empty(n_shards, dtype=torch.int64, device=dev)
+    sb = int(lib().sbbf_shard_route_scratch_bytes(n, n_shards))
+    scratch = torch.empty((sb + 7) // 8, dtype=torch.int64, device=dev)
+    with torch.cuda.device(dev):
+        check(lib().sbbf_shard_route(_hashes_ptr(hashes, dev) if n else None, n, num_blocks,
+                                     n_shards, 1 if pad else 0, routed.data_ptr(),
+                                     perm.data_ptr(), counts.data_ptr(), scratch.data_ptr(),
+                                     scratch.numel() * 8, stream_handle(stream)),
+              "sbbf_shard_route")
+    return routed, perm, counts
+
+
+def shard_insert(f: "Filter", num_blocks: int, lo: int, hashes: torch.Tensor, stream=None):
+    with torch.cuda.device(f.device):
+        check(lib().sbbf_shard_insert(f.handle, num_blocks, lo,
+                                      _hashes_ptr(hashes, f.device) if hashes.numel() else None,
+                                      hashes.numel(), stream_handle(stream)), "sbbf_shard_insert")
+
+
+def shard_find(f: "Filter", num_blocks: int, lo: int, hashes: torch.Tensor, out=None,
+               stream=None) -> torch.Tensor:
+    n = hashes.numel()
+    if out is None:
+        out = torch.empty(out_words(n), dtype=torch.int32, device=f.device)
+    with torch.cuda.device(f.device):
+        check(lib().sbbf_shard_find(f.handle, num_blocks, lo,
+                                    _hashes_ptr(hashes, f.device) if n else None, n,
+                                    out.data_ptr() if n else None, stream_handle(stream)),
+              "sbbf_shard_find")
+    return out
+
+
+def shard_unpermute(routed_bits: torch.Tensor, perm: torch.Tensor, n_routed: int, n: int,
+                    out=None, stream=None) -> torch.Tensor:
+    dev = perm.device
+    if out is None:
+        out = torch.empty(out_words(n), dtype=torch.int32, device=dev)
+    with torch.cuda.device(dev):
+        check(lib().sbbf_shard_unpermute(routed_bits.data_ptr() if n_routed else None,
+                                         perm.data_ptr() if n_routed else None, n_routed, n,
+                                         out.data_ptr() if n else None, stream_handle(stream)),
+              "sbbf_shard_unpermute")
+    return out
