@@ -348,6 +348,45 @@ def measure_row(name: str, dev, stream, peak: float, l2_bytes: int, steps: int,
     return row
 
 
+def batched_and_serving_rows(args) -> dict:
+    """The batched form (4096 filters, one CUDA-graph launch per step against
+    one launch per filter) and the serving form (256 resident filters, a
+    1M-request prefix of the 10M-request workload) as rows of the default
+    line, with the fields that carry their targets."""
+    import copy
+
+    import torch
+
+    a = copy.copy(args)
+    a.steps, a.warmup = 3, 1
+    a.workload = "sbbf_4096filters_1k-4M_keys_10.5bpk_4x_lookup"
+    m = run_multi(a)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    a.workload = "sbbf_serve_256filters_128KiB-1GiB_70pct_lookup"
+    a.requests, a.serial_requests = 1_000_000, 50_000
+    sv = run_serving(a)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    out = {}
+    if m is not None:
+        out["batched_4096filters"] = {
+            "gkeys_s": m["value"], "ms_per_step": m["ms_per_step"],
+            "per_filter_launches_gkeys_s": m["rows"]["per_filter_launches_gkeys_s"],
+            "batched_over_per_filter": m["rows"]["batched_over_per_filter"],
+            "identical_results": m["rows"]["identical_results"],
+            "lookup_roofline_frac": m["roofline"]["frac"], "config": m["config"]["form"]}
+    if sv is not None:
+        out["serving_256filters_1M_requests"] = {
+            "saturation": sv["saturation"], "loads": sv["loads"],
+            "serial_per_request_launches": sv["serial_per_request_launches"],
+            "batched_same_requests": sv["batched_same_requests"],
+            "half_budget": {k: sv["half_budget"][k] for k in
+                            ("gkeys_s", "p50_ms", "p99_ms", "budget_bytes")},
+            "filter_bytes_total": sv["config"]["filter_bytes_total"]}
+    return out
+
+
 # ---- our arm ----------------------------------------------------------------
 
 def run_ours(args):
@@ -541,6 +580,7 @@ def run_ours(args):
             big = wl.WORKLOADS[name].filter_bytes > (1 << 31)
             rows_extra[name] = measure_row(name, dev, stream, peak, l2_bytes, args.row_steps,
                                            ("auto", "on") if big else ("auto",))
+        rows_extra.update(batched_and_serving_rows(args))
     if rank != 0:
         return None
     config = workload_config(w, world, args.lanes, args.keys)

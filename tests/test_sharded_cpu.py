@@ -49,6 +49,8 @@ def _rank_main(rank, world, port, num_blocks, n_per_rank, errq):
             for r in range(world)])
         q = np.concatenate([inp.stream(cfg, 1, 3001 + 17 * rank, start=rank * 10**6),
                             all_keys[rank::world]])
+        if world == 4 and rank == 1:
+            q = q[:0]  # a rank with no queries still takes part in the exchanges
         bits = sf.find(torch.from_numpy(q.view(np.int64).copy())).numpy().view(np.uint32)
 
         ref = oracle.new_filter(num_blocks)
