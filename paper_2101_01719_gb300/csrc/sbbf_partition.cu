@@ -54,8 +54,16 @@ constexpr int kMaxSliceShift = 20;       // 2^20 blocks (32 MiB) per slice
 constexpr uint32_t kTargetSlices = 512;
 constexpr uint32_t kMaxSlices = 4096;    // num_blocks < 2^32 at the largest slice
 constexpr uint32_t kFewSlices = 32;      // ballot ranking up to this many slices
-constexpr int kPartThreads = 1024;
-constexpr uint32_t kTile = 8192;         // keys per scatter tile
+// Scatter CTAs resident per SM (1: 1024 threads and 8192-key tiles; 2: two
+// CTAs of 512 threads and 4096-key tiles, whose barriers and ranking then
+// overlap each other's stores).
+#ifndef SBBF_SCATTER_CTAS_PER_SM
+#define SBBF_SCATTER_CTAS_PER_SM 1
+#endif
+constexpr int kScatterCtasPerSm = SBBF_SCATTER_CTAS_PER_SM;
+static_assert(kScatterCtasPerSm == 1 || kScatterCtasPerSm == 2, "one or two scatter CTAs per SM");
+constexpr int kPartThreads = 1024 / kScatterCtasPerSm;
+constexpr uint32_t kTile = 8192 / kScatterCtasPerSm;  // keys per scatter tile
 constexpr uint32_t kPer = kTile / kPartThreads;
 
 __device__ __forceinline__ uint32_t slice_of(uint64_t h, uint32_t nb, int shift) {
@@ -272,7 +280,7 @@ __host__ __device__ constexpr size_t scatter_smem_bytes(uint32_t n_slices) {
 // sub-range start (and after the last tile) to marks[c][u][q], `rows` rows
 // per CTA.  CTA 0 also resets the slice pass's tile counter.
 template <bool kFew, bool kIndex>
-__global__ void __launch_bounds__(kPartThreads, 1)
+__global__ void __launch_bounds__(kPartThreads, kScatterCtasPerSm)
     scatter_kernel(const uint64_t* __restrict__ hashes, uint64_t n, uint32_t nb, int shift,
                    Buckets bk, uint64_t range, uint64_t* __restrict__ out,
                    uint16_t* __restrict__ out_idx, uint32_t* __restrict__ marks, uint32_t rows,
@@ -779,8 +787,8 @@ int sliced_rounds(unsigned grid, uint64_t n, uint64_t filter_bytes, int min_roun
 constexpr size_t kSmemBudget = 227 * 1024 - 512;
 static_assert(scatter_smem_bytes(kMaxSlices) <= kSmemBudget, "scatter tables fit");
 
-// CTAs of the scatter (one per SM).
-uint32_t partition_ctas() { return static_cast<uint32_t>(sm_count()); }
+// CTAs of the scatter (kScatterCtasPerSm per SM).
+uint32_t partition_ctas() { return static_cast<uint32_t>(sm_count() * kScatterCtasPerSm); }
 
 uint32_t slices_at(uint32_t num_blocks, int shift) {
   return static_cast<uint32_t>((static_cast<uint64_t>(num_blocks) + (1ull << shift) - 1) >> shift);
@@ -938,9 +946,15 @@ template <bool kFew, bool kIndex>
 sbbf_status launch_scatter(const uint64_t* hashes, uint64_t n, uint32_t nb, const Piece& p,
                            const PartScratch& ps, unsigned* status, cudaStream_t s) {
   const size_t smem = scatter_smem_bytes(p.n_slices);
-  static const cudaError_t attr = cudaFuncSetAttribute(
-      scatter_kernel<kFew, kIndex>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-      static_cast<int>(kSmemBudget));
+  static const cudaError_t attr = [] {
+    cudaError_t e = cudaFuncSetAttribute(scatter_kernel<kFew, kIndex>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kSmemBudget));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(scatter_kernel<kFew, kIndex>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    return e;
+  }();
   if (attr != cudaSuccess) return record_cuda(attr);
   scatter_kernel<kFew, kIndex><<<p.bk.ctas, kPartThreads, smem, s>>>(
       hashes, n, nb, p.shift, p.bk, p.range, ps.sorted, kIndex ? ps.idx : nullptr,
