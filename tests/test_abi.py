@@ -71,6 +71,18 @@ def test_argument_checks_need_no_gpu(built):
     assert L.sbbf_set_partitioning(None, 0) == sbbf.SBBF_EINVAL
     assert L.sbbf_device_status(None, None) == sbbf.SBBF_EINVAL
     assert L.sbbf_record_device_status(None, 1, None) == sbbf.SBBF_EINVAL
+    lo, hi = ctypes.c_uint32(7), ctypes.c_uint32(7)
+    assert L.sbbf_shard_range(0, 2, 0, ctypes.byref(lo), ctypes.byref(hi)) == sbbf.SBBF_EINVAL
+    assert L.sbbf_shard_range(10, 1025, 0, ctypes.byref(lo), ctypes.byref(hi)) == sbbf.SBBF_EINVAL
+    assert lo.value == 7 and hi.value == 7  # untouched on error
+    assert L.sbbf_shard_range(10, 3, 2, ctypes.byref(lo), ctypes.byref(hi)) == sbbf.SBBF_OK
+    assert (lo.value, hi.value) == (8, 10)
+    assert L.sbbf_shard_routed_capacity(100, 4, 1) == 100 + 31 * 4
+    assert L.sbbf_shard_routed_capacity(100, 4, 0) == 100
+    assert L.sbbf_shard_route(None, 5, 0, 2, 0, None, None, None, None, 0, None) == sbbf.SBBF_EINVAL
+    assert L.sbbf_shard_insert(None, 10, 0, None, 0, None) == sbbf.SBBF_EINVAL
+    assert L.sbbf_shard_find(None, 10, 0, None, 5, None, None) == sbbf.SBBF_EINVAL
+    assert L.sbbf_shard_unpermute(None, None, 5, 5, None, None) == sbbf.SBBF_EINVAL
     assert L.sbbf_destroy(None) == sbbf.SBBF_OK
     assert L.sbbf_num_blocks(None) == 0
     assert L.sbbf_host_pipe_create(100, ctypes.byref(h)) == sbbf.SBBF_EINVAL  # not /64
