@@ -64,9 +64,10 @@ def parse_args(argv=None):
                    help="auto: with the default workload, also time the 11 bits/key, 32 GiB "
                         "and 1 MiB filters as rows of the line")
     p.add_argument("--row-steps", type=int, default=5)
-    p.add_argument("--parallelism", choices=["sharded", "replicas"], default="sharded",
-                   help="N > 1 ranks: one filter sharded by block range over the ranks "
-                        "(all-to-all of hashes and answers), or independent replicas")
+    p.add_argument("--parallelism", choices=["sharded", "replicas"], default=None,
+                   help="one filter sharded by block range over the ranks (all-to-all of "
+                        "hashes and answers; the default for N > 1, and runnable with one "
+                        "rank), or independent replicas")
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="approximate CPU work for the oracle baseline")
@@ -648,6 +649,15 @@ def run_sharded(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     dist = init_dist(world, "nccl")
+    if dist is None:  # one rank: a one-process group, so that the exchanges still run
+        import socket
+
+        import torch.distributed as tdist
+        with socket.socket() as sock:
+            sock.bind(("127.0.0.1", 0))
+            port = sock.getsockname()[1]
+        tdist.init_process_group("nccl", init_method="tcp://127.0.0.1:%d" % port, rank=0,
+                                 world_size=1)
     w = wl.WORKLOADS[args.workload]
     stream = torch.cuda.current_stream()
     num_blocks = w.num_blocks * world
@@ -1043,17 +1053,15 @@ def main(argv=None):
         line = run_multi(args)
     elif args.workload in wl.SERVING_WORKLOADS:
         line = run_serving(args)
-    elif dist_env()[1] > 1 and args.parallelism == "sharded":
+    elif args.parallelism == "sharded" or (dist_env()[1] > 1 and args.parallelism is None):
         line = run_sharded(args)
     else:
         line = run_ours(args)
     if line is not None:
         print(json.dumps(line), flush=True)
-    rank, world, _ = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        if dist.is_initialized():
-            dist.destroy_process_group()
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.destroy_process_group()
 
 
 if __name__ == "__main__":

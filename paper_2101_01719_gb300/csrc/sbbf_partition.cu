@@ -807,10 +807,14 @@ int find_occupancy() {
   return occ;
 }
 
-// The slice stream keeps its reads exact while a slice plus 1.5 windows of
-// filter bytes stay below ~48 MiB of L2 (measured on a 2 GiB filter: 62 MB
-// live, 5.85 GB of DRAM reads for 3.5 GB of keys and filter; 46 MB, 4.31 GB).
-constexpr double kLiveBytes = 48.0 * 1024 * 1024;
+// Live-set budget of the slice pass: a slice plus 1.5 windows of filter
+// bytes.  Measured: on a 2 GiB filter a 62 MB live set re-read the filter
+// (5.85 GB of DRAM reads for 3.5 GB of keys and filter; 46 MB: 4.31 GB),
+// which the plans below never approach at that density; on the 32 GiB
+// filter with ~1 key per block, 32 MiB slices leave the window room to
+// grow only under a larger budget, and 64 MiB (the grid no longer shrunk
+// to half) ran lookups at 46.5 against 41.8 G/s with 48, 80 no better.
+constexpr double kLiveBytes = 64.0 * 1024 * 1024;
 
 // Slice shift, grid and tile rounds of a partitioned lookup of n keys.  A
 // slice's blocks stay in L2 from its prefetch until its last key is
