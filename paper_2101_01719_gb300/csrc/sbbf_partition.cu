@@ -54,17 +54,21 @@ constexpr int kMaxSliceShift = 20;       // 2^20 blocks (32 MiB) per slice
 constexpr uint32_t kTargetSlices = 512;
 constexpr uint32_t kMaxSlices = 4096;    // num_blocks < 2^32 at the largest slice
 constexpr uint32_t kFewSlices = 32;      // ballot ranking up to this many slices
-// Scatter CTAs resident per SM (1: 1024 threads and 8192-key tiles; 2: two
-// CTAs of 512 threads and 4096-key tiles, whose barriers and ranking then
-// overlap each other's stores).
-#ifndef SBBF_SCATTER_CTAS_PER_SM
-#define SBBF_SCATTER_CTAS_PER_SM 1
-#endif
-constexpr int kScatterCtasPerSm = SBBF_SCATTER_CTAS_PER_SM;
-static_assert(kScatterCtasPerSm == 1 || kScatterCtasPerSm == 2, "one or two scatter CTAs per SM");
-constexpr int kPartThreads = 1024 / kScatterCtasPerSm;
-constexpr uint32_t kTile = 8192 / kScatterCtasPerSm;  // keys per scatter tile
-constexpr uint32_t kPer = kTile / kPartThreads;
+constexpr int kPartThreads = 1024;  // one scatter CTA per SM
+
+// Scatter tiles: 12288 keys where the slice tables leave room in shared
+// memory (longer runs per slice and a third less per-tile work), else 8192.
+// Lookups map answers back to key order by sub-range, a whole number of
+// tiles of at most 2^16 keys (16-bit offsets): five tiles of 12288 or eight
+// of 8192.
+template <uint32_t kT>
+struct TileShape {
+  static_assert(kT == 8192 || kT == 12288, "the two tile sizes");
+  static constexpr uint32_t kPer = kT / kPartThreads;  // keys per thread
+  static constexpr uint32_t kSub = kT == 12288 ? 5 * kT : 8 * kT;
+  static_assert(kSub <= 65536 && kSub % 32 == 0, "16-bit offsets; whole result words");
+};
+constexpr uint32_t kMaxSubKeys = 65536;
 
 __device__ __forceinline__ uint32_t slice_of(uint64_t h, uint32_t nb, int shift) {
   return block_of(h, nb) >> shift;
@@ -106,18 +110,13 @@ __host__ __device__ __forceinline__ uint64_t range_keys(uint64_t n, uint32_t cta
   return (r + 31) & ~31ull;
 }
 
-// Lookups map answers back to key order by sub-range: kSubKeys consecutive
-// positions of a CTA's range (a whole number of scatter tiles).  The scatter
+// Sub-ranges: sub_keys consecutive positions of a CTA's range.  The scatter
 // records its bucket cursors at each sub-range start, so the keys of
 // sub-range u of CTA c that fall in slice q sit at sorted positions
 // [marks[c][u][q], marks[c][u + 1][q]); a key's original position is then
 // stored as its 16-bit offset within its sub-range.
-constexpr uint32_t kSubKeys = 1u << 16;
-static_assert(kSubKeys % kTile == 0, "a sub-range is a whole number of tiles");
-static_assert(kTile % kPartThreads == 0 && kTile <= 8192, "whole keys per thread; 13-bit ranks");
-
-__host__ __device__ __forceinline__ uint32_t sub_ranges(uint64_t range) {
-  return static_cast<uint32_t>((range + kSubKeys - 1) / kSubKeys);
+__host__ __device__ __forceinline__ uint32_t sub_ranges(uint64_t range, uint32_t sub_keys) {
+  return static_cast<uint32_t>((range + sub_keys - 1) / sub_keys);
 }
 
 // Where the slice-ordered keys go: bucket (q, c) -- slice q, scatter CTA c --
@@ -257,8 +256,8 @@ __device__ __forceinline__ void cta_exclusive_scan(unsigned* vals, uint32_t n, u
 // Shared memory of the scatter: two input tiles, the per-slice bucket
 // cursors (i32) and counts / run starts (u32), and the sorted tile as the
 // input positions of its keys (u16).
-__host__ __device__ constexpr size_t scatter_smem_bytes(uint32_t n_slices) {
-  return 2ull * 8 * kTile + 8ull * n_slices + 2ull * kTile;
+__host__ __device__ constexpr size_t scatter_smem_bytes(uint32_t tile, uint32_t n_slices) {
+  return 2ull * 8 * tile + 8ull * n_slices + 2ull * tile;
 }
 
 // Keys into slice order.  CTA c streams its range in tiles: each key, read
@@ -279,20 +278,21 @@ __host__ __device__ constexpr size_t scatter_smem_bytes(uint32_t n_slices) {
 // as its 16-bit offset within its sub-range, and the bucket cursors at every
 // sub-range start (and after the last tile) to marks[c][u][q], `rows` rows
 // per CTA.  CTA 0 also resets the slice pass's tile counter.
-template <bool kFew, bool kIndex>
-__global__ void __launch_bounds__(kPartThreads, kScatterCtasPerSm)
+template <bool kFew, bool kIndex, uint32_t kT>
+__global__ void __launch_bounds__(kPartThreads, 1)
     scatter_kernel(const uint64_t* __restrict__ hashes, uint64_t n, uint32_t nb, int shift,
                    Buckets bk, uint64_t range, uint64_t* __restrict__ out,
                    uint16_t* __restrict__ out_idx, uint32_t* __restrict__ marks, uint32_t rows,
                    uint32_t* __restrict__ fill, uint32_t* __restrict__ spill,
                    unsigned long long* __restrict__ tiles, unsigned* __restrict__ status) {
+  constexpr uint32_t kPer = TileShape<kT>::kPer, kSub = TileShape<kT>::kSub;
   extern __shared__ __align__(16) unsigned long long smem[];
   const uint32_t S = bk.n_slices;
   uint64_t* s_buf0 = reinterpret_cast<uint64_t*>(smem);
-  uint64_t* s_buf1 = s_buf0 + kTile;
-  int* s_rel = reinterpret_cast<int*>(s_buf1 + kTile);              // [S] keys in bucket (q, c)
+  uint64_t* s_buf1 = s_buf0 + kT;
+  int* s_rel = reinterpret_cast<int*>(s_buf1 + kT);                 // [S] keys in bucket (q, c)
   unsigned* s_cnt = reinterpret_cast<unsigned*>(s_rel + S);         // [S]
-  uint16_t* s_perm = reinterpret_cast<uint16_t*>(s_cnt + S);        // [kTile]
+  uint16_t* s_perm = reinterpret_cast<uint16_t*>(s_cnt + S);        // [kT]
   __shared__ unsigned warp_sums[32];
   __shared__ __align__(8) unsigned long long s_bar[2];
   __shared__ unsigned s_spill;
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(kPartThreads, kScatterCtasPerSm)
   if (c == 0 && threadIdx.x == 0) *tiles = 0;
   const uint64_t a = static_cast<uint64_t>(c) * range;
   const uint64_t b = a < n ? (a + range < n ? a + range : n) : a;
-  const uint64_t n_tiles = (b - a + kTile - 1) / kTile;  // 0 past the keys
+  const uint64_t n_tiles = (b - a + kT - 1) / kT;  // 0 past the keys
   for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
     s_rel[i] = 0;
     s_cnt[i] = 0;
@@ -321,8 +321,8 @@ __global__ void __launch_bounds__(kPartThreads, kScatterCtasPerSm)
   // thread 0 starts the copy of tile t (its even-length head; an odd last
   // key is loaded after the wait)
   auto issue = [&](uint64_t t) {
-    const uint64_t t0 = a + t * kTile;
-    const uint64_t m = b - t0 < kTile ? b - t0 : kTile;
+    const uint64_t t0 = a + t * kT;
+    const uint64_t m = b - t0 < kT ? b - t0 : kT;
     const int buf = static_cast<int>(t & 1);
     track.issued(buf, (parity >> buf) & 1);
     bulk_load(buf ? s_buf1 : s_buf0, hashes + t0, static_cast<uint32_t>((m & ~1ull) * 8),
@@ -333,14 +333,14 @@ __global__ void __launch_bounds__(kPartThreads, kScatterCtasPerSm)
 
   uint32_t* my_marks = kIndex ? marks + static_cast<uint64_t>(c) * rows * S : nullptr;
   for (uint64_t t = 0; t < n_tiles; ++t) {
-    const uint64_t t0 = a + t * kTile;
-    const uint32_t m = static_cast<uint32_t>(b - t0 < kTile ? b - t0 : kTile);
+    const uint64_t t0 = a + t * kT;
+    const uint32_t m = static_cast<uint32_t>(b - t0 < kT ? b - t0 : kT);
     const int cur = static_cast<int>(t & 1);
     uint64_t* s_in = cur ? s_buf1 : s_buf0;
     // offset of the tile's first key within its sub-range
-    const uint32_t sub_off = static_cast<uint32_t>((t % (kSubKeys / kTile)) * kTile);
+    const uint32_t sub_off = static_cast<uint32_t>((t % (kSub / kT)) * kT);
     if (kIndex && sub_off == 0) {  // bucket cursors are true cursors between tiles
-      uint32_t* row = my_marks + (t / (kSubKeys / kTile)) * S;
+      uint32_t* row = my_marks + (t / (kSub / kT)) * S;
       for (uint32_t q = threadIdx.x; q < S; q += blockDim.x)
         row[q] = static_cast<uint32_t>(bk.base(q, c) + (s_rel[q] < cap ? s_rel[q] : cap));
     }
@@ -358,14 +358,14 @@ __global__ void __launch_bounds__(kPartThreads, kScatterCtasPerSm)
     const bool from_smem = bulk;
     // each key claims its rank among the tile's keys of its slice (the
     // counters end as the slice counts); slice and rank stay in registers
-    uint32_t qr[kPer];  // slice << 13 | rank
+    uint32_t qr[kPer];  // slice << 14 | rank (ranks < 12288; slices < 4096)
 #pragma unroll
     for (uint32_t i = 0; i < kPer; ++i) {
       const uint32_t j = i * kPartThreads + threadIdx.x;
       const bool v = j < m;
       const uint64_t key = !v ? 0 : from_smem ? s_in[j] : load_key1(hashes + t0 + j, pol);
       const uint32_t q = v ? slice_of(key, nb, shift) : 0u;
-      qr[i] = (q << 13) | rank_warp<kFew>(s_cnt, S, v, q);
+      qr[i] = (q << 14) | rank_warp<kFew>(s_cnt, S, v, q);
     }
     __syncthreads();
     cta_exclusive_scan(s_cnt, S, warp_sums);  // counts -> run starts (ends with a barrier)
@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(kPartThreads, kScatterCtasPerSm)
 #pragma unroll
     for (uint32_t i = 0; i < kPer; ++i) {
       const uint32_t j = i * kPartThreads + threadIdx.x;
-      if (j < m) s_perm[s_cnt[qr[i] >> 13] + (qr[i] & 0x1FFFu)] = static_cast<uint16_t>(j);
+      if (j < m) s_perm[s_cnt[qr[i] >> 14] + (qr[i] & 0x3FFFu)] = static_cast<uint16_t>(j);
     }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(kPartThreads, kScatterCtasPerSm)
     __syncthreads();
   }
   if (kIndex) {
-    uint32_t* row = my_marks + static_cast<uint64_t>(sub_ranges(b - a)) * S;
+    uint32_t* row = my_marks + static_cast<uint64_t>(sub_ranges(b - a, kSub)) * S;
     for (uint32_t q = threadIdx.x; q < S; q += blockDim.x)
       row[q] = static_cast<uint32_t>(bk.base(q, c) + (s_rel[q] < cap ? s_rel[q] : cap));
   }
@@ -641,16 +641,17 @@ __global__ void __launch_bounds__(256, 4)
 constexpr int kUnscatterThreads = 512;
 
 __host__ __device__ constexpr size_t unscatter_smem_bytes(uint32_t n_slices) {
-  return 4ull * (kSubKeys / 32) + 4ull * 3 * n_slices;
+  return 4ull * (kMaxSubKeys / 32) + 4ull * 3 * n_slices;
 }
 
 __global__ void __launch_bounds__(kUnscatterThreads)
     unscatter_kernel(const uint32_t* __restrict__ sorted_bits, const uint16_t* __restrict__ idx,
                      const uint32_t* __restrict__ marks, uint64_t n, uint64_t n_pos,
-                     uint64_t range, uint32_t rows, uint32_t n_slices, uint32_t* __restrict__ out) {
+                     uint64_t range, uint32_t sub_keys, uint32_t rows, uint32_t n_slices,
+                     uint32_t* __restrict__ out) {
   extern __shared__ __align__(16) uint32_t s_mem[];
   uint32_t* s_out = s_mem;                           // result words of the sub-range
-  uint32_t* s_lo = s_out + kSubKeys / 32;            // run q: sorted positions [s_lo, s_hi)
+  uint32_t* s_lo = s_out + kMaxSubKeys / 32;         // run q: sorted positions [s_lo, s_hi)
   uint32_t* s_hi = s_lo + n_slices;
   uint32_t* s_item = s_hi + n_slices;                // list offset of run q's first word
   __shared__ unsigned warp_sums[32];
@@ -659,9 +660,9 @@ __global__ void __launch_bounds__(kUnscatterThreads)
   const uint32_t c = blockIdx.x / subs, u = blockIdx.x % subs;
   const uint64_t a = static_cast<uint64_t>(c) * range;
   const uint64_t end = a + range < n ? a + range : n;
-  const uint64_t lo = a + static_cast<uint64_t>(u) * kSubKeys;
+  const uint64_t lo = a + static_cast<uint64_t>(u) * sub_keys;
   if (lo >= end) return;  // the whole CTA
-  const uint64_t hi = lo + kSubKeys < end ? lo + kSubKeys : end;
+  const uint64_t hi = lo + sub_keys < end ? lo + sub_keys : end;
   const uint32_t span = static_cast<uint32_t>(hi - lo);
   const uint32_t n_words = (span + 31) / 32;
   const uint32_t* m0 = marks + (static_cast<uint64_t>(c) * rows + u) * n_slices;
@@ -785,10 +786,15 @@ int sliced_rounds(unsigned grid, uint64_t n, uint64_t filter_bytes, int min_roun
 // Dynamic shared memory a CTA may use on this architecture (227 KB), less a
 // margin for the kernel's static shared memory.
 constexpr size_t kSmemBudget = 227 * 1024 - 512;
-static_assert(scatter_smem_bytes(kMaxSlices) <= kSmemBudget, "scatter tables fit");
+static_assert(scatter_smem_bytes(8192, kMaxSlices) <= kSmemBudget, "scatter tables fit");
 
-// CTAs of the scatter (kScatterCtasPerSm per SM).
-uint32_t partition_ctas() { return static_cast<uint32_t>(sm_count() * kScatterCtasPerSm); }
+// Scatter tile for n_slices slices: 12288 keys when that fits.
+uint32_t scatter_tile(uint32_t n_slices) {
+  return scatter_smem_bytes(12288, n_slices) <= kSmemBudget ? 12288u : 8192u;
+}
+
+// CTAs of the scatter (one per SM).
+uint32_t partition_ctas() { return static_cast<uint32_t>(sm_count()); }
 
 uint32_t slices_at(uint32_t num_blocks, int shift) {
   return static_cast<uint32_t>((static_cast<uint64_t>(num_blocks) + (1ull << shift) - 1) >> shift);
@@ -886,8 +892,10 @@ struct Piece {
   uint32_t n_slices;
   uint64_t range;
   Buckets bk;
-  uint32_t rows;   // lookups: mark rows per CTA (sub-ranges + 1)
-  FindPlan plan;   // lookups
+  uint32_t tile;      // scatter tile, 8192 or 12288 keys
+  uint32_t sub_keys;  // lookups: keys per sub-range (a whole number of tiles)
+  uint32_t rows;      // lookups: mark rows per CTA (sub-ranges + 1)
+  FindPlan plan;      // lookups
 };
 
 Piece piece_of(uint32_t num_blocks, uint64_t n, bool lookup) {
@@ -902,7 +910,9 @@ Piece piece_of(uint32_t num_blocks, uint64_t n, bool lookup) {
   p.n_slices = slices_at(num_blocks, p.shift);
   p.range = range_keys(n, ctas);
   p.bk = Buckets{ctas, p.n_slices, bucket_cap(p.range, num_blocks, p.shift)};
-  p.rows = sub_ranges(p.range) + 1;
+  p.tile = scatter_tile(p.n_slices);
+  p.sub_keys = p.tile == 12288 ? TileShape<12288>::kSub : TileShape<8192>::kSub;
+  p.rows = sub_ranges(p.range, p.sub_keys) + 1;
   return p;
 }
 
@@ -946,21 +956,21 @@ PartScratch carve(void* scratch, const Piece& p) {
   return r;
 }
 
-template <bool kFew, bool kIndex>
+template <bool kFew, bool kIndex, uint32_t kT>
 sbbf_status launch_scatter(const uint64_t* hashes, uint64_t n, uint32_t nb, const Piece& p,
                            const PartScratch& ps, unsigned* status, cudaStream_t s) {
-  const size_t smem = scatter_smem_bytes(p.n_slices);
+  const size_t smem = scatter_smem_bytes(kT, p.n_slices);
   static const cudaError_t attr = [] {
-    cudaError_t e = cudaFuncSetAttribute(scatter_kernel<kFew, kIndex>,
+    cudaError_t e = cudaFuncSetAttribute(scatter_kernel<kFew, kIndex, kT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(kSmemBudget));
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(scatter_kernel<kFew, kIndex>,
+      e = cudaFuncSetAttribute(scatter_kernel<kFew, kIndex, kT>,
                                cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     return e;
   }();
   if (attr != cudaSuccess) return record_cuda(attr);
-  scatter_kernel<kFew, kIndex><<<p.bk.ctas, kPartThreads, smem, s>>>(
+  scatter_kernel<kFew, kIndex, kT><<<p.bk.ctas, kPartThreads, smem, s>>>(
       hashes, n, nb, p.shift, p.bk, p.range, ps.sorted, kIndex ? ps.idx : nullptr,
       kIndex ? ps.marks : nullptr, p.rows, ps.fill, ps.spill, ps.tiles, status);
   return launch_status();
@@ -969,12 +979,14 @@ sbbf_status launch_scatter(const uint64_t* hashes, uint64_t n, uint32_t nb, cons
 // Step 1: the slice-ordered keys (and positions), bucket fills and spills.
 sbbf_status scatter(const uint64_t* hashes, uint64_t n, uint32_t num_blocks, const Piece& p,
                     const PartScratch& ps, bool with_index, unsigned* status, cudaStream_t s) {
-  const bool few = p.n_slices <= kFewSlices;
-  if (with_index)
-    return few ? launch_scatter<true, true>(hashes, n, num_blocks, p, ps, status, s)
-               : launch_scatter<false, true>(hashes, n, num_blocks, p, ps, status, s);
-  return few ? launch_scatter<true, false>(hashes, n, num_blocks, p, ps, status, s)
-             : launch_scatter<false, false>(hashes, n, num_blocks, p, ps, status, s);
+  const bool few = p.n_slices <= kFewSlices, big = p.tile == 12288;
+  const auto go = [&](auto launch) { return launch(hashes, n, num_blocks, p, ps, status, s); };
+  if (with_index) {
+    if (few) return big ? go(launch_scatter<true, true, 12288>) : go(launch_scatter<true, true, 8192>);
+    return big ? go(launch_scatter<false, true, 12288>) : go(launch_scatter<false, true, 8192>);
+  }
+  if (few) return big ? go(launch_scatter<true, false, 12288>) : go(launch_scatter<true, false, 8192>);
+  return big ? go(launch_scatter<false, false, 12288>) : go(launch_scatter<false, false, 8192>);
 }
 
 bool piece_fits(const Piece& p, bool lookup) {
@@ -1054,8 +1066,8 @@ sbbf_status launch_find_partitioned(const uint32_t* words, uint32_t num_blocks,
     if ((st = launch_status()) != SBBF_OK) return st;
     unscatter_kernel<<<p.bk.ctas * (p.rows - 1), kUnscatterThreads,
                        unscatter_smem_bytes(p.n_slices), s>>>(
-        ps.sorted_bits, ps.idx, ps.marks, m, p.bk.positions(), p.range, p.rows, p.n_slices,
-        d_out + off / 32);
+        ps.sorted_bits, ps.idx, ps.marks, m, p.bk.positions(), p.range, p.sub_keys, p.rows,
+        p.n_slices, d_out + off / 32);
     if ((st = launch_status()) != SBBF_OK) return st;
     fixup_find_kernel<<<p.bk.ctas, kFixupThreads, 0, s>>>(words, num_blocks, hashes + off, m,
                                                           p.range, ps.spill, d_out + off / 32);
