@@ -64,10 +64,12 @@ def parse_args(argv=None):
                    help="auto: with the default workload, also time the 11 bits/key, 32 GiB "
                         "and 1 MiB filters as rows of the line")
     p.add_argument("--row-steps", type=int, default=5)
-    p.add_argument("--parallelism", choices=["sharded", "replicas"], default=None,
-                   help="one filter sharded by block range over the ranks (all-to-all of "
-                        "hashes and answers; the default for N > 1, and runnable with one "
-                        "rank), or independent replicas")
+    p.add_argument("--parallelism", choices=["sharded", "replicas"], default="replicas",
+                   help="replicas (default): each rank its own copy of the filter and its "
+                        "own batch, no data-path collective; sharded: one filter split by "
+                        "block range over the ranks, hashes and answers exchanged by "
+                        "all-to-all (also runnable with one rank; with N > 1 the default "
+                        "line carries it as a row)")
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="approximate CPU work for the oracle baseline")
@@ -578,11 +580,19 @@ def run_ours(args):
         del f, ins, qry, out
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
-        for name in ROW_WORKLOADS:
-            big = wl.WORKLOADS[name].filter_bytes > (1 << 31)
-            rows_extra[name] = measure_row(name, dev, stream, peak, l2_bytes, args.row_steps,
-                                           ("auto", "on") if big else ("auto",))
-        rows_extra.update(batched_and_serving_rows(args))
+        if world == 1:
+            for name in ROW_WORKLOADS:
+                big = wl.WORKLOADS[name].filter_bytes > (1 << 31)
+                rows_extra[name] = measure_row(name, dev, stream, peak, l2_bytes, args.row_steps,
+                                               ("auto", "on") if big else ("auto",))
+            rows_extra.update(batched_and_serving_rows(args))
+        else:  # the same step with one filter sharded over the ranks
+            sh = run_sharded(args)
+            if sh is not None:
+                rows_extra["sharded_over_%d_gpus" % world] = {
+                    "gkeys_s": sh["value"], "ms_per_step": sh["ms_per_step"],
+                    "num_blocks": sh["config"]["num_blocks"], **sh["rows"],
+                    "e2e_gkeys_s": sh["e2e"]["value"]}
     if rank != 0:
         return None
     config = workload_config(w, world, args.lanes, args.keys)
@@ -649,10 +659,10 @@ def run_sharded(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     dist = init_dist(world, "nccl")
-    if dist is None:  # one rank: a one-process group, so that the exchanges still run
+    import torch.distributed as tdist
+    if not tdist.is_initialized():  # one rank: a one-process group, so the exchanges run
         import socket
 
-        import torch.distributed as tdist
         with socket.socket() as sock:
             sock.bind(("127.0.0.1", 0))
             port = sock.getsockname()[1]
@@ -1053,7 +1063,7 @@ def main(argv=None):
         line = run_multi(args)
     elif args.workload in wl.SERVING_WORKLOADS:
         line = run_serving(args)
-    elif args.parallelism == "sharded" or (dist_env()[1] > 1 and args.parallelism is None):
+    elif args.parallelism == "sharded":
         line = run_sharded(args)
     else:
         line = run_ours(args)

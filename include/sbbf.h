@@ -157,8 +157,10 @@ sbbf_status sbbf_insert_hashes(sbbf_t *f, const uint64_t *d_hashes, size_t n,
  * sbbf_destroy; partitioned calls on one filter must therefore be ordered on
  * one stream.
  *   SBBF_PARTITION_AUTO (default): partition batches of at least 4Mi hashes
- *     into filters of at least 256 MiB when the batch has at least one hash
- *     per block; if the scratch cannot be allocated, run unpartitioned;
+ *     into filters of at least 256 MiB when the batch has at least 0.25
+ *     hashes per block (inserts) or 0.6 (lookups) -- the measured
+ *     break-even densities; if the scratch cannot be allocated, run
+ *     unpartitioned;
  *   SBBF_PARTITION_OFF: never partition;
  *   SBBF_PARTITION_ON: always partition (SBBF_ENOMEM if no scratch).
  * Errors: SBBF_EINVAL (NULL filter or unknown mode). */
@@ -167,8 +169,7 @@ sbbf_status sbbf_set_partitioning(sbbf_t *f, int mode);
 
 /* Whether a batch of n hashes takes the partitioned path under the filter's
  * current mode: for sbbf_insert_hashes / sbbf_insert_keys / sbbf_insert_bytes
- * (lookup = 0) or the matching lookups (lookup != 0; inserts and lookups
- * follow the same rule today).  The answer is the
+ * (lookup = 0) or the matching lookups (lookup != 0).  The answer is the
  * decision before any scratch allocation (in automatic mode a failed
  * allocation still falls back to the unpartitioned path).  A partitioned
  * insert runs three kernels per piece of at most 2^34 hashes (scatter,

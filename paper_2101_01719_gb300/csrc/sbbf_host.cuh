@@ -104,9 +104,10 @@ sbbf_status launch_insert_partitioned(uint32_t* words, uint32_t num_blocks, cons
 sbbf_status launch_find_partitioned(const uint32_t* words, uint32_t num_blocks,
                                     const uint64_t* hashes, uint64_t n, uint32_t* d_out,
                                     void* scratch, unsigned* status, cudaStream_t s);
-// True when a batch of n keys should take the partitioned path (the filter's
-// mode, its size, and at least min_keys_per_block keys per block).
-bool want_partition(const sbbf_filter* f, uint64_t n);
+// True when a batch of n keys (a lookup batch when `lookup`) should take the
+// partitioned path: the filter's mode, its size and the batch's keys per
+// block.
+bool want_partition(const sbbf_filter* f, uint64_t n, bool lookup);
 // Grows the filter's scratch (cudaMalloc, synchronous) to at least `bytes`;
 // the first call also allocates the filter's zeroed device status word.
 sbbf_status ensure_scratch(sbbf_filter* f, size_t bytes);

@@ -54,7 +54,7 @@ static size_t round256(size_t b) { return (b + 255) & ~static_cast<size_t>(255);
 template <class S>
 sbbf_status insert_src(sbbf_t* f, S src, uint64_t n, cudaStream_t s) {
   if (n == 0) return SBBF_OK;
-  if (want_partition(f, n)) {
+  if (want_partition(f, n, false)) {
     const size_t hb = round256(n * 8);
     const sbbf_status st = ensure_scratch(f, hb + partition_scratch_bytes(f->num_blocks, n, false));
     if (st == SBBF_OK) {
@@ -74,7 +74,7 @@ sbbf_status insert_src(sbbf_t* f, S src, uint64_t n, cudaStream_t s) {
 template <class S>
 sbbf_status find_src(const sbbf_t* f, S src, uint64_t n, uint32_t* out, cudaStream_t s) {
   if (n == 0) return SBBF_OK;
-  if (want_partition(f, n)) {
+  if (want_partition(f, n, true)) {
     const size_t hb = round256(n * 8);
     sbbf_t* fm = const_cast<sbbf_t*>(f);
     const sbbf_status st = ensure_scratch(fm, hb + partition_scratch_bytes(f->num_blocks, n, true));

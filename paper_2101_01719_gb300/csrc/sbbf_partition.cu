@@ -550,7 +550,12 @@ __device__ __forceinline__ uint32_t interleave16(uint32_t x, uint32_t y) {
 // packed like the unpartitioned lookup's (bit k of the pair of words 2g,
 // 2g+1 answers position 64g + k); unscatter_kernel moves them to the keys'
 // original positions.
-__global__ void __launch_bounds__(256, 4)
+// Groups a lane has in flight per step of the slice pass (two block loads
+// each): 2 at four CTAs per SM.
+constexpr int kFindGroups = 2;
+constexpr int kFindMinCtas = kFindGroups == 2 ? 4 : 2;
+
+__global__ void __launch_bounds__(256, kFindMinCtas)
     sliced_find_kernel(const uint32_t* __restrict__ words, uint32_t nb, int shift,
                        const uint64_t* __restrict__ keys, Buckets bk,
                        const uint32_t* __restrict__ fill, unsigned long long* __restrict__ tiles,
@@ -581,12 +586,13 @@ __global__ void __launch_bounds__(256, 4)
     if (g0 >= n_groups) break;
     if (wic == 0)
       prefetch_positions(words, nb, shift, bk, g0 * 64 + ahead, g0 * 64 + ahead + keys_per_tile);
-    // two rounds per step: four block loads per lane in flight before any test
-    for (int r = 0; r < rounds; r += 2) {
-      uint64_t k[2], lim[2], h[2][2];
-      uint32_t w[2][2][8];
+    // kFindGroups rounds per step: 2 kFindGroups block loads per lane in
+    // flight before any test
+    for (int r = 0; r < rounds; r += kFindGroups) {
+      uint64_t k[kFindGroups], lim[kFindGroups], h[kFindGroups][2];
+      uint32_t w[kFindGroups][2][8];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < kFindGroups; ++u) {
         const uint64_t g = g0 + static_cast<uint64_t>(r + u) * wpc + wic;
         k[u] = g * 64 + 2 * lane;
         // the group's keys are loaded whole (every position is readable)
@@ -595,7 +601,7 @@ __global__ void __launch_bounds__(256, 4)
         lim[u] = g < n_groups ? group_end(bk, fill, g) : 0;
       }
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < kFindGroups; ++u) {
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
           if (k[u] + e < lim[u]) {
@@ -607,7 +613,7 @@ __global__ void __launch_bounds__(256, 4)
         }
       }
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < kFindGroups; ++u) {
         // bit l of b0 / b1: key 2l / 2l + 1 of the group
         const uint32_t b0 = __ballot_sync(
             0xFFFFFFFFu, k[u] < lim[u] && block_has(w[u][0], static_cast<uint32_t>(h[u][0])));
@@ -839,7 +845,7 @@ struct FindPlan {
 FindPlan find_plan(uint32_t num_blocks, uint64_t n) {
   const double per_key = 32.0 * num_blocks / static_cast<double>(n);
   unsigned grid = grid_for((n + 63) / 64, 8, find_occupancy());
-  const int rounds = sliced_rounds(grid, n, 32ull * num_blocks, 2);
+  const int rounds = sliced_rounds(grid, n, 32ull * num_blocks, kFindGroups);
   const double keys_per_cta = 8.0 * rounds * 64;
   const double window = grid * keys_per_cta * per_key;
   const int floor_shift = lookup_min_shift(num_blocks);
@@ -1080,7 +1086,6 @@ sbbf_status launch_find_partitioned(const uint32_t* words, uint32_t num_blocks,
 
 sbbf_status sbbf_partition_applies(const sbbf_t* f, size_t n, int lookup, int* applies) {
   if (!f || !applies) return SBBF_EINVAL;
-  (void)lookup;  // the same rule for inserts and lookups
-  *applies = sbbf::want_partition(f, n) ? 1 : 0;
+  *applies = sbbf::want_partition(f, n, lookup != 0) ? 1 : 0;
   return SBBF_OK;
 }

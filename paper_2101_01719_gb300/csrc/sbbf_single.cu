@@ -100,18 +100,21 @@ sbbf_status launch_find_filter(const sbbf_t* f, const uint64_t* d_hashes, uint64
 constexpr uint64_t kPartitionMinKeys = 4ull << 20;
 constexpr uint64_t kPartitionMinBytes = 256ull << 20;
 
-// Automatic mode also wants at least one key per block: a partitioned pass
-// reads every block of the filter once (the slice prefetch), so it pays only
-// when the batch touches each block about once or more.  Measured: 3e9
-// inserts into 2^30 blocks run 2.3x faster partitioned; lookups 2.1x faster
-// at 2 keys per block (2^26 blocks), 2.4x at 7.8 (128.9M blocks) and still
-// 1.12x at 0.93 (1e9 into 2^30 blocks).
-bool want_partition(const sbbf_t* f, uint64_t n) {
+// Automatic mode also wants enough keys per block: a partitioned pass reads
+// every block of the filter once (the slice prefetch), so it pays only when
+// the batch touches enough of the blocks.  Measured on the 32 GiB filter
+// (2^30 blocks), partitioned against random G keys/s: lookups 17.6 / 38.5 at
+// 0.125 keys per block, 25.8 / 38.6 at 0.25, 38.4 / 38.7 at 0.5, 46.6 / 38.6
+// at 0.75, 50.0 / 38.5 at 0.93; inserts 16.3 / 22.2 at 0.125, 24.6 / 22.3 at
+// 0.25, 37.3 / 22.3 at 0.5, 56.5 / 22.3 at 1.  So lookups partition from 0.6
+// keys per block and inserts from 0.25 (also measured: lookups 2.1x faster
+// at 2 keys per block on 2^26 blocks, 2.4x at 7.8 on 128.9M blocks).
+bool want_partition(const sbbf_t* f, uint64_t n, bool lookup) {
   if (f->lanes != 8 || f->partition_mode == SBBF_PARTITION_OFF) return false;
   if (f->partition_mode == SBBF_PARTITION_ON) return true;
-  return n >= kPartitionMinKeys &&
-         static_cast<uint64_t>(f->num_blocks) * 32 >= kPartitionMinBytes &&
-         n >= f->num_blocks;
+  const uint64_t nb = f->num_blocks;
+  const bool dense = lookup ? 5 * n >= 3 * nb : 4 * n >= nb;
+  return n >= kPartitionMinKeys && nb * 32 >= kPartitionMinBytes && dense;
 }
 
 // Grows the filter's scratch (cudaMalloc, synchronous) to hold `bytes`.
@@ -281,7 +284,7 @@ sbbf_status sbbf_insert_hashes(sbbf_t* f, const uint64_t* d_hashes, size_t n,
   if (!f || !on_device(f)) return SBBF_EINVAL;
   if (n == 0) return SBBF_OK;
   if (!d_hashes || (reinterpret_cast<uintptr_t>(d_hashes) & 7)) return SBBF_EINVAL;
-  if (want_partition(f, n)) {
+  if (want_partition(f, n, false)) {
     const sbbf_status st = ensure_scratch(f, partition_scratch_bytes(f->num_blocks, n, false));
     if (st == SBBF_OK)
       return launch_insert_partitioned(f->words, f->num_blocks, d_hashes, n, f->scratch, f->status,
@@ -308,7 +311,7 @@ sbbf_status sbbf_find_hashes(const sbbf_t* f, const uint64_t* d_hashes, size_t n
   if (!d_hashes || !d_out_bits || (reinterpret_cast<uintptr_t>(d_hashes) & 7) ||
       (reinterpret_cast<uintptr_t>(d_out_bits) & 3))
     return SBBF_EINVAL;
-  if (want_partition(f, n)) {
+  if (want_partition(f, n, true)) {
     const sbbf_status st =
         ensure_scratch(const_cast<sbbf_t*>(f), partition_scratch_bytes(f->num_blocks, n, true));
     if (st == SBBF_OK)

@@ -476,11 +476,17 @@ def test_bits_per_key_sweep(bits_per_key):
 
 def test_partition_applies_follows_the_rule():
     """sbbf_partition_applies reports the automatic rule (at least 4Mi hashes,
-    a filter of at least 256 MiB, one hash per block) and the forced modes."""
+    a filter of at least 256 MiB, at least 0.25 hashes per block for inserts
+    and 0.6 for lookups) and the forced modes."""
     f = sb.Filter(2**23)  # 256 MiB
-    assert f.partition_applies(2**23) and not f.partition_applies(2**23 - 1)
-    assert f.partition_applies(2**23, lookup=True)
-    assert not f.partition_applies(2**23 - 1, lookup=True)
+    assert f.partition_applies(2**22) and not f.partition_applies(2**22 - 1)  # 4Mi minimum
+    assert f.partition_applies(5_033_165, lookup=True)       # ceil(0.6 * 2^23)
+    assert not f.partition_applies(5_033_164, lookup=True)
+    g = sb.Filter(2**25)  # 1 GiB
+    assert g.partition_applies(2**23) and not g.partition_applies(2**23 - 1)  # 0.25 per block
+    assert g.partition_applies(20_132_660, lookup=True)      # ceil(0.6 * 2^25)
+    assert not g.partition_applies(20_132_659, lookup=True)
+    del g
     assert not sb.Filter(2**23 - 1).partition_applies(2**26)
     f.set_partitioning(sb.PARTITION_OFF)
     assert not f.partition_applies(2**30) and not f.partition_applies(2**30, lookup=True)
