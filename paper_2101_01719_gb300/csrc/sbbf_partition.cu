@@ -551,7 +551,7 @@ __device__ __forceinline__ uint32_t interleave16(uint32_t x, uint32_t y) {
 // 2g+1 answers position 64g + k); unscatter_kernel moves them to the keys'
 // original positions.
 // Groups a lane has in flight per step of the slice pass (two block loads
-// each): 2 at four CTAs per SM.
+// each): 2 at four CTAs per SM (4 at two CTAs per SM measured 18% slower).
 constexpr int kFindGroups = 2;
 constexpr int kFindMinCtas = kFindGroups == 2 ? 4 : 2;
 
