@@ -138,3 +138,39 @@ def test_route_groups_and_pads_by_owner():
                 assert real.all()
             start += c
         assert seen.all()
+
+
+def test_sharded_filter_over_nccl_with_one_rank():
+    """The sharded filter through its default communicator -- NCCL
+    all-to-alls over a one-process group -- and the library's kernels:
+    words and answers equal the oracle's (the exchanges move every hash and
+    answer word through NCCL even with one rank)."""
+    import socket
+
+    import torch.distributed as dist
+    from paper_2101_01719_gb300.sharded import TorchComm
+
+    if dist.is_initialized():
+        pytest.skip("a process group is already initialised in this process")
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    torch.cuda.set_device(dev())
+    dist.init_process_group("nccl", init_method="tcp://127.0.0.1:%d" % port, rank=0,
+                            world_size=1)
+    try:
+        B = 1_000_003
+        keys = inp.stream(99, 0, 700_001)
+        q = np.concatenate([inp.stream(99, 1, 300_000), keys[::5]])
+        sf = ShardedFilter(B, comm=TorchComm(device=dev()), ops=DeviceOps(dev()))
+        assert (sf.lo, sf.hi) == (0, B)
+        sf.insert(to_dev(keys[:350_000]))
+        sf.insert(to_dev(keys[350_000:]))
+        bits = bits_np(sf.find(to_dev(q)))
+        ref = oracle.new_filter(B)
+        oracle.insert(ref, B, keys)
+        assert np.array_equal(sf.local_words(), ref)
+        assert np.array_equal(bits, oracle.find(ref, B, q))
+        assert bits_np(sf.find(to_dev(q[:0]))).size == 0  # an empty batch
+    finally:
+        dist.destroy_process_group()
