@@ -64,10 +64,15 @@ __global__ void __launch_bounds__(kRouteThreads)
   const uint64_t a = static_cast<uint64_t>(blockIdx.x) * range;
   const uint64_t b = a + range < n ? a + range : n;
   const uint64_t pol = policy_evict_first();
-  for (uint64_t k = a + threadIdx.x; k < b; k += blockDim.x) {
-    const uint32_t g = owner_of(load_key1(hashes + k, pol), nb, per_shard);
-    const unsigned peers = __match_any_sync(__activemask(), g);
-    if (lane_id() == static_cast<unsigned>(__ffs(peers) - 1)) atomicAdd(&s_cnt[g], __popc(peers));
+  // warp-uniform trip count: every lane takes part in the match, lanes past
+  // the range with an owner no shard has
+  for (uint64_t k0 = a; k0 < b; k0 += blockDim.x) {
+    const uint64_t k = k0 + threadIdx.x;
+    const bool v = k < b;
+    const uint32_t g = v ? owner_of(load_key1(hashes + k, pol), nb, per_shard) : kMaxShards;
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, g);
+    if (v && lane_id() == static_cast<unsigned>(__ffs(peers) - 1))
+      atomicAdd(&s_cnt[g], __popc(peers));
   }
   __syncthreads();
   for (uint32_t g = threadIdx.x; g < G; g += blockDim.x)
@@ -128,14 +133,17 @@ __global__ void __launch_bounds__(kRouteThreads)
   const uint64_t pol = policy_evict_first();
   unsigned lt;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
-  for (uint64_t k = a + threadIdx.x; k < b; k += blockDim.x) {
-    const uint64_t h = load_key1(hashes + k, pol);
-    const uint32_t g = owner_of(h, nb, per_shard);
-    const unsigned peers = __match_any_sync(__activemask(), g);
+  for (uint64_t k0 = a; k0 < b; k0 += blockDim.x) {  // warp-uniform, as in the count
+    const uint64_t k = k0 + threadIdx.x;
+    const bool v = k < b;
+    const uint64_t h = v ? load_key1(hashes + k, pol) : 0;
+    const uint32_t g = v ? owner_of(h, nb, per_shard) : kMaxShards;
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, g);
     const int leader = __ffs(peers) - 1;
     unsigned long long first = 0;
-    if (lane_id() == static_cast<unsigned>(leader)) first = atomicAdd(&s_cur[g], __popc(peers));
-    first = __shfl_sync(peers, first, leader);
+    if (v && lane_id() == static_cast<unsigned>(leader)) first = atomicAdd(&s_cur[g], __popc(peers));
+    first = __shfl_sync(0xFFFFFFFFu, first, leader);
+    if (!v) continue;
     const unsigned long long slot = first + __popc(peers & lt);
     routed[slot] = h;
     perm[slot] = static_cast<uint32_t>(k);
