@@ -25,6 +25,11 @@ def test_reference_arm_prints_the_contract_line():
     assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
     assert line["config"]["workload"] == "sbbf_4194304blk_100M_ins_1G_lookup"
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+    # the same config dict as our arm emits for the default workload
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2101_01719_gb300 import workloads as wl
+    assert line["config"] == bench.workload_config(wl.C2, 1)
 
 
 def _stored_names(node):
