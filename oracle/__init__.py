@@ -83,6 +83,7 @@ def lib():
                 "oracle_xxh64_fixed": (None, [ctypes.c_void_p, sz, sz, u64, P64]),
                 "oracle_xxh64_var": (None, [ctypes.c_void_p, P64, sz, u64, P64]),
                 "oracle_swap_lane_pairs": (None, [P32, sz, P32]),
+                "oracle_range_digest": (None, [P32, u64, i32, u64, P64, P64, P64]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(L, name)
@@ -283,3 +284,17 @@ def swap_lane_pairs(words: np.ndarray) -> np.ndarray:
     out = np.empty_like(w)
     lib().oracle_swap_lane_pairs(_u32p(w), w.size, _u32p(out))
     return out
+
+
+def range_digest(words: np.ndarray, lanes: int, range_blocks: int):
+    """Per block range: (digest, set bits, blocks with both a zero and a
+    non-zero lane), each a uint64 array of ceil(num_blocks / range_blocks)."""
+    w = _c_u32(words)
+    assert lanes in (4, 8, 16) and w.size % lanes == 0 and range_blocks >= 1
+    nb = w.size // lanes
+    n_ranges = -(-nb // range_blocks)
+    d = np.zeros(n_ranges, np.uint64)
+    b = np.zeros(n_ranges, np.uint64)
+    p = np.zeros(n_ranges, np.uint64)
+    lib().oracle_range_digest(_u32p(w), nb, lanes, range_blocks, _u64p(d), _u64p(b), _u64p(p))
+    return d, b, p

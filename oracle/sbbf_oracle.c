@@ -370,6 +370,48 @@ void oracle_swap_lane_pairs(const uint32_t *in, size_t n_words, uint32_t *out) {
   for (size_t w = 0; w < n_words; ++w) out[w] = in[w ^ 1];
 }
 
+/* ---- verification digest (a checking aid; not part of the method) -------
+ * The filter's words, read as 64-bit units (unit u holds word 2u in its low
+ * half and word 2u+1 in its high half, the little-endian pairing), are split
+ * into ranges of range_blocks blocks: range r holds the blocks
+ * [r * range_blocks, min(num_blocks, (r + 1) * range_blocks)).  For each:
+ *   digest[r]  = sum over the range's units u of splitmix64 output u of the
+ *                stream seeded with the unit's value, mod 2^64;
+ *   bits[r]    = number of set bits in the range;
+ *   partial[r] = number of its blocks holding both an all-zero lane and a
+ *                non-zero lane.
+ * Every insert sets one bit in each lane of its block (the make_mask step),
+ * and a union ORs whole blocks, so partial is 0 for any filter built by them. */
+void oracle_range_digest(const uint32_t *words, uint64_t num_blocks, int lanes,
+                         uint64_t range_blocks, uint64_t *digest, uint64_t *bits,
+                         uint64_t *partial) {
+  const uint64_t n_ranges = (num_blocks + range_blocks - 1) / range_blocks;
+  for (uint64_t r = 0; r < n_ranges; ++r) {
+    digest[r] = 0;
+    bits[r] = 0;
+    partial[r] = 0;
+  }
+  for (uint64_t b = 0; b < num_blocks; ++b) {
+    const uint64_t r = b / range_blocks;
+    const uint32_t *blk = words + b * (uint64_t)lanes;
+    int zero_lanes = 0;
+    for (int i = 0; i < lanes; ++i) {
+      uint32_t w = blk[i];
+      if (w == 0) ++zero_lanes;
+      while (w) {
+        bits[r] += w & 1u;
+        w >>= 1;
+      }
+    }
+    if (zero_lanes > 0 && zero_lanes < lanes) ++partial[r];
+    for (int i = 0; i < lanes; i += 2) {
+      const uint64_t u = (b * (uint64_t)lanes + (uint64_t)i) / 2;
+      const uint64_t v = (uint64_t)blk[i] | ((uint64_t)blk[i + 1] << 32);
+      digest[r] += oracle_splitmix64_at(v, u);
+    }
+  }
+}
+
 int oracle_num_cores(void) {
   long c = sysconf(_SC_NPROCESSORS_ONLN);
   return c > 0 ? (int)c : 1;

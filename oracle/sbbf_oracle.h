@@ -128,6 +128,17 @@ void oracle_xxh64_var(const uint8_t *data, const uint64_t *offsets, size_t n,
  * little-endian lane order). */
 void oracle_swap_lane_pairs(const uint32_t *in, size_t n_words, uint32_t *out);
 
+/* Verification digest over block ranges (a checking aid, not part of the
+ * method).  Range r holds blocks [r*range_blocks, min(num_blocks,
+ * (r+1)*range_blocks)); digest[r] = sum mod 2^64 over the range's 64-bit units
+ * u (words 2u | 2u+1 << 32) of splitmix64 output u seeded with the unit's
+ * value; bits[r] = set bits; partial[r] = blocks with both a zero and a
+ * non-zero lane.  Arrays hold ceil(num_blocks / range_blocks) entries;
+ * lanes is 4, 8 or 16 and range_blocks >= 1. */
+void oracle_range_digest(const uint32_t *words, uint64_t num_blocks, int lanes,
+                         uint64_t range_blocks, uint64_t *digest, uint64_t *bits,
+                         uint64_t *partial);
+
 /* Number of online host cores. */
 int oracle_num_cores(void);
 
