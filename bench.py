@@ -346,6 +346,12 @@ def measure_row(name: str, dev, stream, peak: float, l2_bytes: int, steps: int,
             "roofline_frac": round(lb * w.n_lookup / (find_ms / 1e3) / 1e9 / peak, 4),
             "hit_frac": round(hits / w.n_lookup, 5)}
     f.set_partitioning(sb.PARTITION_AUTO)
+    if w.filter_bytes > l2_bytes:  # the verification digest streams every word once
+        rb = 1 << 20
+        digest_ms = timed(lambda: f.range_digest(rb))
+        gbs = w.filter_bytes / (digest_ms / 1e3) / 1e9
+        row["digest"] = {"range_blocks": rb, "ms": round(digest_ms, 4), "gbs": round(gbs, 1),
+                         "roofline_frac": round(gbs / peak, 4)}
     del f, ins, qry, out
     torch.cuda.synchronize()
     torch.cuda.empty_cache()

@@ -563,6 +563,35 @@ sbbf_status sbbf_count_bits(const uint32_t *d_bits, size_t n,
                             unsigned long long *d_count, sbbf_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Verification digest (a checking aid; not part of the method).
+ *
+ * Compares filters, or a filter and a host copy, range by range without
+ * moving the words.  d_words holds num_blocks blocks of `lanes` 32-bit words
+ * (the layout above; 16-byte aligned, device memory), read as 64-bit units:
+ * unit u is word 2u in its low half and word 2u+1 in its high half.  Range r
+ * holds the blocks [r * range_blocks, min(num_blocks, (r + 1) *
+ * range_blocks)), r < n_ranges = ceil(num_blocks / range_blocks), and gets
+ *   d_digest[r]  = sum mod 2^64 over its units u of splitmix64 output u of the
+ *                  stream seeded with the unit's value (the generator above),
+ *   d_bits[r]    = number of set bits,
+ *   d_partial[r] = number of its blocks with both an all-zero lane and a
+ *                  non-zero lane.
+ * An insert sets one bit in every lane of its block (the paper's make_mask)
+ * and a union ORs whole blocks, so d_partial is 0 in every range of a filter
+ * built by them.  The three arrays (device, n_ranges entries each, owned by
+ * the caller) are zeroed on the stream and then filled by one kernel reading
+ * every word once; the result does not depend on the launch's schedule.
+ * Errors: SBBF_EINVAL for lanes not 4, 8 or 16, range_blocks == 0, a NULL
+ * output, num_blocks > 2^40, or (num_blocks > 0) a NULL or unaligned
+ * d_words.  num_blocks == 0 enqueues nothing. */
+sbbf_status sbbf_range_digest(const uint32_t *d_words, uint64_t num_blocks,
+                              uint32_t lanes, uint64_t range_blocks,
+                              unsigned long long *d_digest,
+                              unsigned long long *d_bits,
+                              unsigned long long *d_partial,
+                              sbbf_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Many filters in one arena (batched form; not in the paper).
  *
  * Filter t of a set is the plain filter of num_blocks[t] blocks whose block 0

@@ -83,7 +83,7 @@ def lib():
                 "oracle_xxh64_fixed": (None, [ctypes.c_void_p, sz, sz, u64, P64]),
                 "oracle_xxh64_var": (None, [ctypes.c_void_p, P64, sz, u64, P64]),
                 "oracle_swap_lane_pairs": (None, [P32, sz, P32]),
-                "oracle_range_digest": (None, [P32, u64, i32, u64, P64, P64, P64]),
+                "oracle_range_digest": (None, [P32, u64, u64, i32, u64, P64, P64, P64]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(L, name)
@@ -286,9 +286,11 @@ def swap_lane_pairs(words: np.ndarray) -> np.ndarray:
     return out
 
 
-def range_digest(words: np.ndarray, lanes: int, range_blocks: int):
+def range_digest(words: np.ndarray, lanes: int, range_blocks: int, threads: int = 1):
     """Per block range: (digest, set bits, blocks with both a zero and a
-    non-zero lane), each a uint64 array of ceil(num_blocks / range_blocks)."""
+    non-zero lane), each a uint64 array of ceil(num_blocks / range_blocks).
+    With threads > 1 the ranges are split into that many runs of whole ranges,
+    each computed by the same scalar C code on its own thread."""
     w = _c_u32(words)
     assert lanes in (4, 8, 16) and w.size % lanes == 0 and range_blocks >= 1
     nb = w.size // lanes
@@ -296,5 +298,20 @@ def range_digest(words: np.ndarray, lanes: int, range_blocks: int):
     d = np.zeros(n_ranges, np.uint64)
     b = np.zeros(n_ranges, np.uint64)
     p = np.zeros(n_ranges, np.uint64)
-    lib().oracle_range_digest(_u32p(w), nb, lanes, range_blocks, _u64p(d), _u64p(b), _u64p(p))
+    runs = max(1, min(threads, n_ranges))
+    cuts = [n_ranges * k // runs for k in range(runs + 1)]
+
+    def run(k):
+        r0, r1 = cuts[k], cuts[k + 1]
+        b0, b1 = r0 * range_blocks, min(nb, r1 * range_blocks)
+        if r1 > r0:
+            lib().oracle_range_digest(_u32p(w[b0 * lanes:]), b0, b1 - b0, lanes, range_blocks,
+                                      _u64p(d[r0:]), _u64p(b[r0:]), _u64p(p[r0:]))
+
+    if runs == 1:
+        run(0)
+    else:
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(runs) as ex:
+            list(ex.map(run, range(runs)))
     return d, b, p

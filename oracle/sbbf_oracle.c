@@ -374,7 +374,11 @@ void oracle_swap_lane_pairs(const uint32_t *in, size_t n_words, uint32_t *out) {
  * The filter's words, read as 64-bit units (unit u holds word 2u in its low
  * half and word 2u+1 in its high half, the little-endian pairing), are split
  * into ranges of range_blocks blocks: range r holds the blocks
- * [r * range_blocks, min(num_blocks, (r + 1) * range_blocks)).  For each:
+ * [r * range_blocks, min(num_blocks, (r + 1) * range_blocks)).  `words` may
+ * start at block first_block of a larger filter (a multiple of range_blocks,
+ * so that callers can split the work at range boundaries): unit indexes are
+ * then those of the whole filter and r counts from the slice's first range.
+ * For each range:
  *   digest[r]  = sum over the range's units u of splitmix64 output u of the
  *                stream seeded with the unit's value, mod 2^64;
  *   bits[r]    = number of set bits in the range;
@@ -382,9 +386,9 @@ void oracle_swap_lane_pairs(const uint32_t *in, size_t n_words, uint32_t *out) {
  *                non-zero lane.
  * Every insert sets one bit in each lane of its block (the make_mask step),
  * and a union ORs whole blocks, so partial is 0 for any filter built by them. */
-void oracle_range_digest(const uint32_t *words, uint64_t num_blocks, int lanes,
-                         uint64_t range_blocks, uint64_t *digest, uint64_t *bits,
-                         uint64_t *partial) {
+void oracle_range_digest(const uint32_t *words, uint64_t first_block,
+                         uint64_t num_blocks, int lanes, uint64_t range_blocks,
+                         uint64_t *digest, uint64_t *bits, uint64_t *partial) {
   const uint64_t n_ranges = (num_blocks + range_blocks - 1) / range_blocks;
   for (uint64_t r = 0; r < n_ranges; ++r) {
     digest[r] = 0;
@@ -398,14 +402,14 @@ void oracle_range_digest(const uint32_t *words, uint64_t num_blocks, int lanes,
     for (int i = 0; i < lanes; ++i) {
       uint32_t w = blk[i];
       if (w == 0) ++zero_lanes;
-      while (w) {
-        bits[r] += w & 1u;
-        w >>= 1;
+      while (w) { /* one pass per set bit: clear the lowest */
+        bits[r] += 1;
+        w &= w - 1u;
       }
     }
     if (zero_lanes > 0 && zero_lanes < lanes) ++partial[r];
     for (int i = 0; i < lanes; i += 2) {
-      const uint64_t u = (b * (uint64_t)lanes + (uint64_t)i) / 2;
+      const uint64_t u = ((first_block + b) * (uint64_t)lanes + (uint64_t)i) / 2;
       const uint64_t v = (uint64_t)blk[i] | ((uint64_t)blk[i + 1] << 32);
       digest[r] += oracle_splitmix64_at(v, u);
     }

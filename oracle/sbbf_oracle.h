@@ -134,10 +134,12 @@ void oracle_swap_lane_pairs(const uint32_t *in, size_t n_words, uint32_t *out);
  * u (words 2u | 2u+1 << 32) of splitmix64 output u seeded with the unit's
  * value; bits[r] = set bits; partial[r] = blocks with both a zero and a
  * non-zero lane.  Arrays hold ceil(num_blocks / range_blocks) entries;
- * lanes is 4, 8 or 16 and range_blocks >= 1. */
-void oracle_range_digest(const uint32_t *words, uint64_t num_blocks, int lanes,
-                         uint64_t range_blocks, uint64_t *digest, uint64_t *bits,
-                         uint64_t *partial);
+ * lanes is 4, 8 or 16 and range_blocks >= 1.  words may be the slice of a
+ * filter starting at block first_block (a multiple of range_blocks); unit
+ * indexes are the whole filter's and ranges count from the slice's first. */
+void oracle_range_digest(const uint32_t *words, uint64_t first_block,
+                         uint64_t num_blocks, int lanes, uint64_t range_blocks,
+                         uint64_t *digest, uint64_t *bits, uint64_t *partial);
 
 /* Number of online host cores. */
 int oracle_num_cores(void);

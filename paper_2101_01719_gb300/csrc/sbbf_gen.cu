@@ -1,6 +1,7 @@
 // Synthetic inputs on the device (not part of the method): splitmix64 in
 // counter form (Steele, Lea, Flood, OOPSLA 2014), the member/fresh query
-// mix, and a popcount of packed lookup results.
+// mix, a popcount of packed lookup results, and the block-range verification
+// digest of a filter's words.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -102,6 +103,105 @@ __global__ void count_bits_kernel(const uint32_t* __restrict__ bits, uint64_t n,
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
 }
 
+// ---- verification digest ------------------------------------------------
+// Over block ranges of a filter's words, read as 64-bit units (unit u = word
+// 2u | word 2u+1 << 32): the sum mod 2^64 of splitmix64 output u seeded with
+// the unit's value, the set bits, and the blocks holding both an all-zero
+// and a non-zero lane (never produced by inserts, which set one bit in every
+// lane of their block).  The sums are order-free, so the per-CTA partial sums
+// meet in 64-bit atomics and the result is the same whatever the schedule.
+//
+// Each CTA streams one contiguous chunk of blocks; a thread reads 16-byte
+// vectors (two units) with fully coalesced loads, and the lanes of one block
+// (1, 2 or 4 vectors, adjacent threads of a warp) add their zero-lane counts
+// by shuffles.  Per (chunk, range) segment the CTA reduces once and adds to
+// the range's three counters.
+constexpr int kDigestThreads = 256;
+constexpr int kDigestUnroll = 4;
+
+template <int kLanes>
+__global__ void __launch_bounds__(kDigestThreads)
+    range_digest_kernel(const uint4* __restrict__ vecs, uint64_t num_blocks,
+                        uint64_t range_blocks, uint64_t chunk,
+                        unsigned long long* __restrict__ digest,
+                        unsigned long long* __restrict__ bits,
+                        unsigned long long* __restrict__ partial) {
+  constexpr int kVec = kLanes / 4;  // 16-byte vectors per block
+  __shared__ unsigned long long red[3][kDigestThreads / 32];
+  const uint64_t lo = static_cast<uint64_t>(blockIdx.x) * chunk;
+  const uint64_t hi = min(num_blocks, lo + chunk);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint64_t seg = lo; seg < hi;) {
+    const uint64_t r = seg / range_blocks;
+    const uint64_t end = min(hi, (r + 1) * range_blocks);
+    const uint64_t v_end = end * kVec;
+    unsigned long long d = 0, b = 0, p = 0;
+    for (uint64_t v0 = seg * kVec; v0 < v_end; v0 += kDigestThreads * kDigestUnroll) {
+      uint4 x[kDigestUnroll];
+#pragma unroll
+      for (int k = 0; k < kDigestUnroll; ++k) {
+        const uint64_t v = v0 + k * kDigestThreads + threadIdx.x;
+        x[k] = v < v_end ? __ldcs(vecs + v) : make_uint4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int k = 0; k < kDigestUnroll; ++k) {
+        const uint64_t v = v0 + k * kDigestThreads + threadIdx.x;
+        const bool live = v < v_end;  // the lanes of one block are live together
+        int zero = (x[k].x == 0) + (x[k].y == 0) + (x[k].z == 0) + (x[k].w == 0);
+#pragma unroll
+        for (int o = 1; o < kVec; o <<= 1) zero += __shfl_xor_sync(0xFFFFFFFFu, zero, o);
+        if (live) {
+          const uint64_t u = 2 * v;
+          d += splitmix64_at((static_cast<uint64_t>(x[k].y) << 32) | x[k].x, u);
+          d += splitmix64_at((static_cast<uint64_t>(x[k].w) << 32) | x[k].z, u + 1);
+          b += __popc(x[k].x) + __popc(x[k].y) + __popc(x[k].z) + __popc(x[k].w);
+          if ((lane & (kVec - 1)) == 0 && zero > 0 && zero < kLanes) ++p;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      d += __shfl_xor_sync(0xFFFFFFFFu, d, o);
+      b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
+      p += __shfl_xor_sync(0xFFFFFFFFu, p, o);
+    }
+    if (lane == 0) {
+      red[0][warp] = d;
+      red[1][warp] = b;
+      red[2][warp] = p;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long sd = 0, sb = 0, sp = 0;
+#pragma unroll
+      for (int w = 0; w < kDigestThreads / 32; ++w) {
+        sd += red[0][w];
+        sb += red[1][w];
+        sp += red[2][w];
+      }
+      atomicAdd(digest + r, sd);
+      if (sb) atomicAdd(bits + r, sb);
+      if (sp) atomicAdd(partial + r, sp);
+    }
+    __syncthreads();  // red is rewritten by the next segment
+    seg = end;
+  }
+}
+
+template <int kLanes>
+sbbf_status launch_range_digest(const uint32_t* words, uint64_t num_blocks, uint64_t range_blocks,
+                                unsigned long long* digest, unsigned long long* bits,
+                                unsigned long long* partial, cudaStream_t stream) {
+  static int occ = occupancy(range_digest_kernel<kLanes>, kDigestThreads);
+  const uint64_t per_cta = static_cast<uint64_t>(kDigestThreads) * kDigestUnroll / (kLanes / 4);
+  const unsigned grid = grid_for(num_blocks, per_cta, occ);
+  const uint64_t chunk = (num_blocks + grid - 1) / grid;
+  range_digest_kernel<kLanes><<<grid, kDigestThreads, 0, stream>>>(
+      reinterpret_cast<const uint4*>(words), num_blocks, range_blocks, chunk, digest, bits,
+      partial);
+  return launch_status();
+}
+
 }  // namespace sbbf
 
 using namespace sbbf;
@@ -164,6 +264,29 @@ sbbf_status sbbf_count_bits(const uint32_t* d_bits, size_t n, unsigned long long
   static int occ = occupancy(count_bits_kernel, 256);
   count_bits_kernel<<<grid_for((n + 31) / 32, 256, occ), 256, 0, stream>>>(d_bits, n, d_count);
   return launch_status();
+}
+
+sbbf_status sbbf_range_digest(const uint32_t* d_words, uint64_t num_blocks, uint32_t lanes,
+                              uint64_t range_blocks, unsigned long long* d_digest,
+                              unsigned long long* d_bits, unsigned long long* d_partial,
+                              sbbf_stream_t stream) {
+  if ((lanes != 4 && lanes != 8 && lanes != 16) || range_blocks == 0 || !d_digest || !d_bits ||
+      !d_partial || num_blocks > (1ull << 40))
+    return SBBF_EINVAL;
+  if (num_blocks == 0) return SBBF_OK;
+  if (!d_words || (reinterpret_cast<uintptr_t>(d_words) & 15)) return SBBF_EINVAL;
+  const size_t bytes = ((num_blocks - 1) / range_blocks + 1) * sizeof(unsigned long long);
+  SBBF_CUDA(cudaMemsetAsync(d_digest, 0, bytes, stream));
+  SBBF_CUDA(cudaMemsetAsync(d_bits, 0, bytes, stream));
+  SBBF_CUDA(cudaMemsetAsync(d_partial, 0, bytes, stream));
+  if (lanes == 4)
+    return launch_range_digest<4>(d_words, num_blocks, range_blocks, d_digest, d_bits, d_partial,
+                                  stream);
+  if (lanes == 8)
+    return launch_range_digest<8>(d_words, num_blocks, range_blocks, d_digest, d_bits, d_partial,
+                                  stream);
+  return launch_range_digest<16>(d_words, num_blocks, range_blocks, d_digest, d_bits, d_partial,
+                                 stream);
 }
 
 }  // extern "C"

@@ -75,6 +75,7 @@ SIGNATURES = {
     "sbbf_fill_splitmix64": (_int, [_P, _sz, _u64, _u64, _P]),
     "sbbf_fill_queries": (_int, [_P, _sz, _u64, _u64, _u64, _u64, _u64, _u64, _u64, _P]),
     "sbbf_count_bits": (_int, [_P, _sz, _P, _P]),
+    "sbbf_range_digest": (_int, [_P, _u64, _u32, _u64, _P, _P, _P, _P]),
     "sbbf_fill_segment_queries": (_int, [_P, _sz, _P, _P, _u32, _u64, _u64, _u64, _u64, _P]),
     "sbbf_fill_segment_ids": (_int, [_P, _sz, _P, _u32, _P]),
     "sbbf_multi_create": (_int, [_P, _u32, _c.POINTER(_P)]),
@@ -468,6 +469,11 @@ class Filter:
         import numpy as np
         return self.words.cpu().numpy().view(np.uint32)
 
+    def range_digest(self, range_blocks: int, stream=None):
+        """Verification digest of this filter's words per range of
+        ``range_blocks`` blocks (see :func:`range_digest`)."""
+        return range_digest(self.words, self.lanes, range_blocks, stream)
+
 
 class HostPipe:
     """Staging buffers and streams for host-memory insert/lookup calls."""
@@ -534,6 +540,24 @@ def count_bits(bits: torch.Tensor, n: int, stream=None) -> torch.Tensor:
     check(lib().sbbf_count_bits(bits.data_ptr(), n, cnt.data_ptr(), stream_handle(stream)),
           "sbbf_count_bits")
     return cnt
+
+
+def range_digest(words: torch.Tensor, lanes: int, range_blocks: int, stream=None):
+    """Per block range of a device word array (``lanes`` words per block):
+    (digest, set bits, blocks with both a zero and a non-zero lane), three
+    int64 tensors on the device holding the uint64 values bit for bit."""
+    if not words.is_cuda or not words.is_contiguous() or words.element_size() != 4:
+        raise ValueError("words must be a contiguous CUDA tensor of 32-bit words")
+    if lanes not in (4, 8, 16) or words.numel() % lanes or range_blocks < 1:
+        raise ValueError("lanes must be 4, 8 or 16 and divide the words; range_blocks >= 1")
+    nb = words.numel() // lanes
+    n_ranges = -(-nb // range_blocks)
+    out = torch.empty(3, n_ranges, dtype=torch.int64, device=words.device)
+    with torch.cuda.device(words.device):
+        check(lib().sbbf_range_digest(words.data_ptr(), nb, lanes, range_blocks, out[0].data_ptr(),
+                                      out[1].data_ptr(), out[2].data_ptr(), stream_handle(stream)),
+              "sbbf_range_digest")
+    return out[0], out[1], out[2]
 
 
 def fill_segment_queries(out: torch.Tensor, q_offsets: torch.Tensor, ins_offsets: torch.Tensor,

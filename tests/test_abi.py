@@ -83,6 +83,16 @@ def test_argument_checks_need_no_gpu(built):
     assert L.sbbf_shard_insert(None, 10, 0, None, 0, None) == sbbf.SBBF_EINVAL
     assert L.sbbf_shard_find(None, 10, 0, None, 5, None, None) == sbbf.SBBF_EINVAL
     assert L.sbbf_shard_unpermute(None, None, 5, 5, None, None) == sbbf.SBBF_EINVAL
+    out = ctypes.c_void_p(0x2000)
+    words = ctypes.c_void_p(0x3000)
+    assert L.sbbf_range_digest(words, 10, 5, 4, out, out, out, None) == sbbf.SBBF_EINVAL
+    assert L.sbbf_range_digest(words, 10, 8, 0, out, out, out, None) == sbbf.SBBF_EINVAL
+    assert L.sbbf_range_digest(words, 10, 8, 4, None, out, out, None) == sbbf.SBBF_EINVAL
+    assert L.sbbf_range_digest(words, 2**40 + 1, 8, 4, out, out, out, None) == sbbf.SBBF_EINVAL
+    assert L.sbbf_range_digest(ctypes.c_void_p(0x3004), 10, 8, 4, out, out, out, None) \
+        == sbbf.SBBF_EINVAL  # words not 16-byte aligned
+    assert L.sbbf_range_digest(None, 10, 8, 4, out, out, out, None) == sbbf.SBBF_EINVAL
+    assert L.sbbf_range_digest(None, 0, 8, 4, out, out, out, None) == sbbf.SBBF_OK  # nothing
     assert L.sbbf_destroy(None) == sbbf.SBBF_OK
     assert L.sbbf_num_blocks(None) == 0
     assert L.sbbf_host_pipe_create(100, ctypes.byref(h)) == sbbf.SBBF_EINVAL  # not /64

@@ -3,7 +3,8 @@
 10% members, in the batches the benchmark uses.  The oracle rebuilds each
 filter whole on the host (all cores, each thread owning a block range), and
 every word and every one of the 1e9 answers must match; the random and the
-slice-ordered lookup paths must give the same answers; the whole output is
+slice-ordered lookup paths must give the same answers; the device's
+block-range digest must equal the oracle's; the whole output is
 also checked statistically (members always hit; the false positive count of
 the non-members within a Poisson interval of the formula)."""
 import numpy as np
@@ -38,6 +39,14 @@ def test_three_billion_inserts_full_parity(w):
     ref = oracle_filter_of_stream(w)
     compare_words(f.words, ref)
     compare_all_lookups(w, ref, q, bits)
+    # the block-range digest in one device pass, against the oracle's over
+    # its rebuilt filter; no block has a zero lane beside a non-zero one
+    R = 1 << 20
+    got = [t.cpu().numpy().view(np.uint64) for t in f.range_digest(R)]
+    exp = oracle.range_digest(ref, 8, R, threads=oracle.num_cores())
+    for g, e in zip(got, exp):
+        assert np.array_equal(g, e)
+    assert not exp[2].any()
     del ref
 
     # statistics over all 1e9 answers

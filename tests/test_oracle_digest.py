@@ -27,8 +27,11 @@ MUTANTS = {
     "high_half_dropped": ("(uint64_t)blk[i] | ((uint64_t)blk[i + 1] << 32)", "(uint64_t)blk[i]"),
     "index_off_by_one": ("digest[r] += oracle_splitmix64_at(v, u);",
                          "digest[r] += oracle_splitmix64_at(v, u + 1);"),
-    "index_per_block": ("const uint64_t u = (b * (uint64_t)lanes + (uint64_t)i) / 2;",
+    "index_per_block": ("const uint64_t u = ((first_block + b) * (uint64_t)lanes + (uint64_t)i) / 2;",
                         "const uint64_t u = (uint64_t)i / 2;"),
+    "slice_index_local": ("const uint64_t u = ((first_block + b) * (uint64_t)lanes + (uint64_t)i) / 2;",
+                          "const uint64_t u = (b * (uint64_t)lanes + (uint64_t)i) / 2;"),
+    "popcount_once_per_word": ("bits[r] += 1;\n        w &= w - 1u;", "bits[r] += 1;\n        w = 0;"),
     "xor_fold": ("digest[r] += oracle_splitmix64_at(v, u);",
                  "digest[r] ^= oracle_splitmix64_at(v, u);"),
     "bits_skip_last_lane": ("for (int i = 0; i < lanes; ++i) {\n      uint32_t w = blk[i];",
@@ -46,17 +49,23 @@ class _Lib:
     def __init__(self, so):
         self.L = ctypes.CDLL(so)
         P64, P32 = ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32)
-        self.L.oracle_range_digest.argtypes = [P32, ctypes.c_uint64, ctypes.c_int,
-                                               ctypes.c_uint64, P64, P64, P64]
+        self.L.oracle_range_digest.argtypes = [P32, ctypes.c_uint64, ctypes.c_uint64,
+                                               ctypes.c_int, ctypes.c_uint64, P64, P64, P64]
 
-    def __call__(self, words, lanes, range_blocks):
+    def __call__(self, words, lanes, range_blocks, threads=1):
+        """As oracle.range_digest; `threads` runs of whole ranges, one after
+        another, each from its own first block."""
         w = np.ascontiguousarray(words, np.uint32)
         nb = w.size // lanes
         n = -(-nb // range_blocks)
         out = [np.zeros(n, np.uint64) for _ in range(3)]
-        p64 = [o.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)) for o in out]
-        self.L.oracle_range_digest(w.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), nb,
-                                   lanes, range_blocks, *p64)
+        runs = max(1, min(threads, n))
+        for k in range(runs):
+            r0, r1 = n * k // runs, n * (k + 1) // runs
+            b0, b1 = r0 * range_blocks, min(nb, r1 * range_blocks)
+            p64 = [o[r0:].ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)) for o in out]
+            self.L.oracle_range_digest(w[b0 * lanes:].ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                       b0, b1 - b0, lanes, range_blocks, *p64)
         return out
 
 
@@ -197,6 +206,15 @@ def _pins(D):
     sw[[k, k + 1]] = sw[[k + 1, k]]
     ok &= D(sw, 8, 4)[0][0] != d0[0]
     yield "unit order and halves", ok
+    # 8. split into runs of whole ranges (each run from its own first block),
+    #    the figures are those of one pass over everything.
+    ok = True
+    for lanes in (4, 16):
+        words = _built_filter(lanes, 301, 900, 12)
+        one = D(words, lanes, 10)
+        for runs in (2, 7, 31):
+            ok &= all(np.array_equal(a, c) for a, c in zip(D(words, lanes, 10, threads=runs), one))
+    yield "runs of ranges", ok
 
 
 def test_oracle_digest_passes_every_pin():
