@@ -157,10 +157,10 @@ sbbf_status sbbf_insert_hashes(sbbf_t *f, const uint64_t *d_hashes, size_t n,
  * sbbf_destroy; partitioned calls on one filter must therefore be ordered on
  * one stream.
  *   SBBF_PARTITION_AUTO (default): partition batches of at least 4Mi hashes
- *     into filters of at least 256 MiB when the batch has at least 0.25
- *     hashes per block (inserts) or 0.6 (lookups) -- the measured
- *     break-even densities; if the scratch cannot be allocated, run
- *     unpartitioned;
+ *     when the filter holds at least 96 MiB (inserts) or more than 128 MiB
+ *     (lookups) and the batch has at least 0.25 hashes per block (inserts)
+ *     or 0.6 (lookups) -- the measured break-evens; if the scratch cannot be
+ *     allocated, run unpartitioned;
  *   SBBF_PARTITION_OFF: never partition;
  *   SBBF_PARTITION_ON: always partition (SBBF_ENOMEM if no scratch).
  * Errors: SBBF_EINVAL (NULL filter or unknown mode). */

@@ -112,12 +112,25 @@ __global__ void count_bits_kernel(const uint32_t* __restrict__ bits, uint64_t n,
 // meet in 64-bit atomics and the result is the same whatever the schedule.
 //
 // Each CTA streams one contiguous chunk of blocks; a thread reads 16-byte
-// vectors (two units) with fully coalesced loads, and the lanes of one block
-// (1, 2 or 4 vectors, adjacent threads of a warp) add their zero-lane counts
-// by shuffles.  Per (chunk, range) segment the CTA reduces once and adds to
+// vectors (two units) with fully coalesced loads, four per thread, and issues
+// the next four before mixing the current ones; the lanes of one block (1, 2
+// or 4 vectors, adjacent threads of a warp) add their zero-lane counts by
+// shuffles.  Per (chunk, range) segment the CTA reduces once and adds to
 // the range's three counters.
 constexpr int kDigestThreads = 256;
 constexpr int kDigestUnroll = 4;
+
+// Vectors v0 + k * kDigestThreads + threadIdx.x, k < kUnroll, below v_end
+// (zero past it), read once with streaming loads.
+template <int kUnroll>
+__device__ __forceinline__ void load_digest_batch(const uint4* __restrict__ vecs, uint64_t v0,
+                                                  uint64_t v_end, uint4 (&x)[kUnroll]) {
+#pragma unroll
+  for (int k = 0; k < kUnroll; ++k) {
+    const uint64_t v = v0 + k * kDigestThreads + threadIdx.x;
+    x[k] = v < v_end ? __ldcs(vecs + v) : make_uint4(0, 0, 0, 0);
+  }
+}
 
 template <int kLanes>
 __global__ void __launch_bounds__(kDigestThreads)
@@ -135,14 +148,14 @@ __global__ void __launch_bounds__(kDigestThreads)
     const uint64_t r = seg / range_blocks;
     const uint64_t end = min(hi, (r + 1) * range_blocks);
     const uint64_t v_end = end * kVec;
+    constexpr uint64_t kBatch = static_cast<uint64_t>(kDigestThreads) * kDigestUnroll;
     unsigned long long d = 0, b = 0, p = 0;
-    for (uint64_t v0 = seg * kVec; v0 < v_end; v0 += kDigestThreads * kDigestUnroll) {
-      uint4 x[kDigestUnroll];
-#pragma unroll
-      for (int k = 0; k < kDigestUnroll; ++k) {
-        const uint64_t v = v0 + k * kDigestThreads + threadIdx.x;
-        x[k] = v < v_end ? __ldcs(vecs + v) : make_uint4(0, 0, 0, 0);
-      }
+    uint4 x[kDigestUnroll];
+    load_digest_batch<kDigestUnroll>(vecs, seg * kVec, v_end, x);
+    for (uint64_t v0 = seg * kVec; v0 < v_end; v0 += kBatch) {
+      uint4 y[kDigestUnroll];  // the next batch is in flight while this one is mixed
+      load_digest_batch<kDigestUnroll>(vecs, v0 + kBatch, v_end, y);
+      unsigned bb = 0, pp = 0;
 #pragma unroll
       for (int k = 0; k < kDigestUnroll; ++k) {
         const uint64_t v = v0 + k * kDigestThreads + threadIdx.x;
@@ -154,10 +167,14 @@ __global__ void __launch_bounds__(kDigestThreads)
           const uint64_t u = 2 * v;
           d += splitmix64_at((static_cast<uint64_t>(x[k].y) << 32) | x[k].x, u);
           d += splitmix64_at((static_cast<uint64_t>(x[k].w) << 32) | x[k].z, u + 1);
-          b += __popc(x[k].x) + __popc(x[k].y) + __popc(x[k].z) + __popc(x[k].w);
-          if ((lane & (kVec - 1)) == 0 && zero > 0 && zero < kLanes) ++p;
+          bb += __popc(x[k].x) + __popc(x[k].y) + __popc(x[k].z) + __popc(x[k].w);
+          if ((lane & (kVec - 1)) == 0 && zero > 0 && zero < kLanes) ++pp;
         }
       }
+      b += bb;
+      p += pp;
+#pragma unroll
+      for (int k = 0; k < kDigestUnroll; ++k) x[k] = y[k];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

@@ -91,14 +91,18 @@ sbbf_status launch_find_filter(const sbbf_t* f, const uint64_t* d_hashes, uint64
   return launch_find(f->words, f->num_blocks, d_hashes, n, d_out, s);
 }
 
-// Batches at least this large go through the partitioned insert when the
-// filter is at least kPartitionMinBytes (automatic mode).  Measured on GB300:
-// a 32 GiB filter takes 3e9 inserts at 49 G/s partitioned against 21.5 G/s
-// unpartitioned, a 4.1 GB filter 71 against 27.5 G/s, while a 128 MiB filter
-// (about the size of L2) keeps enough L2 hits unpartitioned (65 G/s) that the
-// two extra passes over the keys do not pay.
+// Batches at least this large go through the partitioned path when the
+// filter is at least kPartitionMin{Insert,Lookup}Bytes (automatic mode).
+// Measured on GB300 (100M inserts in 16M batches, 1e9 lookups, partitioned
+// against random G keys/s): inserts 78 / 119 at 64 MiB (the filter stays in
+// L2), 77 / 73 at 96 MiB, 77 / 55-65 at 128 MiB, 70 / 40 at 256 MiB;
+// lookups 113 / 148 at 96 MiB, 111-113 / 108-114 at 128 MiB (the two within
+// the spread between boxes: the random path, one kernel and no scratch, is
+// kept there), 110 / 97 at 144 MiB, 118 / 66 at 256 MiB; at 32 GiB 49 / 21.5
+// G inserts/s.
 constexpr uint64_t kPartitionMinKeys = 4ull << 20;
-constexpr uint64_t kPartitionMinBytes = 256ull << 20;
+constexpr uint64_t kPartitionMinInsertBytes = 96ull << 20;
+constexpr uint64_t kPartitionMinLookupBytes = (128ull << 20) + 1;
 
 // Automatic mode also wants enough keys per block: a partitioned pass reads
 // every block of the filter once (the slice prefetch), so it pays only when
@@ -114,7 +118,8 @@ bool want_partition(const sbbf_t* f, uint64_t n, bool lookup) {
   if (f->partition_mode == SBBF_PARTITION_ON) return true;
   const uint64_t nb = f->num_blocks;
   const bool dense = lookup ? 5 * n >= 3 * nb : 4 * n >= nb;
-  return n >= kPartitionMinKeys && nb * 32 >= kPartitionMinBytes && dense;
+  const uint64_t min_bytes = lookup ? kPartitionMinLookupBytes : kPartitionMinInsertBytes;
+  return n >= kPartitionMinKeys && nb * 32 >= min_bytes && dense;
 }
 
 // Grows the filter's scratch (cudaMalloc, synchronous) to hold `bytes`.

@@ -475,9 +475,10 @@ def test_bits_per_key_sweep(bits_per_key):
 
 
 def test_partition_applies_follows_the_rule():
-    """sbbf_partition_applies reports the automatic rule (at least 4Mi hashes,
-    a filter of at least 256 MiB, at least 0.25 hashes per block for inserts
-    and 0.6 for lookups) and the forced modes."""
+    """sbbf_partition_applies reports the automatic rule (at least 4Mi hashes;
+    a filter of at least 96 MiB for inserts and more than 128 MiB for
+    lookups; at least 0.25 hashes per block for inserts and 0.6 for lookups)
+    and the forced modes."""
     f = sb.Filter(2**23)  # 256 MiB
     assert f.partition_applies(2**22) and not f.partition_applies(2**22 - 1)  # 4Mi minimum
     assert f.partition_applies(5_033_165, lookup=True)       # ceil(0.6 * 2^23)
@@ -487,7 +488,14 @@ def test_partition_applies_follows_the_rule():
     assert g.partition_applies(20_132_660, lookup=True)      # ceil(0.6 * 2^25)
     assert not g.partition_applies(20_132_659, lookup=True)
     del g
-    assert not sb.Filter(2**23 - 1).partition_applies(2**26)
+    big = 2**27
+    ins96 = sb.Filter(3 * 2**20)  # 96 MiB: inserts partition, lookups do not
+    assert ins96.partition_applies(big) and not ins96.partition_applies(big, lookup=True)
+    assert not sb.Filter(3 * 2**20 - 1).partition_applies(big)
+    at128 = sb.Filter(2**22)  # 128 MiB: lookups still random
+    assert at128.partition_applies(big) and not at128.partition_applies(big, lookup=True)
+    assert sb.Filter(2**22 + 1).partition_applies(big, lookup=True)
+    del ins96, at128
     f.set_partitioning(sb.PARTITION_OFF)
     assert not f.partition_applies(2**30) and not f.partition_applies(2**30, lookup=True)
     f.set_partitioning(sb.PARTITION_ON)
