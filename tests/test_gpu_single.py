@@ -357,14 +357,17 @@ def test_config_c2_full_size():
     torch.cuda.empty_cache()
 
 
-PARTITION_CASES = [(2**20, 0), (2**20, 1), (2**20 + 5, 16385), (3 * 2**20 - 1, 1_000_003),
+PARTITION_CASES = [(2**17, 300_001), (3 * 2**17 + 9, 700_001), (2**19, 1_000_003),
+                   (2**20, 0), (2**20, 1), (2**20 + 5, 16385), (3 * 2**20 - 1, 1_000_003),
                    (5 * 2**20 + 77, 2_500_000), (4_194_304, 4_200_000)]
 
 
 @pytest.mark.parametrize("B,n", PARTITION_CASES)
 def test_partitioned_insert_equals_oracle(B, n):
     """Slice-partitioned inserts (forced on) give the oracle's filter,
-    across slice counts 8..41 (4 MiB slices for inserts), ragged tiles and tails."""
+    across slice counts 1..41 (4 MiB slices for inserts; up to 4 slices the
+    scatter ranks by warp match, past 4 by per-key atomics), ragged tiles and
+    tails."""
     keys = inp.stream(130 + B % 11, 0, n)
     f = sb.Filter(B).set_partitioning(sb.PARTITION_ON)
     f.insert(to_dev(keys))
@@ -390,7 +393,7 @@ def test_partitioned_insert_unaligned_and_repeated():
 
 
 def test_partitioned_many_slices():
-    """41 slices (more than the ballot-counted few): inserts and lookups,
+    """41 slices (per-key atomic ranking): inserts and lookups,
     with an odd batch length and an 8-byte-aligned (not 16) hash array, which
     the scatter reads without bulk copies."""
     B, n = 41 * 2**20 + 123, 2_000_001
@@ -415,7 +418,8 @@ def test_partitioned_many_slices():
                                  (5 * 2**20 + 77, 2_500_033)])
 def test_partitioned_find_equals_oracle(B, n):
     """Slice-partitioned lookups (forced on) answer exactly as the oracle,
-    every bit at its original position, tail bits zero."""
+    every bit at its original position, tail bits zero; 1 and 3 slices (32
+    MiB slices, warp-match ranking) and 6 (per-key atomics)."""
     keys = inp.stream(140 + B % 13, 0, max(1, n // 3))
     q = np.concatenate([inp.stream(140 + B % 13, 1, n - n // 4), keys[: n // 4]])[:n]
     f = sb.Filter(B)
