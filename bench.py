@@ -352,6 +352,17 @@ def measure_row(name: str, dev, stream, peak: float, l2_bytes: int, steps: int,
         gbs = w.filter_bytes / (digest_ms / 1e3) / 1e9
         row["digest"] = {"range_blocks": rb, "ms": round(digest_ms, 4), "gbs": round(gbs, 1),
                          "roofline_frac": round(gbs / peak, 4)}
+    if l2_bytes < w.filter_bytes <= 8 << 30:
+        # union (two reads and one write of every word: 96 B per block) and
+        # clear (one write, 32 B per block), streaming
+        g = sb.Filter(w.num_blocks, device=dev)
+        for name, fn, nbytes in (("union", lambda: f.union_(g), 3 * w.filter_bytes),
+                                 ("clear", g.clear, w.filter_bytes)):
+            ms = timed(fn)
+            gbs = nbytes / (ms / 1e3) / 1e9
+            row[name] = {"ms": round(ms, 4), "bytes": nbytes, "gbs": round(gbs, 1),
+                         "roofline_frac": round(gbs / peak, 4)}
+        del g
     del f, ins, qry, out
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
