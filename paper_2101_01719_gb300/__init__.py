@@ -13,6 +13,7 @@ from .sbbf import (  # noqa: F401
     PARTITION_AUTO,
     PARTITION_OFF,
     PARTITION_ON,
+    PARTITION_REGIONS,
     PIPE_AUTO,
     PIPE_COPY,
     PIPE_DIRECT,

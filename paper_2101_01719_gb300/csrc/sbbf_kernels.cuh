@@ -384,4 +384,96 @@ __global__ void __launch_bounds__(kMaxThreads, find_min_blocks<R, S>(kLanes8, U)
   res.finish();
 }
 
+// ---- region-pass lookup ----------------------------------------------------
+
+// One pass of a region-pass lookup into a one-filter of num_blocks blocks:
+// the keys whose block (the appendix block_index) lies in [lo, hi) are looked
+// up; the others answer 0 in the first pass (kMerge false: every answer word
+// is written) and keep their bit in the later passes (kMerge true: the new
+// bits are ORed in with fire-and-forget reductions, one per answer word that
+// gains a bit).  With the filter split into regions small enough to stay in
+// L2, each pass finds its blocks in L2 at the price of reading all the keys.
+// Each warp takes units of U 64-key groups by grid stride and loads the next
+// unit's hashes before it waits on this unit's blocks, so the DRAM latency of
+// the key stream and the L2 latency of the block loads overlap.
+template <int U, bool kMerge>
+__global__ void __launch_bounds__(kMaxThreads)
+    region_find_kernel(const uint32_t* __restrict__ words, uint32_t num_blocks, uint32_t lo,
+                       uint32_t hi, HashInput src, uint64_t n, uint32_t* __restrict__ out) {
+  const unsigned lane = lane_id();
+  const uint64_t n_groups = (n + 63) >> 6;
+  const uint64_t n_units = (n_groups + U - 1) / U;
+  const uint64_t n_out = (n + 31) >> 5;
+  const uint64_t n_warps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+  const uint64_t pk = policy_evict_first();
+  const uint64_t pf = policy_evict_last();
+  const bool out16 = (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+  const bool out8 = (reinterpret_cast<uintptr_t>(out) & 7) == 0;
+  const uint32_t span = hi - lo;
+
+  uint64_t unit = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  uint64_t h[U][2];
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+    src.pair((unit * U + u) * 64 + 2 * lane, unit < n_units ? n : 0, pk, h[u][0], h[u][1]);
+  for (; unit < n_units; unit += n_warps) {
+    const uint64_t g0 = unit * U;
+    uint32_t b[U][2];
+    bool act[U][2];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const uint64_t k = (g0 + u) * 64 + 2 * lane + s;
+        b[u][s] = block_of(h[u][s], num_blocks);
+        act[u][s] = k < n && b[u][s] - lo < span;
+      }
+    uint32_t w[U][2][8];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        if (act[u][s]) {
+          load_block_na(words + 8ull * b[u][s], pf, w[u][s]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) w[u][s][i] = 0;
+        }
+      }
+    // the next unit's hashes, in flight while this unit's blocks arrive
+    const uint64_t next = unit + n_warps;
+    uint64_t hn[U][2];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      src.pair((next * U + u) * 64 + 2 * lane, next < n_units ? n : 0, pk, hn[u][0], hn[u][1]);
+    uint32_t lo_w[U], hi_w[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t r0 = act[u][0] && block_has(w[u][0], static_cast<uint32_t>(h[u][0]));
+      const uint32_t r1 = act[u][1] && block_has(w[u][1], static_cast<uint32_t>(h[u][1]));
+      const uint32_t v = (r0 | (r1 << 1)) << (2 * (lane & 15));
+      lo_w[u] = __reduce_or_sync(0xFFFFFFFFu, lane < 16 ? v : 0u);
+      hi_w[u] = __reduce_or_sync(0xFFFFFFFFu, lane >= 16 ? v : 0u);
+    }
+    if (kMerge) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const unsigned l = lane - 2u * u;  // 0: lo_w[u], 1: hi_w[u]
+        if (l < 2u) {
+          const uint32_t v = l ? hi_w[u] : lo_w[u];
+          const uint64_t wd = 2 * (g0 + u) + l;
+          if (v && wd < n_out) atomicOr(out + wd, v);
+        }
+      }
+    } else {
+      store_answers<U>(out, n_out, 2 * g0, lo_w, hi_w, lane, out16, out8);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      h[u][0] = hn[u][0];
+      h[u][1] = hn[u][1];
+    }
+  }
+}
+
 }  // namespace sbbf

@@ -83,24 +83,85 @@ sbbf_status launch_insert_filter(const sbbf_t* f, const uint64_t* d_hashes, uint
   return launch_insert(f->words, f->num_blocks, d_hashes, n, s);
 }
 
+// Region passes of a lookup: the filter's blocks split into `passes` equal
+// ranges of at most kRegionBytes, one launch per range over all the keys,
+// each looking up only the keys whose block lies in its range (the first
+// writes every answer word, the later ones OR their bits in).  A filter
+// somewhat larger than what L2 keeps under random access is then read from
+// L2 range by range, at the price of reading the keys once per pass.
+// Automatic mode takes them for filters of more than 84 MiB and at most
+// 192 MiB (two or three 64 MiB regions) and batches of at least 8Mi hashes.
+// Measured on GB300 (1e9 lookups, G/s, region passes against random and
+// partitioned): 80 MiB 183 / 217 / 108, 88 MiB 183 / 171 / 112, 128 MiB 181
+// / 108 / 114, 160 MiB 121 / 88 / 115, 192 MiB 121 / 78 / 116, and at 128
+// MiB with 4Mi, 16Mi and 64Mi hashes 82 / 85 / 45, 137 / 104 / 85, 168 / 110
+// / 106.  Every pass reads all the keys (about 2.8 ms per 1e9 hashes), so
+// smaller regions do not pay: four 32 MiB passes ran 79 G/s at 128 MiB (in
+// a form of the kernel without the hash prefetch, which ran 157 with two).
+constexpr uint64_t kRegionBytes = 64ull << 20;
+constexpr uint64_t kRegionMinBytes = 84ull << 20;
+constexpr uint64_t kRegionMaxBytes = 192ull << 20;
+constexpr uint64_t kRegionMinKeys = 8ull << 20;
+
+uint32_t region_passes(const sbbf_t* f, uint64_t n) {
+  if (f->lanes != 8) return 1;
+  const uint64_t bytes = static_cast<uint64_t>(f->num_blocks) * 32;
+  const uint64_t p = (bytes + kRegionBytes - 1) / kRegionBytes;
+  if (f->partition_mode == SBBF_PARTITION_REGIONS) return p > 1 ? static_cast<uint32_t>(p) : 1;
+  if (f->partition_mode != SBBF_PARTITION_AUTO) return 1;
+  return bytes > kRegionMinBytes && bytes <= kRegionMaxBytes && n >= kRegionMinKeys && p > 1
+             ? static_cast<uint32_t>(p)
+             : 1;
+}
+
+constexpr int kRegionThreads = 512;
+constexpr int kRegionUnroll = 2;
+
+template <bool kMerge>
+sbbf_status launch_region_pass(const sbbf_t* f, const uint64_t* d_hashes, uint64_t n,
+                               uint32_t* d_out, uint32_t lo, uint32_t hi, cudaStream_t s) {
+  auto k = region_find_kernel<kRegionUnroll, kMerge>;
+  const uint64_t units = ((n + 63) / 64 + kRegionUnroll - 1) / kRegionUnroll;
+  const unsigned grid = grid_for(units, kRegionThreads / 32,
+                                 cached_occupancy(reinterpret_cast<const void*>(k), kRegionThreads));
+  k<<<grid, kRegionThreads, 0, s>>>(f->words, f->num_blocks, lo, hi, HashInput(d_hashes), n, d_out);
+  return launch_status();
+}
+
 sbbf_status launch_find_filter(const sbbf_t* f, const uint64_t* d_hashes, uint64_t n,
                                uint32_t* d_out, cudaStream_t s) {
   if (f->lanes != 8)
     return launch_find_lanes(static_cast<int>(f->lanes), f->words, f->num_blocks,
                              HashInput(d_hashes), n, d_out, s);
+  const uint32_t passes = n ? region_passes(f, n) : 1;
+  if (passes > 1) {
+    const uint64_t nb = f->num_blocks;
+    for (uint32_t p = 0; p < passes; ++p) {
+      const uint32_t lo = static_cast<uint32_t>(nb * p / passes);
+      const uint32_t hi = static_cast<uint32_t>(nb * (p + 1) / passes);
+      const sbbf_status st = p == 0 ? launch_region_pass<false>(f, d_hashes, n, d_out, lo, hi, s)
+                                    : launch_region_pass<true>(f, d_hashes, n, d_out, lo, hi, s);
+      if (st != SBBF_OK) return st;
+    }
+    return SBBF_OK;
+  }
   return launch_find(f->words, f->num_blocks, d_hashes, n, d_out, s);
 }
 
-// Batches at least this large go through the partitioned path when the
-// filter is at least kPartitionMin{Insert,Lookup}Bytes (automatic mode).
+// Batches at least this large (kPartitionMinKeys for inserts,
+// kPartitionMinLookupKeys for lookups) go through the partitioned path when
+// the filter is at least kPartitionMin{Insert,Lookup}Bytes (automatic mode;
+// lookups into filters of at most 192 MiB take region passes instead).
 // Measured on GB300 (100M inserts in 16M batches, 1e9 lookups, partitioned
 // against random G keys/s): inserts 78 / 119 at 64 MiB (the filter stays in
 // L2), 77 / 73 at 96 MiB, 77 / 55-65 at 128 MiB, 70 / 40 at 256 MiB;
 // lookups 113 / 148 at 96 MiB, 111-113 / 108-114 at 128 MiB (the two within
 // the spread between boxes: the random path, one kernel and no scratch, is
 // kept there), 110 / 97 at 144 MiB, 118 / 66 at 256 MiB; at 32 GiB 49 / 21.5
-// G inserts/s.
+// G inserts/s.  Partitioned lookups of 4Mi hashes ran 45 / 85 G/s at 128 MiB
+// and 42 / 69 at 192 MiB, so lookups partition from 8Mi hashes.
 constexpr uint64_t kPartitionMinKeys = 4ull << 20;
+constexpr uint64_t kPartitionMinLookupKeys = 8ull << 20;
 constexpr uint64_t kPartitionMinInsertBytes = 96ull << 20;
 constexpr uint64_t kPartitionMinLookupBytes = (128ull << 20) + 1;
 
@@ -116,10 +177,12 @@ constexpr uint64_t kPartitionMinLookupBytes = (128ull << 20) + 1;
 bool want_partition(const sbbf_t* f, uint64_t n, bool lookup) {
   if (f->lanes != 8 || f->partition_mode == SBBF_PARTITION_OFF) return false;
   if (f->partition_mode == SBBF_PARTITION_ON) return true;
+  if (lookup && region_passes(f, n) > 1) return false;  // the lookup takes region passes
   const uint64_t nb = f->num_blocks;
   const bool dense = lookup ? 5 * n >= 3 * nb : 4 * n >= nb;
   const uint64_t min_bytes = lookup ? kPartitionMinLookupBytes : kPartitionMinInsertBytes;
-  return n >= kPartitionMinKeys && nb * 32 >= min_bytes && dense;
+  const uint64_t min_keys = lookup ? kPartitionMinLookupKeys : kPartitionMinKeys;
+  return n >= min_keys && nb * 32 >= min_bytes && dense;
 }
 
 // Grows the filter's scratch (cudaMalloc, synchronous) to hold `bytes`.
@@ -300,9 +363,15 @@ sbbf_status sbbf_insert_hashes(sbbf_t* f, const uint64_t* d_hashes, size_t n,
   return launch_insert_filter(f, d_hashes, n, stream);
 }
 
+sbbf_status sbbf_region_passes(const sbbf_t* f, size_t n, uint32_t* passes) {
+  if (!f || !passes) return SBBF_EINVAL;
+  *passes = n ? region_passes(f, n) : 1;
+  return SBBF_OK;
+}
+
 sbbf_status sbbf_set_partitioning(sbbf_t* f, int mode) {
   if (!f || (mode != SBBF_PARTITION_AUTO && mode != SBBF_PARTITION_OFF &&
-             mode != SBBF_PARTITION_ON))
+             mode != SBBF_PARTITION_ON && mode != SBBF_PARTITION_REGIONS))
     return SBBF_EINVAL;
   f->partition_mode = mode;
   return SBBF_OK;

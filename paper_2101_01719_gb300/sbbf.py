@@ -75,6 +75,7 @@ SIGNATURES = {
     "sbbf_fill_splitmix64": (_int, [_P, _sz, _u64, _u64, _P]),
     "sbbf_fill_queries": (_int, [_P, _sz, _u64, _u64, _u64, _u64, _u64, _u64, _u64, _P]),
     "sbbf_count_bits": (_int, [_P, _sz, _P, _P]),
+    "sbbf_region_passes": (_int, [_P, _sz, _c.POINTER(_u32)]),
     "sbbf_range_digest": (_int, [_P, _u64, _u32, _u64, _P, _P, _P, _P]),
     "sbbf_fill_segment_queries": (_int, [_P, _sz, _P, _P, _u32, _u64, _u64, _u64, _u64, _P]),
     "sbbf_fill_segment_ids": (_int, [_P, _sz, _P, _u32, _P]),
@@ -123,7 +124,7 @@ SIGNATURES = {
 
 OP_INSERT, OP_FIND = 0, 1
 FORM_SEGMENTS, FORM_TAGGED = 0, 1
-PARTITION_AUTO, PARTITION_OFF, PARTITION_ON = 0, 1, 2
+PARTITION_AUTO, PARTITION_OFF, PARTITION_ON, PARTITION_REGIONS = 0, 1, 2, 3
 PIPE_AUTO, PIPE_COPY, PIPE_DIRECT = 0, 1, 2
 
 
@@ -369,7 +370,7 @@ class Filter:
         return self
 
     def set_partitioning(self, mode: int):
-        """PARTITION_AUTO / PARTITION_OFF / PARTITION_ON (see sbbf.h)."""
+        """PARTITION_AUTO / PARTITION_OFF / PARTITION_ON / PARTITION_REGIONS (see sbbf.h)."""
         check(lib().sbbf_set_partitioning(self._h, mode), "sbbf_set_partitioning")
         return self
 
@@ -380,6 +381,12 @@ class Filter:
         check(lib().sbbf_partition_applies(self._h, n, 1 if lookup else 0, _c.byref(v)),
               "sbbf_partition_applies")
         return bool(v.value)
+
+    def region_passes(self, n: int) -> int:
+        """Region passes a lookup of n hashes takes (1: a single pass)."""
+        p = _u32()
+        check(lib().sbbf_region_passes(self._h, n, _c.byref(p)), "sbbf_region_passes")
+        return int(p.value)
 
     def device_status(self, stream=None) -> int:
         """sbbf_device_status: OK, or ETIMEOUT when a device-side wait of a

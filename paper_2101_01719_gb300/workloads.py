@@ -79,7 +79,14 @@ C2_PROFILE = SingleFilterWorkload("sbbf_4194304blk_100M_ins_64M_lookup", 2, 4_19
 C2_PART_PROFILE = SingleFilterWorkload("sbbf_2^26blk_128M_ins_128M_lookup", 32, 2**26,
                                        128 * 2**20, 128 * 2**20, 128 * 2**20, 0.1)
 
-WORKLOADS = {w.name: w for w in (C0, C1, C2, C2_BIG, C2_11BPK, C2_PROFILE, C2_PART_PROFILE)}
+# The same filter with 256M lookups (about 3.2 GB on the device): with the
+# 64M case, separates the per-key DRAM traffic of a lookup by region passes
+# from the per-pass part (each pass loads its region into L2).
+C2_PROFILE_256M = SingleFilterWorkload("sbbf_4194304blk_100M_ins_256M_lookup", 2, 4_194_304,
+                                       100_000_000, 16_000_000, 256 * 2**20, 0.1)
+
+WORKLOADS = {w.name: w for w in (C0, C1, C2, C2_BIG, C2_11BPK, C2_PROFILE, C2_PROFILE_256M,
+                                 C2_PART_PROFILE)}
 
 
 def gen_inserts(w: SingleFilterWorkload, start: int, n: int, out: torch.Tensor | None = None,

@@ -72,18 +72,21 @@ def test_bench_uses_no_undefined_names():
 
 def test_step_kernel_counts():
     """gpu_launches: a step launches the clear, one kernel per unpartitioned
-    batch, three per 2^34-key piece of a partitioned insert batch and four per
-    2^31-key piece of a partitioned lookup, plus one hashing kernel per
-    partitioned batch of raw keys."""
+    batch, three per 2^34-key piece of a partitioned insert batch, four per
+    2^31-key piece of a partitioned lookup and one per region pass of a hash
+    lookup, plus one hashing kernel per partitioned batch of raw keys."""
     sys.path.insert(0, ROOT)
     import bench
 
     class FakeFilter:
-        def __init__(self, ins, look):
-            self.ins, self.look = ins, look
+        def __init__(self, ins, look, passes=1):
+            self.ins, self.look, self.passes = ins, look, passes
 
         def partition_applies(self, n, lookup=False):
             return self.look if lookup else self.ins
+
+        def region_passes(self, n):
+            return self.passes
 
     assert bench.step_kernels(FakeFilter(False, False), [(0, 10)], 100, False) == 3
     assert bench.step_kernels(FakeFilter(False, False), [(0, 10), (10, 5)], 100, True) == 4
@@ -91,3 +94,6 @@ def test_step_kernel_counts():
     assert bench.step_kernels(FakeFilter(True, False), [(0, 10)], 100, True) == 1 + 4 + 1
     assert bench.step_kernels(FakeFilter(False, True), [(0, 10)], 2**31 + 1, True) == 1 + 1 + 8 + 1
     assert bench.step_kernels(FakeFilter(True, False), [(0, 2**34 + 1)], 1, False) == 1 + 6 + 1
+    # a lookup by region passes: one launch per pass (hash lookups only)
+    assert bench.step_kernels(FakeFilter(True, False, 2), [(0, 10)], 100, False) == 1 + 3 + 2
+    assert bench.step_kernels(FakeFilter(False, False, 3), [(0, 10)], 100, True) == 1 + 1 + 1

@@ -435,6 +435,36 @@ def test_partitioned_find_equals_oracle(B, n):
     assert np.array_equal(bits_np(f.find(to_dev(q))), oracle.find(ref, B, q))
 
 
+@pytest.mark.parametrize("B,n,passes", [(2**21 + 1, 1, 2), (2**21 + 1, 100_003, 2),
+                                         (3 * 2**20 - 1, 1_000_003, 2),
+                                         (5 * 2**20 + 77, 2_500_033, 3)])
+def test_region_pass_lookups_equal_oracle(B, n, passes):
+    """Lookups by region passes (forced): the first pass writes every answer
+    word, the later ones OR in the answers of the hashes whose block lies in
+    their range.  Every answer equals the oracle's and the single-pass
+    lookup's, tail bits are zero, and nothing is written outside the answer
+    words, with the output at 0, 4, 8 and 12 bytes past a 16-byte boundary
+    (over stale words, which the first pass must overwrite)."""
+    keys = inp.stream(150 + B % 7, 0, max(1, n // 3))
+    q = np.concatenate([inp.stream(150 + B % 7, 1, n - n // 4), keys[: n // 4]])[:n]
+    f = sb.Filter(B)
+    f.insert(to_dev(keys))
+    ref = _oracle_filter(B, keys)
+    exp = oracle.find(ref, B, q)
+    dq = to_dev(q)
+    f.set_partitioning(sb.PARTITION_REGIONS)
+    assert f.region_passes(n) == passes
+    nw = sb.out_words(n)
+    for shift_words in (0, 1, 2, 3):
+        out = torch.full((shift_words + nw + 1,), -1, dtype=torch.int32, device=dev())
+        f.find(dq, out=out[shift_words: shift_words + nw])
+        got = bits_np(out)
+        assert (got[:shift_words] == 0xFFFFFFFF).all() and got[-1] == 0xFFFFFFFF
+        assert np.array_equal(got[shift_words: shift_words + nw], exp)
+    f.set_partitioning(sb.PARTITION_OFF)
+    assert np.array_equal(bits_np(f.find(dq)), exp)
+
+
 @pytest.mark.parametrize("B,n", [(32768, 1_000_003), (3 * 2**20 - 1, 200_001), (7, 130)])
 @pytest.mark.parametrize("shift_words", [1, 2, 3])
 def test_find_into_offset_outputs(B, n, shift_words):
@@ -479,14 +509,17 @@ def test_bits_per_key_sweep(bits_per_key):
 
 
 def test_partition_applies_follows_the_rule():
-    """sbbf_partition_applies reports the automatic rule (at least 4Mi hashes;
-    a filter of at least 96 MiB for inserts and more than 128 MiB for
-    lookups; at least 0.25 hashes per block for inserts and 0.6 for lookups)
-    and the forced modes."""
+    """sbbf_partition_applies and sbbf_region_passes report the automatic
+    rule (region passes for lookups of at least 8Mi hashes into filters of
+    84-192 MiB, 64 MiB per region; otherwise partitioned from 4Mi hashes for
+    inserts and 8Mi for lookups, a filter of at least 96 MiB for inserts and
+    more than 128 MiB for lookups, at least 0.25 hashes per block for
+    inserts and 0.6 for lookups) and the forced modes."""
     f = sb.Filter(2**23)  # 256 MiB
     assert f.partition_applies(2**22) and not f.partition_applies(2**22 - 1)  # 4Mi minimum
-    assert f.partition_applies(5_033_165, lookup=True)       # ceil(0.6 * 2^23)
-    assert not f.partition_applies(5_033_164, lookup=True)
+    assert f.partition_applies(2**23, lookup=True)           # 8Mi minimum for lookups
+    assert not f.partition_applies(2**23 - 1, lookup=True)
+    assert f.region_passes(2**27) == 1
     g = sb.Filter(2**25)  # 1 GiB
     assert g.partition_applies(2**23) and not g.partition_applies(2**23 - 1)  # 0.25 per block
     assert g.partition_applies(20_132_660, lookup=True)      # ceil(0.6 * 2^25)
@@ -496,10 +529,27 @@ def test_partition_applies_follows_the_rule():
     ins96 = sb.Filter(3 * 2**20)  # 96 MiB: inserts partition, lookups do not
     assert ins96.partition_applies(big) and not ins96.partition_applies(big, lookup=True)
     assert not sb.Filter(3 * 2**20 - 1).partition_applies(big)
-    at128 = sb.Filter(2**22)  # 128 MiB: lookups still random
+    at128 = sb.Filter(2**22)  # 128 MiB: lookups by two region passes
     assert at128.partition_applies(big) and not at128.partition_applies(big, lookup=True)
-    assert sb.Filter(2**22 + 1).partition_applies(big, lookup=True)
-    del ins96, at128
+    assert at128.region_passes(big) == 2 and at128.region_passes(2**23) == 2
+    assert at128.region_passes(2**23 - 1) == 1 and at128.region_passes(0) == 1
+    at192 = sb.Filter(6 * 2**20)  # 192 MiB: three region passes
+    assert at192.region_passes(big) == 3 and not at192.partition_applies(big, lookup=True)
+    assert at192.partition_applies(2**23 - 1, lookup=True) is False  # below 8Mi: random
+    above = sb.Filter(6 * 2**20 + 1)  # past 192 MiB: partitioned lookups
+    assert above.region_passes(big) == 1 and above.partition_applies(big, lookup=True)
+    assert sb.Filter(84 * 2**15).region_passes(big) == 1       # 84 MiB: random
+    assert sb.Filter(84 * 2**15 + 1).region_passes(big) == 2
+    assert ins96.region_passes(big) == 2
+    ins96.set_partitioning(sb.PARTITION_OFF)
+    assert ins96.region_passes(big) == 1
+    forced = sb.Filter(2**21 + 1).set_partitioning(sb.PARTITION_REGIONS)  # 64 MiB + 32 B
+    assert forced.region_passes(1) == 2 and sb.Filter(2**21).set_partitioning(
+        sb.PARTITION_REGIONS).region_passes(big) == 1
+    assert not forced.partition_applies(big, lookup=True)
+    assert forced.partition_applies(2**22) is False and sb.Filter(2**23).set_partitioning(
+        sb.PARTITION_REGIONS).partition_applies(2**22)  # inserts: the automatic rule
+    del ins96, at128, at192, above, forced
     f.set_partitioning(sb.PARTITION_OFF)
     assert not f.partition_applies(2**30) and not f.partition_applies(2**30, lookup=True)
     f.set_partitioning(sb.PARTITION_ON)
