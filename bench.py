@@ -82,7 +82,7 @@ def parse_args(argv=None):
                    help="measurement variant: 4- or 16-lane blocks (same filter bytes)")
     p.add_argument("--partition", choices=["auto", "on", "off", "regions"], default="auto",
                    help="single-filter workloads: the filter's partitioning mode (auto: the "
-                        "library's rule; regions: lookups by region passes)")
+                        "library's rule; regions: inserts and lookups by region passes)")
     p.add_argument("--eager", action="store_true",
                    help="launch each kernel from Python instead of replaying CUDA graphs")
     p.add_argument("--requests", type=int, default=0,
@@ -131,12 +131,17 @@ def aggregate(units_per_rank: list[int], seconds_max: float) -> float:
 
 def step_kernels(f, batches, n_lookup, raw_keys):
     """Kernels one single-filter step launches: the clear, each insert batch
-    and the lookup, partitioned or not (sbbf_partition_applies; the kernel
-    counts of each path are stated in sbbf.h)."""
+    and the lookup, by region passes, partitioned or not
+    (sbbf_region_passes, sbbf_partition_applies; the kernel counts of each
+    path are stated in sbbf.h)."""
     hashing = 1 if raw_keys else 0
     n = 1
     for _, cnt in batches:
-        n += (3 * ((cnt + 2**34 - 1) // 2**34) + hashing) if f.partition_applies(cnt) else 1
+        ins_passes = f.region_passes(cnt, lookup=False) if not raw_keys else 1
+        if ins_passes > 1:
+            n += ins_passes
+        else:
+            n += (3 * ((cnt + 2**34 - 1) // 2**34) + hashing) if f.partition_applies(cnt) else 1
     passes = f.region_passes(n_lookup) if not raw_keys else 1
     if passes > 1:
         n += passes
@@ -595,6 +600,7 @@ def run_ours(args):
     clocks = sampler.summary()
     partitioned = {"insert": f.partition_applies(batches[0][1]),
                    "lookup": f.partition_applies(w.n_lookup, lookup=True)}
+    insert_passes = f.region_passes(batches[0][1], lookup=False) if args.keys == "hashes" else 1
     # blocks served from L2: the filter is L2-resident, or each region pass
     # keeps its range of blocks there
     blocks_in_l2 = l2_resident or passes > 1
@@ -631,7 +637,8 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (seeded splitmix64 hashes generated on the device)",
         "config": config,
-        "path": {"partitioned": partitioned, "lookup_region_passes": passes,
+        "path": {"partitioned": partitioned, "insert_region_passes": insert_passes,
+                 "lookup_region_passes": passes,
                  "launch": "eager" if args.eager else "CUDA graph of the step"},
         "roofline": {"bound": "hbm", "kernel": lookup_kernel, "launches_per_lookup": passes,
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",

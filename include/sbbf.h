@@ -156,13 +156,14 @@ sbbf_status sbbf_insert_hashes(sbbf_t *f, const uint64_t *d_hashes, size_t n,
  * batch needs more than the filter holds, kept by the filter and freed by
  * sbbf_destroy; partitioned calls on one filter must therefore be ordered on
  * one stream.
- * Region passes (lookups only, no scratch): the filter's blocks are split
- * into P equal ranges of at most 64 MiB and the lookup runs P kernels over
- * all the hashes, each answering only the hashes whose block lies in its
- * range (the first writes every answer word, the later ones OR their bits
- * in with atomics, so answers of one call must not be read before its last
- * pass ends -- the stream orders that).  Each pass finds its blocks in L2,
- * for filters somewhat larger than what L2 keeps under random access.
+ * Region passes (no scratch): the filter's blocks are split into P equal
+ * ranges of at most 64 MiB and the call runs P kernels over all the hashes,
+ * each inserting or answering only the hashes whose block lies in its range
+ * (a lookup's first pass writes every answer word, the later ones OR their
+ * bits in with atomics, so the answers of one call must not be read before
+ * its last pass ends -- the stream orders that).  Each pass finds its
+ * blocks in L2, for filters somewhat larger than what L2 keeps under random
+ * access.
  *   SBBF_PARTITION_AUTO (default): lookups of at least 8Mi hashes into
  *     filters of more than 84 MiB and at most 192 MiB take region passes
  *     (two or three); otherwise partition batches of at least 4Mi hashes
@@ -172,9 +173,9 @@ sbbf_status sbbf_insert_hashes(sbbf_t *f, const uint64_t *d_hashes, size_t n,
  *     break-evens; if the scratch cannot be allocated, run unpartitioned;
  *   SBBF_PARTITION_OFF: never partition, no region passes;
  *   SBBF_PARTITION_ON: always partition (SBBF_ENOMEM if no scratch);
- *   SBBF_PARTITION_REGIONS: lookups of sbbf_find_hashes (and the host-buffer
- *     lookups) by region passes whenever the filter spans more than one
- *     region; inserts as in automatic mode.
+ *   SBBF_PARTITION_REGIONS: inserts and lookups of hashes (sbbf_*_hashes
+ *     and the host-buffer calls) by region passes whenever the filter spans
+ *     more than one region.
  * Filters of 4 or 16 lanes never partition or take region passes; lookups
  * of raw keys or byte strings take no region passes (where hashes would,
  * they run unpartitioned).
@@ -199,11 +200,12 @@ sbbf_status sbbf_set_partitioning(sbbf_t *f, int mode);
  * Errors: SBBF_EINVAL (NULL filter or applies). */
 sbbf_status sbbf_partition_applies(const sbbf_t *f, size_t n, int lookup, int *applies);
 
-/* Number of region passes (one kernel each) a lookup of n hashes by
- * sbbf_find_hashes takes under the filter's mode, in *passes (1: a single
- * pass, unpartitioned or partitioned).
+/* Number of region passes (one kernel each) an insert (lookup = 0) or a
+ * lookup (lookup != 0) of n hashes by sbbf_insert_hashes / sbbf_find_hashes
+ * takes under the filter's mode, in *passes (1: a single pass, unpartitioned
+ * or partitioned).
  * Errors: SBBF_EINVAL (NULL filter or passes). */
-sbbf_status sbbf_region_passes(const sbbf_t *f, size_t n, uint32_t *passes);
+sbbf_status sbbf_region_passes(const sbbf_t *f, size_t n, int lookup, uint32_t *passes);
 
 /* Outcome of the device-side waits of the partitioned calls on f since the
  * last query.  The partitioned passes stream each CTA's hashes through

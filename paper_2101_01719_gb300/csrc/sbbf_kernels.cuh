@@ -6,7 +6,10 @@
 //                block_index);
 //   Segments     several filters in one arena; keys grouped by filter,
 //                filter t owning keys [offsets[t], offsets[t+1]);
-//   Tagged       several filters; key k names its filter in ids[k].
+//   Tagged       several filters; key k names its filter in ids[k];
+//   RegionFilter one filter restricted to the blocks [lo, hi): keys whose
+//                block lies outside are skipped (one pass of a region-pass
+//                insert).
 // For several filters, filter t is the plain filter of dir[t].num_blocks
 // blocks whose block 0 is arena block dir[t].base, so every filter keeps the
 // paper's block selection and mask.
@@ -60,6 +63,18 @@ struct OneFilter {
   __device__ __forceinline__ void begin_chunk(uint64_t) {}
   __device__ __forceinline__ uint64_t block(uint64_t, uint64_t h) const {
     return block_of(h, num_blocks);
+  }
+  __device__ __forceinline__ void finish() const {}
+};
+
+struct RegionFilter {
+  static constexpr int kMinBlocks = 3;
+  uint32_t num_blocks;
+  uint32_t lo, hi;
+  __device__ __forceinline__ void begin_chunk(uint64_t) {}
+  __device__ __forceinline__ uint64_t block(uint64_t, uint64_t h) const {
+    const uint32_t b = block_of(h, num_blocks);
+    return b - lo < hi - lo ? static_cast<uint64_t>(b) : kNoBlock64;
   }
   __device__ __forceinline__ void finish() const {}
 };

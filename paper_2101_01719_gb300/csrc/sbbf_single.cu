@@ -75,13 +75,6 @@ sbbf_status launch_clear(uint32_t* dst, uint64_t n_words, cudaStream_t s) {
 
 static bool on_device(const sbbf_t* f) { return f->device == current_device(); }
 
-sbbf_status launch_insert_filter(const sbbf_t* f, const uint64_t* d_hashes, uint64_t n,
-                                 cudaStream_t s) {
-  if (f->lanes != 8)
-    return launch_insert_lanes(static_cast<int>(f->lanes), f->words, f->num_blocks,
-                               HashInput(d_hashes), n, s);
-  return launch_insert(f->words, f->num_blocks, d_hashes, n, s);
-}
 
 // Region passes of a lookup: the filter's blocks split into `passes` equal
 // ranges of at most kRegionBytes, one launch per range over all the keys,
@@ -102,16 +95,48 @@ constexpr uint64_t kRegionBytes = 64ull << 20;
 constexpr uint64_t kRegionMinBytes = 84ull << 20;
 constexpr uint64_t kRegionMaxBytes = 192ull << 20;
 constexpr uint64_t kRegionMinKeys = 8ull << 20;
+// Inserts by region passes (the same ranges; one insert_kernel launch per
+// pass, keys outside the pass's range skipped) are not taken in automatic
+// mode: measured against the partitioned insert (100M hashes in 16M batches,
+// G/s) 75 / 77 at 96 MiB, 71 / 77 at 128 MiB, 52 / 75 at 160 MiB; with 4M
+// batches at 128 MiB 56 / 50 against 56 random.  SBBF_PARTITION_REGIONS
+// still forces them.
+constexpr uint64_t kRegionInsertMinBytes = 0;
+constexpr uint64_t kRegionInsertMaxBytes = 0;
+constexpr uint64_t kRegionInsertMinKeys = 8ull << 20;
 
-uint32_t region_passes(const sbbf_t* f, uint64_t n) {
-  if (f->lanes != 8) return 1;
+uint32_t region_passes(const sbbf_t* f, uint64_t n, bool lookup) {
+  if (f->lanes != 8 || n == 0) return 1;
   const uint64_t bytes = static_cast<uint64_t>(f->num_blocks) * 32;
   const uint64_t p = (bytes + kRegionBytes - 1) / kRegionBytes;
   if (f->partition_mode == SBBF_PARTITION_REGIONS) return p > 1 ? static_cast<uint32_t>(p) : 1;
   if (f->partition_mode != SBBF_PARTITION_AUTO) return 1;
-  return bytes > kRegionMinBytes && bytes <= kRegionMaxBytes && n >= kRegionMinKeys && p > 1
-             ? static_cast<uint32_t>(p)
-             : 1;
+  const uint64_t lo = lookup ? kRegionMinBytes : kRegionInsertMinBytes;
+  const uint64_t hi = lookup ? kRegionMaxBytes : kRegionInsertMaxBytes;
+  const uint64_t min_keys = lookup ? kRegionMinKeys : kRegionInsertMinKeys;
+  return bytes > lo && bytes <= hi && n >= min_keys && p > 1 ? static_cast<uint32_t>(p) : 1;
+}
+
+// Block range of pass p of `passes` over num_blocks blocks.
+void region_of(uint64_t num_blocks, uint32_t p, uint32_t passes, uint32_t& lo, uint32_t& hi) {
+  lo = static_cast<uint32_t>(num_blocks * p / passes);
+  hi = static_cast<uint32_t>(num_blocks * (p + 1) / passes);
+}
+
+sbbf_status launch_insert_filter(const sbbf_t* f, const uint64_t* d_hashes, uint64_t n,
+                                 cudaStream_t s) {
+  if (f->lanes != 8)
+    return launch_insert_lanes(static_cast<int>(f->lanes), f->words, f->num_blocks,
+                               HashInput(d_hashes), n, s);
+  const uint32_t passes = region_passes(f, n, false);
+  for (uint32_t p = 0; passes > 1 && p < passes; ++p) {
+    uint32_t lo, hi;
+    region_of(f->num_blocks, p, passes, lo, hi);
+    const sbbf_status st = launch_insert_t(kDefaultInsert, f->words,
+                                           RegionFilter{f->num_blocks, lo, hi}, d_hashes, n, s);
+    if (st != SBBF_OK || p + 1 == passes) return st;
+  }
+  return launch_insert(f->words, f->num_blocks, d_hashes, n, s);
 }
 
 constexpr int kRegionThreads = 512;
@@ -133,12 +158,11 @@ sbbf_status launch_find_filter(const sbbf_t* f, const uint64_t* d_hashes, uint64
   if (f->lanes != 8)
     return launch_find_lanes(static_cast<int>(f->lanes), f->words, f->num_blocks,
                              HashInput(d_hashes), n, d_out, s);
-  const uint32_t passes = n ? region_passes(f, n) : 1;
+  const uint32_t passes = region_passes(f, n, true);
   if (passes > 1) {
-    const uint64_t nb = f->num_blocks;
     for (uint32_t p = 0; p < passes; ++p) {
-      const uint32_t lo = static_cast<uint32_t>(nb * p / passes);
-      const uint32_t hi = static_cast<uint32_t>(nb * (p + 1) / passes);
+      uint32_t lo, hi;
+      region_of(f->num_blocks, p, passes, lo, hi);
       const sbbf_status st = p == 0 ? launch_region_pass<false>(f, d_hashes, n, d_out, lo, hi, s)
                                     : launch_region_pass<true>(f, d_hashes, n, d_out, lo, hi, s);
       if (st != SBBF_OK) return st;
@@ -177,7 +201,7 @@ constexpr uint64_t kPartitionMinLookupBytes = (128ull << 20) + 1;
 bool want_partition(const sbbf_t* f, uint64_t n, bool lookup) {
   if (f->lanes != 8 || f->partition_mode == SBBF_PARTITION_OFF) return false;
   if (f->partition_mode == SBBF_PARTITION_ON) return true;
-  if (lookup && region_passes(f, n) > 1) return false;  // the lookup takes region passes
+  if (region_passes(f, n, lookup) > 1) return false;  // region passes take the batch
   const uint64_t nb = f->num_blocks;
   const bool dense = lookup ? 5 * n >= 3 * nb : 4 * n >= nb;
   const uint64_t min_bytes = lookup ? kPartitionMinLookupBytes : kPartitionMinInsertBytes;
@@ -363,9 +387,9 @@ sbbf_status sbbf_insert_hashes(sbbf_t* f, const uint64_t* d_hashes, size_t n,
   return launch_insert_filter(f, d_hashes, n, stream);
 }
 
-sbbf_status sbbf_region_passes(const sbbf_t* f, size_t n, uint32_t* passes) {
+sbbf_status sbbf_region_passes(const sbbf_t* f, size_t n, int lookup, uint32_t* passes) {
   if (!f || !passes) return SBBF_EINVAL;
-  *passes = n ? region_passes(f, n) : 1;
+  *passes = region_passes(f, n, lookup != 0);
   return SBBF_OK;
 }
 

@@ -75,7 +75,7 @@ SIGNATURES = {
     "sbbf_fill_splitmix64": (_int, [_P, _sz, _u64, _u64, _P]),
     "sbbf_fill_queries": (_int, [_P, _sz, _u64, _u64, _u64, _u64, _u64, _u64, _u64, _P]),
     "sbbf_count_bits": (_int, [_P, _sz, _P, _P]),
-    "sbbf_region_passes": (_int, [_P, _sz, _c.POINTER(_u32)]),
+    "sbbf_region_passes": (_int, [_P, _sz, _int, _c.POINTER(_u32)]),
     "sbbf_range_digest": (_int, [_P, _u64, _u32, _u64, _P, _P, _P, _P]),
     "sbbf_fill_segment_queries": (_int, [_P, _sz, _P, _P, _u32, _u64, _u64, _u64, _u64, _P]),
     "sbbf_fill_segment_ids": (_int, [_P, _sz, _P, _u32, _P]),
@@ -382,10 +382,12 @@ class Filter:
               "sbbf_partition_applies")
         return bool(v.value)
 
-    def region_passes(self, n: int) -> int:
-        """Region passes a lookup of n hashes takes (1: a single pass)."""
+    def region_passes(self, n: int, lookup: bool = True) -> int:
+        """Region passes a lookup (or an insert) of n hashes takes (1: a
+        single pass)."""
         p = _u32()
-        check(lib().sbbf_region_passes(self._h, n, _c.byref(p)), "sbbf_region_passes")
+        check(lib().sbbf_region_passes(self._h, n, 1 if lookup else 0, _c.byref(p)),
+              "sbbf_region_passes")
         return int(p.value)
 
     def device_status(self, stream=None) -> int:

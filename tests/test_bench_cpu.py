@@ -74,19 +74,20 @@ def test_step_kernel_counts():
     """gpu_launches: a step launches the clear, one kernel per unpartitioned
     batch, three per 2^34-key piece of a partitioned insert batch, four per
     2^31-key piece of a partitioned lookup and one per region pass of a hash
-    lookup, plus one hashing kernel per partitioned batch of raw keys."""
+    insert or lookup, plus one hashing kernel per partitioned batch of raw
+    keys."""
     sys.path.insert(0, ROOT)
     import bench
 
     class FakeFilter:
-        def __init__(self, ins, look, passes=1):
-            self.ins, self.look, self.passes = ins, look, passes
+        def __init__(self, ins, look, passes=1, ins_passes=1):
+            self.ins, self.look, self.passes, self.ins_passes = ins, look, passes, ins_passes
 
         def partition_applies(self, n, lookup=False):
             return self.look if lookup else self.ins
 
-        def region_passes(self, n):
-            return self.passes
+        def region_passes(self, n, lookup=True):
+            return self.passes if lookup else self.ins_passes
 
     assert bench.step_kernels(FakeFilter(False, False), [(0, 10)], 100, False) == 3
     assert bench.step_kernels(FakeFilter(False, False), [(0, 10), (10, 5)], 100, True) == 4
@@ -97,3 +98,5 @@ def test_step_kernel_counts():
     # a lookup by region passes: one launch per pass (hash lookups only)
     assert bench.step_kernels(FakeFilter(True, False, 2), [(0, 10)], 100, False) == 1 + 3 + 2
     assert bench.step_kernels(FakeFilter(False, False, 3), [(0, 10)], 100, True) == 1 + 1 + 1
+    assert bench.step_kernels(FakeFilter(True, False, 2, 2), [(0, 10), (10, 5)], 100,
+                              False) == 1 + 2 + 2 + 2

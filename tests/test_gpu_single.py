@@ -465,6 +465,22 @@ def test_region_pass_lookups_equal_oracle(B, n, passes):
     assert np.array_equal(bits_np(f.find(dq)), exp)
 
 
+@pytest.mark.parametrize("B,n,passes", [(2**21 + 1, 1, 2), (2**21 + 1, 1_000_003, 2),
+                                         (5 * 2**20 + 77, 2_500_001, 3)])
+def test_region_pass_inserts_equal_oracle(B, n, passes):
+    """Inserts by region passes (forced): one launch per block range, each
+    inserting only the hashes whose block lies in its range, give the
+    oracle's filter, from a 16-byte aligned and an 8-byte aligned hash
+    array."""
+    keys = inp.stream(160 + B % 5, 0, n + 1)
+    dk = to_dev(keys)
+    for view, kk in ((dk[:n], keys[:n]), (dk[1:], keys[1:])):
+        f = sb.Filter(B).set_partitioning(sb.PARTITION_REGIONS)
+        assert f.region_passes(n, lookup=False) == passes
+        f.insert(view)
+        assert np.array_equal(f.to_numpy(), _oracle_filter(B, kk))
+
+
 @pytest.mark.parametrize("B,n", [(32768, 1_000_003), (3 * 2**20 - 1, 200_001), (7, 130)])
 @pytest.mark.parametrize("shift_words", [1, 2, 3])
 def test_find_into_offset_outputs(B, n, shift_words):
@@ -547,9 +563,11 @@ def test_partition_applies_follows_the_rule():
     assert forced.region_passes(1) == 2 and sb.Filter(2**21).set_partitioning(
         sb.PARTITION_REGIONS).region_passes(big) == 1
     assert not forced.partition_applies(big, lookup=True)
-    assert forced.partition_applies(2**22) is False and sb.Filter(2**23).set_partitioning(
-        sb.PARTITION_REGIONS).partition_applies(2**22)  # inserts: the automatic rule
-    del ins96, at128, at192, above, forced
+    assert forced.partition_applies(2**22) is False and forced.region_passes(5, lookup=False) == 2
+    big_forced = sb.Filter(2**23).set_partitioning(sb.PARTITION_REGIONS)  # 256 MiB: 4 regions
+    assert big_forced.region_passes(2**22, lookup=False) == 4
+    assert not big_forced.partition_applies(2**22)
+    del ins96, at128, at192, above, forced, big_forced
     f.set_partitioning(sb.PARTITION_OFF)
     assert not f.partition_applies(2**30) and not f.partition_applies(2**30, lookup=True)
     f.set_partitioning(sb.PARTITION_ON)
