@@ -69,6 +69,9 @@ def test_argument_checks_need_no_gpu(built):
     assert L.sbbf_partition_applies(None, 10, 0, ctypes.byref(flag)) == sbbf.SBBF_EINVAL
     assert flag.value == 7  # untouched on error
     assert L.sbbf_set_partitioning(None, 0) == sbbf.SBBF_EINVAL
+    passes = ctypes.c_uint32(9)
+    assert L.sbbf_region_passes(None, 10, 1, ctypes.byref(passes)) == sbbf.SBBF_EINVAL
+    assert passes.value == 9  # untouched on error
     assert L.sbbf_device_status(None, None) == sbbf.SBBF_EINVAL
     assert L.sbbf_record_device_status(None, 1, None) == sbbf.SBBF_EINVAL
     lo, hi = ctypes.c_uint32(7), ctypes.c_uint32(7)
