@@ -174,8 +174,10 @@ sbbf_status sbbf_insert_hashes(sbbf_t *f, const uint64_t *d_hashes, size_t n,
  *   SBBF_PARTITION_OFF: never partition, no region passes;
  *   SBBF_PARTITION_ON: always partition (SBBF_ENOMEM if no scratch);
  *   SBBF_PARTITION_REGIONS: inserts and lookups of hashes (sbbf_*_hashes
- *     and the host-buffer calls) by region passes whenever the filter spans
- *     more than one region.
+ *     and the staged host-buffer calls) by region passes whenever the filter
+ *     spans more than one region.
+ * Host-buffer calls that read the hashes in place from host memory (direct
+ * mode) never take region passes: each pass would read them again.
  * Filters of 4 or 16 lanes never partition or take region passes; lookups
  * of raw keys or byte strings take no region passes (where hashes would,
  * they run unpartitioned).

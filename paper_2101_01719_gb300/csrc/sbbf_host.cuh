@@ -118,10 +118,13 @@ inline uint64_t filter_words(const sbbf_filter* f) {
 }
 inline uint64_t filter_bytes(const sbbf_filter* f) { return filter_words(f) * 4; }
 
-// Unpartitioned insert / lookup of device hashes for any lane count.
+// Unpartitioned insert / lookup of device hashes for any lane count: by
+// region passes where the filter's mode asks for them (region_passes), else
+// in one pass.  Callers whose hashes are read from host memory pass
+// regions = false: every region pass would read them again over the link.
 sbbf_status launch_insert_filter(const sbbf_filter* f, const uint64_t* d_hashes, uint64_t n,
-                                 cudaStream_t s);
+                                 cudaStream_t s, bool regions = true);
 sbbf_status launch_find_filter(const sbbf_filter* f, const uint64_t* d_hashes, uint64_t n,
-                               uint32_t* d_out, cudaStream_t s);
+                               uint32_t* d_out, cudaStream_t s, bool regions = true);
 
 }  // namespace sbbf

@@ -139,7 +139,7 @@ sbbf_status sbbf_insert_hashes_host(sbbf_t* f, sbbf_host_pipe_t* p, const uint64
   if (direct < 0) return SBBF_EINVAL;
   if (direct) {
     const sbbf_status st =
-        launch_insert_filter(f, static_cast<const uint64_t*>(d_in), n, stream);
+        launch_insert_filter(f, static_cast<const uint64_t*>(d_in), n, stream, false);
     if (st != SBBF_OK) return st;
     SBBF_CUDA(cudaStreamSynchronize(stream));
     return SBBF_OK;
@@ -165,7 +165,7 @@ sbbf_status sbbf_find_hashes_host(const sbbf_t* f, sbbf_host_pipe_t* p, const ui
     if (reinterpret_cast<uintptr_t>(d_in) & 7 || reinterpret_cast<uintptr_t>(d_out) & 3)
       return SBBF_EINVAL;
     const sbbf_status st = launch_find_filter(f, static_cast<const uint64_t*>(d_in), n,
-                                              static_cast<uint32_t*>(d_out), stream);
+                                              static_cast<uint32_t*>(d_out), stream, false);
     if (st != SBBF_OK) return st;
     SBBF_CUDA(cudaStreamSynchronize(stream));
     return SBBF_OK;

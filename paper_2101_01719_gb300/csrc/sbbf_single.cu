@@ -124,11 +124,11 @@ void region_of(uint64_t num_blocks, uint32_t p, uint32_t passes, uint32_t& lo, u
 }
 
 sbbf_status launch_insert_filter(const sbbf_t* f, const uint64_t* d_hashes, uint64_t n,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, bool regions) {
   if (f->lanes != 8)
     return launch_insert_lanes(static_cast<int>(f->lanes), f->words, f->num_blocks,
                                HashInput(d_hashes), n, s);
-  const uint32_t passes = region_passes(f, n, false);
+  const uint32_t passes = regions ? region_passes(f, n, false) : 1;
   for (uint32_t p = 0; passes > 1 && p < passes; ++p) {
     uint32_t lo, hi;
     region_of(f->num_blocks, p, passes, lo, hi);
@@ -154,11 +154,11 @@ sbbf_status launch_region_pass(const sbbf_t* f, const uint64_t* d_hashes, uint64
 }
 
 sbbf_status launch_find_filter(const sbbf_t* f, const uint64_t* d_hashes, uint64_t n,
-                               uint32_t* d_out, cudaStream_t s) {
+                               uint32_t* d_out, cudaStream_t s, bool regions) {
   if (f->lanes != 8)
     return launch_find_lanes(static_cast<int>(f->lanes), f->words, f->num_blocks,
                              HashInput(d_hashes), n, d_out, s);
-  const uint32_t passes = region_passes(f, n, true);
+  const uint32_t passes = regions ? region_passes(f, n, true) : 1;
   if (passes > 1) {
     for (uint32_t p = 0; p < passes; ++p) {
       uint32_t lo, hi;

@@ -223,6 +223,28 @@ def test_host_pipe_parity():
 
 
 @pytest.mark.parametrize("mode", ["copy", "direct"])
+def test_host_pipe_into_region_pass_filter(mode):
+    """Host-buffer lookups into a 128 MiB filter, which takes region passes
+    for device batches of 8Mi hashes or more: staged chunks of 16Mi hashes go
+    through two region passes, direct access to host memory through one
+    pass; both give the single-pass device lookup's answers."""
+    B = 2**22
+    keys = inp.stream(127, 0, 2_000_000)
+    q = np.concatenate([inp.stream(127, 1, 18_000_003), keys])
+    f = sb.Filter(B)
+    f.insert(to_dev(keys))
+    assert f.region_passes(2**24) == 2
+    f.set_partitioning(sb.PARTITION_OFF)
+    exp = bits_np(f.find(to_dev(q)))
+    f.set_partitioning(sb.PARTITION_AUTO)
+    hq = torch.from_numpy(q.view(np.int64)).pin_memory()
+    out = torch.full((sb.out_words(q.size),), -1, dtype=torch.int32).pin_memory()
+    pipe = sb.HostPipe(2**24, mode=sb.PIPE_COPY if mode == "copy" else sb.PIPE_DIRECT)
+    pipe.find(f, hq, out)
+    assert np.array_equal(out.numpy().view(np.uint32), exp)
+
+
+@pytest.mark.parametrize("mode", ["copy", "direct"])
 def test_host_pipe_modes(mode):
     """Staged copies and in-place kernel access to pinned host memory give the
     oracle's filter and bits; direct mode refuses unmapped (pageable) memory."""
