@@ -443,18 +443,14 @@ __global__ void __launch_bounds__(kMaxThreads)
         b[u][s] = block_of(h[u][s], num_blocks);
         act[u][s] = k < n && b[u][s] - lo < span;
       }
+    // the blocks of the keys in range (the others' words are never read:
+    // their test below is not evaluated)
     uint32_t w[U][2][8];
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        if (act[u][s]) {
-          load_block_na(words + 8ull * b[u][s], pf, w[u][s]);
-        } else {
-#pragma unroll
-          for (int i = 0; i < 8; ++i) w[u][s][i] = 0;
-        }
-      }
+      for (int s = 0; s < 2; ++s)
+        if (act[u][s]) load_block_na(words + 8ull * b[u][s], pf, w[u][s]);
     // the next unit's hashes, in flight while this unit's blocks arrive
     const uint64_t next = unit + n_warps;
     uint64_t hn[U][2];
