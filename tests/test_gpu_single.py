@@ -487,6 +487,28 @@ def test_region_pass_lookups_equal_oracle(B, n, passes):
     assert np.array_equal(bits_np(f.find(dq)), exp)
 
 
+def test_region_passes_random_shapes():
+    """Seeded random filter sizes (one to four 64 MiB regions, ragged) and
+    batch lengths (ragged tails, empty): lookups by forced region passes
+    equal the single-pass lookups, and inserts by forced region passes give
+    the single-pass filter, word for word."""
+    rng = np.random.default_rng(2101)
+    for trial in range(12):
+        B = int(rng.integers(2**20, 4 * 2**21 + 3))
+        n = int(rng.choice([0, 1, 63, 65, int(rng.integers(1, 3_000_000))]))
+        keys = inp.stream(190 + trial, 0, max(n, 1))[:n]
+        dk = to_dev(keys) if n else torch.empty(0, dtype=torch.int64, device=dev())
+        f = sb.Filter(B).set_partitioning(sb.PARTITION_REGIONS)
+        g = sb.Filter(B).set_partitioning(sb.PARTITION_OFF)
+        f.insert(dk)
+        g.insert(dk)
+        assert torch.equal(f.words, g.words), (B, n)
+        q = np.concatenate([inp.stream(190 + trial, 1, n), keys[: n // 3]])
+        dq = to_dev(q) if q.size else torch.empty(0, dtype=torch.int64, device=dev())
+        assert torch.equal(f.find(dq), g.find(dq)), (B, n)
+        del f, g
+
+
 @pytest.mark.parametrize("B,n,passes", [(2**21 + 1, 1, 2), (2**21 + 1, 1_000_003, 2),
                                          (5 * 2**20 + 77, 2_500_001, 3)])
 def test_region_pass_inserts_equal_oracle(B, n, passes):
