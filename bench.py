@@ -298,11 +298,11 @@ def bytes_per_insert(w, l2_bytes: int) -> float:
 def measure_row(name: str, dev, stream, peak: float, l2_bytes: int, steps: int,
                 partition_lookups=("auto",)) -> dict:
     """One single-filter workload timed on its own: build the inputs on the
-    device, warm up, then time `steps` repetitions of all its insert batches
-    (the filter cleared once before; repeated inserts do the same work) and
-    of its lookup batch with CUDA events on the launching stream; the lookup
-    is timed once per partitioning mode listed.  Members must hit (checked
-    on the last answers)."""
+    device, warm up, then time `steps` replays of a CUDA graph of all its
+    insert batches (the filter cleared once before; repeated inserts do the
+    same work) and of one of its lookup batch with CUDA events on the
+    launching stream; the lookup is timed once per partitioning mode listed.
+    Members must hit (checked on the last answers)."""
     import torch
 
     import paper_2101_01719_gb300 as sb
@@ -320,22 +320,33 @@ def measure_row(name: str, dev, stream, peak: float, l2_bytes: int, steps: int,
         for s0, cnt in batches:
             f.insert(ins[s0:s0 + cnt])
 
-    def timed(fn):
+    def timed(fn, graph=False):
+        """fn's average time over `steps` runs after two warm-up runs; with
+        graph, fn is captured once as a CUDA graph and the replays are timed
+        (no host launch overhead between the steps)."""
         for _ in range(2):
             fn()
+        run = fn
+        if graph:
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                fn()
+            run = g.replay
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         a.record(stream)
         for _ in range(steps):
-            fn()
+            run()
         b.record(stream)
         torch.cuda.synchronize()
         return a.elapsed_time(b) / steps
 
     f.clear()
-    insert_ms = timed(insert_all)
+    insert_ms = timed(insert_all, graph=True)
     row = {"filter_bytes": w.filter_bytes, "n_insert": w.n_insert, "n_lookup": w.n_lookup,
+           "launch": "CUDA graph of each operation",
            "insert_partitioned": f.partition_applies(batches[0][1]),
            "insert_gkeys_s": round(w.n_insert / (insert_ms / 1e3) / 1e9, 3),
            "insert_ms": round(insert_ms, 4)}
@@ -348,7 +359,7 @@ def measure_row(name: str, dev, stream, peak: float, l2_bytes: int, steps: int,
              "regions": sb.PARTITION_REGIONS}
     for mode in partition_lookups:
         f.set_partitioning(modes[mode])
-        find_ms = timed(lambda: f.find(qry, out=out))
+        find_ms = timed(lambda: f.find(qry, out=out), graph=True)
         hits = int(sb.count_bits(out, w.n_lookup).item())
         row["lookup"][mode] = {
             "partitioned": f.partition_applies(w.n_lookup, lookup=True),
