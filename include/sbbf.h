@@ -178,9 +178,10 @@ sbbf_status sbbf_insert_hashes(sbbf_t *f, const uint64_t *d_hashes, size_t n,
  *     spans more than one region.
  * Host-buffer calls that read the hashes in place from host memory (direct
  * mode) never take region passes: each pass would read them again.
- * Filters of 4 or 16 lanes never partition or take region passes; lookups
- * of raw keys or byte strings take no region passes (where hashes would,
- * they run unpartitioned).
+ * Filters of 4 or 16 lanes never partition or take region passes.  Lookups
+ * of 4- or 8-byte raw keys take region passes as hashes do (every pass
+ * hashes its keys again); lookups of byte strings take none (where hashes
+ * would, they run unpartitioned).
  * Errors: SBBF_EINVAL (NULL filter or unknown mode). */
 enum {
   SBBF_PARTITION_AUTO = 0,
@@ -204,8 +205,8 @@ sbbf_status sbbf_partition_applies(const sbbf_t *f, size_t n, int lookup, int *a
 
 /* Number of region passes (one kernel each) an insert (lookup = 0) or a
  * lookup (lookup != 0) of n hashes by sbbf_insert_hashes / sbbf_find_hashes
- * takes under the filter's mode, in *passes (1: a single pass, unpartitioned
- * or partitioned).
+ * (and of n fixed-width keys by sbbf_find_keys) takes under the filter's
+ * mode, in *passes (1: a single pass, unpartitioned or partitioned).
  * Errors: SBBF_EINVAL (NULL filter or passes). */
 sbbf_status sbbf_region_passes(const sbbf_t *f, size_t n, int lookup, uint32_t *passes);
 

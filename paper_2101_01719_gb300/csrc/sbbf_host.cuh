@@ -108,6 +108,9 @@ sbbf_status launch_find_partitioned(const uint32_t* words, uint32_t num_blocks,
 // partitioned path: the filter's mode, its size and the batch's keys per
 // block.
 bool want_partition(const sbbf_filter* f, uint64_t n, bool lookup);
+// Region passes an insert or lookup of n hashes takes under the filter's
+// mode (1: none).
+uint32_t region_passes(const sbbf_filter* f, uint64_t n, bool lookup);
 // Grows the filter's scratch (cudaMalloc, synchronous) to at least `bytes`;
 // the first call also allocates the filter's zeroed device status word.
 sbbf_status ensure_scratch(sbbf_filter* f, size_t bytes);

@@ -409,12 +409,13 @@ __global__ void __launch_bounds__(kMaxThreads, find_min_blocks<R, S>(kLanes8, U)
 // gains a bit).  With the filter split into regions small enough to stay in
 // L2, each pass finds its blocks in L2 at the price of reading all the keys.
 // Each warp takes units of U 64-key groups by grid stride and loads the next
-// unit's hashes before it waits on this unit's blocks, so the DRAM latency of
-// the key stream and the L2 latency of the block loads overlap.
-template <int U, bool kMerge>
+// unit's hashes (or keys, hashed as they arrive) before it waits on this
+// unit's blocks, so the DRAM latency of the key stream and the L2 latency of
+// the block loads overlap.
+template <int U, bool kMerge, class S = HashInput>
 __global__ void __launch_bounds__(kMaxThreads)
     region_find_kernel(const uint32_t* __restrict__ words, uint32_t num_blocks, uint32_t lo,
-                       uint32_t hi, HashInput src, uint64_t n, uint32_t* __restrict__ out) {
+                       uint32_t hi, S src, uint64_t n, uint32_t* __restrict__ out) {
   const unsigned lane = lane_id();
   const uint64_t n_groups = (n + 63) >> 6;
   const uint64_t n_units = (n_groups + U - 1) / U;

@@ -139,36 +139,14 @@ sbbf_status launch_insert_filter(const sbbf_t* f, const uint64_t* d_hashes, uint
   return launch_insert(f->words, f->num_blocks, d_hashes, n, s);
 }
 
-constexpr int kRegionThreads = 512;
-constexpr int kRegionUnroll = 2;
-
-template <bool kMerge>
-sbbf_status launch_region_pass(const sbbf_t* f, const uint64_t* d_hashes, uint64_t n,
-                               uint32_t* d_out, uint32_t lo, uint32_t hi, cudaStream_t s) {
-  auto k = region_find_kernel<kRegionUnroll, kMerge>;
-  const uint64_t units = ((n + 63) / 64 + kRegionUnroll - 1) / kRegionUnroll;
-  const unsigned grid = grid_for(units, kRegionThreads / 32,
-                                 cached_occupancy(reinterpret_cast<const void*>(k), kRegionThreads));
-  k<<<grid, kRegionThreads, 0, s>>>(f->words, f->num_blocks, lo, hi, HashInput(d_hashes), n, d_out);
-  return launch_status();
-}
-
 sbbf_status launch_find_filter(const sbbf_t* f, const uint64_t* d_hashes, uint64_t n,
                                uint32_t* d_out, cudaStream_t s, bool regions) {
   if (f->lanes != 8)
     return launch_find_lanes(static_cast<int>(f->lanes), f->words, f->num_blocks,
                              HashInput(d_hashes), n, d_out, s);
   const uint32_t passes = regions ? region_passes(f, n, true) : 1;
-  if (passes > 1) {
-    for (uint32_t p = 0; p < passes; ++p) {
-      uint32_t lo, hi;
-      region_of(f->num_blocks, p, passes, lo, hi);
-      const sbbf_status st = p == 0 ? launch_region_pass<false>(f, d_hashes, n, d_out, lo, hi, s)
-                                    : launch_region_pass<true>(f, d_hashes, n, d_out, lo, hi, s);
-      if (st != SBBF_OK) return st;
-    }
-    return SBBF_OK;
-  }
+  if (passes > 1)
+    return launch_find_regions(f->words, f->num_blocks, HashInput(d_hashes), n, d_out, passes, s);
   return launch_find(f->words, f->num_blocks, d_hashes, n, d_out, s);
 }
 

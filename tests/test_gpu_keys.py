@@ -150,3 +150,38 @@ def test_key_arguments_rejected():
     assert L.sbbf_hash_bytes(buf.data_ptr(), buf.data_ptr() + 4, 1, 0, buf.data_ptr(), s) == abi.SBBF_EINVAL
     assert L.sbbf_insert_keys(f.handle, None, 8, 0, 0, s) == abi.SBBF_OK  # n == 0
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("width", [8, 4])
+def test_fused_keys_by_region_passes(width):
+    """Raw 8- and 4-byte keys looked up by region passes (forced, and in
+    automatic mode on a 128 MiB filter with 8Mi keys or more): each pass
+    hashes its keys again; the answers equal the oracle's on the XXH64
+    hashes and the single-pass lookup's; byte strings take no region pass."""
+    B = 2**22
+    n = 1_000_003
+    if width == 8:
+        keys, q = inp.stream(145, 0, n), inp.stream(145, 1, 3 * n)
+        dk, dq = to_dev(keys), to_dev(np.concatenate([q, keys[: n // 2]]))
+        hq = oracle.xxh64_fixed(np.concatenate([q, keys[: n // 2]]), 9)
+        hk = oracle.xxh64_fixed(keys, 9)
+    else:
+        keys, q = _keys32(n, 7), _keys32(3 * n, 8)
+        qq = np.concatenate([q, keys[: n // 2]])
+        dk, dq = _dev32(keys), _dev32(qq)
+        hq, hk = oracle.xxh64_fixed(qq, 9), oracle.xxh64_fixed(keys, 9)
+    f = sb.Filter(B)
+    f.insert_keys(dk, seed=9)
+    ref = _oracle_filter(B, hk)
+    assert np.array_equal(f.to_numpy(), ref)
+    f.set_partitioning(abi.PARTITION_REGIONS)
+    got = bits_np(f.find_keys(dq, seed=9))
+    assert np.array_equal(got, oracle.find(ref, B, hq))
+    f.set_partitioning(abi.PARTITION_OFF)
+    assert np.array_equal(bits_np(f.find_keys(dq, seed=9)), got)
+    f.set_partitioning(abi.PARTITION_AUTO)
+    assert f.region_passes(2**23) == 2
+    big = torch.cat([dq] * (2**23 // dq.numel() + 1))[: 2**23]
+    auto = bits_np(f.find_keys(big, seed=9))
+    f.set_partitioning(abi.PARTITION_OFF)
+    assert np.array_equal(auto, bits_np(f.find_keys(big, seed=9)))
