@@ -142,7 +142,7 @@ def step_kernels(f, batches, n_lookup, raw_keys):
             n += ins_passes
         else:
             n += (3 * ((cnt + 2**34 - 1) // 2**34) + hashing) if f.partition_applies(cnt) else 1
-    passes = f.region_passes(n_lookup) if not raw_keys else 1
+    passes = f.region_passes(n_lookup)  # hashes and fixed-width raw keys alike
     if passes > 1:
         n += passes
     elif f.partition_applies(n_lookup, lookup=True):
@@ -605,7 +605,7 @@ def run_ours(args):
     ins_per_key = bytes_per_insert(w, l2_bytes)
     ins_per_key -= key_bytes_less
     ins_achieved = ins_per_key * w.n_insert / (insert_ms / 1e3) / 1e9
-    passes = f.region_passes(w.n_lookup) if args.keys == "hashes" else 1
+    passes = f.region_passes(w.n_lookup)
     lookup_kernel = REGION_KERNEL if passes > 1 else DOMINANT_KERNEL
     traffic = None if variant else profiled_traffic(w.name, lookup_kernel)
     clocks = sampler.summary()

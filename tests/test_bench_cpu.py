@@ -73,9 +73,9 @@ def test_bench_uses_no_undefined_names():
 def test_step_kernel_counts():
     """gpu_launches: a step launches the clear, one kernel per unpartitioned
     batch, three per 2^34-key piece of a partitioned insert batch, four per
-    2^31-key piece of a partitioned lookup and one per region pass of a hash
-    insert or lookup, plus one hashing kernel per partitioned batch of raw
-    keys."""
+    2^31-key piece of a partitioned lookup and one per region pass of an
+    insert of hashes or a lookup of hashes or fixed-width keys, plus one
+    hashing kernel per partitioned batch of raw keys."""
     sys.path.insert(0, ROOT)
     import bench
 
@@ -97,6 +97,6 @@ def test_step_kernel_counts():
     assert bench.step_kernels(FakeFilter(True, False), [(0, 2**34 + 1)], 1, False) == 1 + 6 + 1
     # a lookup by region passes: one launch per pass (hash lookups only)
     assert bench.step_kernels(FakeFilter(True, False, 2), [(0, 10)], 100, False) == 1 + 3 + 2
-    assert bench.step_kernels(FakeFilter(False, False, 3), [(0, 10)], 100, True) == 1 + 1 + 1
+    assert bench.step_kernels(FakeFilter(False, False, 3), [(0, 10)], 100, True) == 1 + 1 + 3
     assert bench.step_kernels(FakeFilter(True, False, 2, 2), [(0, 10), (10, 5)], 100,
                               False) == 1 + 2 + 2 + 2
