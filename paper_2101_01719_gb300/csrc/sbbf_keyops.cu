@@ -91,7 +91,9 @@ sbbf_status find_src(const sbbf_t* f, S src, uint64_t n, uint32_t* out, cudaStre
     return launch_find_lanes(static_cast<int>(f->lanes), f->words, f->num_blocks, src, n, out, s);
   if (!S::kHeavy) {  // fixed-width keys, hashed in every pass
     const uint32_t passes = region_passes(f, n, true);
-    if (passes > 1) return launch_find_regions(f->words, f->num_blocks, src, n, out, passes, s);
+    if (passes > 1)
+      return launch_find_regions(f->words, f->num_blocks, 0, 0, f->num_blocks, src, n, out,
+                                 passes, s);
   }
   const bool bypass = static_cast<uint64_t>(f->num_blocks) * 32 > kL1BypassBytes;
   return launch_find_src(bypass, f->words, OneFilter{f->num_blocks}, src, n, out, s);

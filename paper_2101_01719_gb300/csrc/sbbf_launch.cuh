@@ -134,8 +134,9 @@ sbbf_status launch_find_src(bool l1_bypass, const uint32_t* words, R res, S src,
 
 // Region passes of a one-filter lookup (region_find_kernel): `passes`
 // launches over all n keys, pass p answering the keys whose block lies in
-// the p-th of `passes` equal block ranges; the first writes every answer
-// word, the later ones OR their bits in.
+// the p-th of `passes` equal parts of the block range [lo, hi) (the whole
+// filter, or a shard whose words, held from block `base` on, cover it); the
+// first writes every answer word, the later ones OR their bits in.
 // Hashes: two 64-key groups per warp in flight; raw keys (hashed in the
 // kernel, more registers) one.
 constexpr int kRegionThreads = 512;
@@ -145,27 +146,29 @@ constexpr int region_unroll() {
 }
 
 template <bool kMerge, class S>
-sbbf_status launch_region_pass(const uint32_t* words, uint32_t num_blocks, S src, uint64_t n,
-                               uint32_t* out, uint32_t lo, uint32_t hi, cudaStream_t s) {
+sbbf_status launch_region_pass(const uint32_t* words, uint32_t num_blocks, uint32_t base,
+                               S src, uint64_t n, uint32_t* out, uint32_t lo, uint32_t hi,
+                               cudaStream_t s) {
   constexpr int kU = region_unroll<S>();
   auto k = region_find_kernel<kU, kMerge, S>;
   const uint64_t units = ((n + 63) / 64 + kU - 1) / kU;
   const unsigned grid = grid_for(units, kRegionThreads / 32,
                                  cached_occupancy(reinterpret_cast<const void*>(k), kRegionThreads));
-  k<<<grid, kRegionThreads, 0, s>>>(words, num_blocks, lo, hi, src, n, out);
+  k<<<grid, kRegionThreads, 0, s>>>(words, num_blocks, base, lo, hi, src, n, out);
   return launch_status();
 }
 
 template <class S>
-sbbf_status launch_find_regions(const uint32_t* words, uint32_t num_blocks, S src, uint64_t n,
-                                uint32_t* out, uint32_t passes, cudaStream_t s) {
+sbbf_status launch_find_regions(const uint32_t* words, uint32_t num_blocks, uint32_t base,
+                                uint32_t lo, uint32_t hi, S src, uint64_t n, uint32_t* out,
+                                uint32_t passes, cudaStream_t s) {
+  const uint64_t span = hi - lo;
   for (uint32_t p = 0; p < passes; ++p) {
-    const uint32_t lo = static_cast<uint32_t>(static_cast<uint64_t>(num_blocks) * p / passes);
-    const uint32_t hi =
-        static_cast<uint32_t>(static_cast<uint64_t>(num_blocks) * (p + 1) / passes);
-    const sbbf_status st = p == 0
-                               ? launch_region_pass<false>(words, num_blocks, src, n, out, lo, hi, s)
-                               : launch_region_pass<true>(words, num_blocks, src, n, out, lo, hi, s);
+    const uint32_t a = lo + static_cast<uint32_t>(span * p / passes);
+    const uint32_t b = lo + static_cast<uint32_t>(span * (p + 1) / passes);
+    const sbbf_status st =
+        p == 0 ? launch_region_pass<false>(words, num_blocks, base, src, n, out, a, b, s)
+               : launch_region_pass<true>(words, num_blocks, base, src, n, out, a, b, s);
     if (st != SBBF_OK) return st;
   }
   return SBBF_OK;

@@ -250,6 +250,12 @@ sbbf_status sbbf_shard_find(const sbbf_t* f, uint32_t num_blocks, uint32_t lo,
   if (!d_hashes || !d_out_bits || (reinterpret_cast<uintptr_t>(d_hashes) & 7) ||
       (reinterpret_cast<uintptr_t>(d_out_bits) & 3))
     return SBBF_EINVAL;
+  // a shard somewhat larger than what L2 keeps under random access is looked
+  // up in region passes over its block range, as a whole filter would be
+  const uint32_t passes = region_passes(f, n, true);
+  if (passes > 1)
+    return launch_find_regions(f->words, num_blocks, lo, lo, lo + f->num_blocks,
+                               HashInput(d_hashes), n, d_out_bits, passes, stream);
   Tuning t = kDefaultFind;
   t.l1_bypass = static_cast<uint64_t>(f->num_blocks) * 32 > kL1BypassBytes;
   return launch_find_t(t, f->words, ShardFilter{num_blocks, lo, lo + f->num_blocks}, d_hashes, n,

@@ -146,7 +146,8 @@ sbbf_status launch_find_filter(const sbbf_t* f, const uint64_t* d_hashes, uint64
                              HashInput(d_hashes), n, d_out, s);
   const uint32_t passes = regions ? region_passes(f, n, true) : 1;
   if (passes > 1)
-    return launch_find_regions(f->words, f->num_blocks, HashInput(d_hashes), n, d_out, passes, s);
+    return launch_find_regions(f->words, f->num_blocks, 0, 0, f->num_blocks, HashInput(d_hashes),
+                               n, d_out, passes, s);
   return launch_find(f->words, f->num_blocks, d_hashes, n, d_out, s);
 }
 

@@ -174,3 +174,44 @@ def test_sharded_filter_over_nccl_with_one_rank():
         assert bits_np(sf.find(to_dev(q[:0]))).size == 0  # an empty batch
     finally:
         dist.destroy_process_group()
+
+
+def test_sharded_shards_take_region_passes():
+    """Two 128 MiB shards of a 256 MiB filter and over 8Mi routed lookups per
+    shard: each shard looks its hashes up in two region passes over its own
+    block range.  Every answer equals the oracle's and the unsharded
+    filter's."""
+    world, B = 2, 2**23
+    assert sb.Filter(B // world).region_passes(9_000_000) == 2  # a shard-sized filter
+    keys = inp.stream(96, 0, 2_000_000)
+    queries = [np.concatenate([inp.stream(96, 1 + r, 9_000_000), keys[r::world]])
+               for r in range(world)]
+    hub = LoopbackHub(world)
+    results, errors = [None] * world, []
+
+    def rank_main(r):
+        try:
+            torch.cuda.set_device(dev())
+            sf = ShardedFilter(B, comm=LoopbackComm(hub, r), ops=DeviceOps(dev()))
+            sf.insert(to_dev(keys[r::world]))
+            bits = sf.find(to_dev(queries[r]))
+            torch.cuda.synchronize()
+            results[r] = bits_np(bits)
+        except BaseException as e:  # noqa: BLE001 - reported below
+            errors.append("rank %d: %r" % (r, e))
+            hub.barrier.abort()
+
+    threads = [threading.Thread(target=rank_main, args=(r,)) for r in range(world)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=300)
+    assert not errors, errors
+    ref = oracle.new_filter(B)
+    oracle.insert_mt(ref, B, keys, oracle.num_cores())
+    whole = sb.Filter(B).set_partitioning(sb.PARTITION_OFF)
+    whole.insert(to_dev(keys))
+    for r in range(world):
+        exp, _ = oracle.find_mt(ref, B, queries[r], oracle.num_cores())
+        assert np.array_equal(results[r], exp), "answers of shard %d" % r
+        assert np.array_equal(bits_np(whole.find(to_dev(queries[r]))), exp)
