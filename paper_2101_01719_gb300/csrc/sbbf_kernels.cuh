@@ -402,9 +402,10 @@ __global__ void __launch_bounds__(kMaxThreads, find_min_blocks<R, S>(kLanes8, U)
 // ---- region-pass lookup ----------------------------------------------------
 
 // One pass of a region-pass lookup into a one-filter of num_blocks blocks,
-// of which `words` holds the blocks from `base` on (0 for a whole filter, the
-// shard's first block for a block-range shard): the keys whose block (the
-// appendix block_index) lies in [lo, hi) are looked up; the others answer 0 in the first pass (kMerge false: every answer word
+// of which `words` holds the blocks from `base` on (kBased: a block-range
+// shard; otherwise the whole filter and base is 0 -- a separate instance,
+// since the subtraction measured 5% slower for whole filters): the keys whose
+// block (the appendix block_index) lies in [lo, hi) are looked up; the others answer 0 in the first pass (kMerge false: every answer word
 // is written) and keep their bit in the later passes (kMerge true: the new
 // bits are ORed in with fire-and-forget reductions, one per answer word that
 // gains a bit).  With the filter split into regions small enough to stay in
@@ -413,7 +414,7 @@ __global__ void __launch_bounds__(kMaxThreads, find_min_blocks<R, S>(kLanes8, U)
 // unit's hashes (or keys, hashed as they arrive) before it waits on this
 // unit's blocks, so the DRAM latency of the key stream and the L2 latency of
 // the block loads overlap.
-template <int U, bool kMerge, class S = HashInput>
+template <int U, bool kMerge, class S = HashInput, bool kBased = false>
 __global__ void __launch_bounds__(kMaxThreads)
     region_find_kernel(const uint32_t* __restrict__ words, uint32_t num_blocks, uint32_t base,
                        uint32_t lo, uint32_t hi, S src, uint64_t n,
@@ -453,7 +454,7 @@ __global__ void __launch_bounds__(kMaxThreads)
     for (int u = 0; u < U; ++u)
 #pragma unroll
       for (int s = 0; s < 2; ++s)
-        if (act[u][s]) load_block_na(words + 8ull * (b[u][s] - base), pf, w[u][s]);
+        if (act[u][s]) load_block_na(words + 8ull * (kBased ? b[u][s] - base : b[u][s]), pf, w[u][s]);
     // the next unit's hashes, in flight while this unit's blocks arrive
     const uint64_t next = unit + n_warps;
     uint64_t hn[U][2];

@@ -150,7 +150,7 @@ sbbf_status launch_region_pass(const uint32_t* words, uint32_t num_blocks, uint3
                                S src, uint64_t n, uint32_t* out, uint32_t lo, uint32_t hi,
                                cudaStream_t s) {
   constexpr int kU = region_unroll<S>();
-  auto k = region_find_kernel<kU, kMerge, S>;
+  auto k = base ? region_find_kernel<kU, kMerge, S, true> : region_find_kernel<kU, kMerge, S, false>;
   const uint64_t units = ((n + 63) / 64 + kU - 1) / kU;
   const unsigned grid = grid_for(units, kRegionThreads / 32,
                                  cached_occupancy(reinterpret_cast<const void*>(k), kRegionThreads));
